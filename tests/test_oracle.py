@@ -1,0 +1,284 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+* its FFT against a brute-force direct DFT and Parseval's identity;
+* its cutoff sphere against Table 1 of arXiv:2110.07670;
+* its Coulomb pair energies and exchange potentials against closed forms
+  (plane waves, a normalised Gaussian with the Madelung term);
+* its exchange operator against invariants of Eq. 1-4 (Hermiticity, v_ij
+  symmetry, negative semidefiniteness, scaling with the cell);
+* its ACE construction (Section 2.2) against exactness on span(Phi), the
+  trace identity E_x = tr(M), unitary invariance and an LU route.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+# ------------------------------------------------------------------ FFT
+
+def _direct_dft3(a, sign):
+    """Brute force: X[k] = sum_j a[j] exp(sign 2 pi i sum_d j_d k_d / n_d)."""
+    out = np.zeros_like(a, dtype=np.complex128)
+    n = a.shape
+    js = np.indices(n).reshape(3, -1).T
+    flat = a.reshape(-1)
+    for k in np.ndindex(*n):
+        ph = sum(js[:, d] * k[d] / n[d] for d in range(3))
+        out[k] = (flat * np.exp(sign * 2j * np.pi * ph)).sum()
+    return out
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 2), (3, 3, 3), (4, 4, 4), (5, 5, 5), (6, 6, 6), (7, 7, 7), (8, 8, 8),
+                                   (9, 9, 9), (10, 10, 10), (12, 12, 12), (4, 6, 10), (16, 15, 2),
+                                   (1, 18, 1), (20, 1, 1), (1, 1, 24), (30, 1, 1)])
+@pytest.mark.parametrize("sign", [-1, +1])
+def test_fft_matches_direct_dft(shape, sign):
+    rng = np.random.default_rng(hash(shape) % 1000)
+    a = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    ref = _direct_dft3(a, sign)
+    got = oracle.fft3d(a, sign)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max() * max(1, np.log2(a.size))
+
+
+def test_fft_parseval_and_roundtrip():
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((12, 10, 18)) + 1j * rng.standard_normal((12, 10, 18))
+    A = oracle.fft3d(a, -1)
+    assert abs((abs(A) ** 2).sum() / a.size - (abs(a) ** 2).sum()) < 1e-12 * (abs(a) ** 2).sum()
+    back = oracle.fft3d(A, +1) / a.size
+    assert np.abs(back - a).max() < 1e-13
+
+
+def test_fft_single_mode():
+    """A single plane wave transforms to one nonzero entry of height N."""
+    n = (8, 6, 10)
+    k0 = (3, 5, 7)
+    idx = np.indices(n)
+    a = np.exp(2j * np.pi * sum(idx[d] * k0[d] / n[d] for d in range(3)))
+    A = oracle.fft3d(a, -1)
+    expect = np.zeros(n, dtype=complex)
+    expect[k0] = np.prod(n)
+    assert np.abs(A - expect).max() < 1e-10
+
+
+# --------------------------------------------------------------- cutoff
+
+def test_table1_plane_wave_counts():
+    for edge, n_wave, n_dens in _golden("table1_pw_counts.txt"):
+        cell = gen.cubic_cell(float(edge) * gen.BOHR_PER_ANGSTROM)
+        assert len(oracle.half_sphere(cell, 80.0)) == int(n_wave)
+        assert len(oracle.half_sphere(cell, 320.0)) == int(n_dens)
+
+
+@pytest.mark.parametrize("L,ecut", [(10.0, 30.0), (18.6, 80.0), (9.3, 55.5)])
+def test_half_sphere_order_matches_generator(L, ecut):
+    cell = gen.cubic_cell(L)
+    a = oracle.half_sphere(cell, ecut)
+    b = gen.half_sphere(cell, ecut)
+    assert np.array_equal(a, b)
+    assert tuple(a[0]) == (0, 0, 0)
+
+
+def test_half_sphere_non_cubic_cell():
+    cell = np.array([[8.0, 0.0, 0.0], [1.0, 9.0, 0.0], [0.5, -0.7, 10.0]])
+    a = oracle.half_sphere(cell, 25.0)
+    assert np.array_equal(a, gen.half_sphere(cell, 25.0))
+    # every +-G pair represented exactly once
+    s = {tuple(m) for m in a}
+    assert all(tuple(-m) not in s for m in a if any(m))
+
+
+# --------------------------------------------------------- closed forms
+
+def _cos_orbital(miller, mode):
+    """Coefficients of sqrt(2/Omega) cos(G.r) for G = mode (or -mode)."""
+    c = np.zeros(len(miller), dtype=complex)
+    m = np.array(mode)
+    hit = np.nonzero((miller == m).all(1))[0]
+    if len(hit) == 0:
+        hit = np.nonzero((miller == -m).all(1))[0]
+    c[hit[0]] = 1 / np.sqrt(2)
+    return c
+
+
+def test_plane_wave_self_energy():
+    L, ecut, grid = 10.0, 30.0, (18, 18, 18)
+    cell = gen.cubic_cell(L)
+    m = oracle.half_sphere(cell, ecut)
+    c = _cos_orbital(m, (1, 2, 0))
+    e = oracle.pair_energy(c, c, cell, grid, ecut)
+    G2 = (2 * np.pi / L) ** 2 * 5
+    expect = np.pi / (2 * L ** 3 * G2)
+    assert abs(e - expect) < 1e-15
+    golden = dict((k, float(v)) for k, v in _golden("closed_forms.txt"))
+    assert abs(e - golden["plane_wave_L10_G120"]) < 1e-16
+
+
+def test_plane_wave_pair_energy():
+    L, ecut, grid = 10.0, 30.0, (18, 18, 18)
+    cell = gen.cubic_cell(L)
+    m = oracle.half_sphere(cell, ecut)
+    g1, g2 = np.array((1, 2, 0)), np.array((0, -1, 3))
+    ca, cb = _cos_orbital(m, g1), _cos_orbital(m, g2)
+    e = oracle.pair_energy(ca, cb, cell, grid, ecut)
+    f = (2 * np.pi / L) ** 2
+    expect = 2 * np.pi / L ** 3 * (1 / (f * ((g1 - g2) ** 2).sum()) + 1 / (f * ((g1 + g2) ** 2).sum()))
+    assert abs(e - expect) < 1e-15
+    assert abs(oracle.pair_energy(cb, ca, cell, grid, ecut) - e) < 1e-18
+
+
+def test_plane_wave_exchange_potential():
+    """One cosine orbital: V_X phi = -alpha v phi; its G-component is
+    -alpha pi/(2 Omega |G|^2) c(G) (the 3G harmonic lies outside the sphere)."""
+    L, ecut, grid, alpha = 10.0, 5.0, (16, 16, 16), 0.25
+    cell = gen.cubic_cell(L)
+    m = oracle.half_sphere(cell, ecut)
+    mode = np.array((1, 1, 0))
+    c = _cos_orbital(m, mode)[None, :]
+    W, E = oracle.exchange(c, cell, grid, ecut, alpha)
+    G2 = (2 * np.pi / L) ** 2 * 2
+    expect = -alpha * np.pi / (2 * L ** 3 * G2) * c
+    assert np.abs(W - expect).max() < 1e-16
+    assert abs(E - (-alpha * np.pi / (2 * L ** 3 * G2))) < 1e-16
+
+
+@pytest.mark.parametrize("sigma,L,n", [(1.0, 20.0, 96), (0.8, 14.0, 64)])
+def test_gaussian_self_energy_madelung(sigma, L, n):
+    ecut = 80.0
+    cell = gen.cubic_cell(L)
+    m = oracle.half_sphere(cell, ecut)
+    c = gen.gaussian_sum_coefficients(cell, m, [np.array([3.0, 4.0, 5.0])], [sigma], [1.0])
+    assert abs(2 * (abs(c) ** 2).sum() - abs(c[0]) ** 2 - 1) < 1e-12
+    e = oracle.pair_energy(c, c, cell, (n, n, n), ecut)
+    xi_m = 2.83729747948
+    expect = np.sqrt(2 / np.pi) / sigma - xi_m / L + 2 * np.pi * sigma ** 2 / L ** 3
+    assert abs(e - expect) < 1e-10
+    if (sigma, L) == (1.0, 20.0):
+        golden = dict((k, float(v)) for k, v in _golden("closed_forms.txt"))
+        assert abs(e - golden["gaussian_sigma1_L20"]) < 1e-11
+
+
+# ------------------------------------------------------------ invariants
+
+@pytest.fixture(scope="module")
+def small():
+    cell = gen.cubic_cell(7.0)
+    ecut, grid = 14.0, (16, 16, 16)
+    psi = gen.random_orbitals(cell, ecut, 5, seed=11)
+    trials = gen.random_trials(cell, ecut, 3, seed=12)
+    return dict(cell=cell, ecut=ecut, grid=grid, alpha=0.25, psi=psi, trials=trials,
+                m=oracle.half_sphere(cell, ecut))
+
+
+def test_vx_hermitian_and_negative(small):
+    s = small
+    V = oracle.vx_apply(s["psi"], s["trials"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    A = oracle.gamma_gram(s["trials"], V, s["m"])  # <t_a | V_X t_b>
+    assert np.abs(A - A.T).max() < 1e-15
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).max() < 1e-14
+
+
+def test_pair_symmetry(small):
+    s = small
+    p = s["psi"]
+    for a, b in [(0, 1), (2, 4), (3, 3)]:
+        e1 = oracle.pair_energy(p[a], p[b], s["cell"], s["grid"], s["ecut"])
+        e2 = oracle.pair_energy(p[b], p[a], s["cell"], s["grid"], s["ecut"])
+        assert abs(e1 - e2) < 1e-16 + 1e-13 * abs(e1)
+        assert e1 >= -1e-16 if a == b else True
+
+
+def test_symmetric_and_one_sided_paths_agree(small):
+    s = small
+    W, E = oracle.exchange(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    V = oracle.vx_apply(s["psi"], s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    assert np.abs(W - V).max() < 1e-15
+    # E_x = -alpha sum_ij e_ij from pair energies
+    n = len(s["psi"])
+    e = sum(oracle.pair_energy(s["psi"][i], s["psi"][j], s["cell"], s["grid"], s["ecut"])
+            for i in range(n) for j in range(n))
+    assert abs(E + s["alpha"] * e) < 1e-14
+
+
+def test_ace_exactness_trace_and_lu(small):
+    s = small
+    r = oracle.ace_build(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    # K phi_i = W_i on span(Phi)
+    K = oracle.ace_apply(r["xi"], s["psi"], s["m"])
+    assert np.abs(K - r["W_G"]).max() < 1e-15
+    # E_x = tr(M)
+    assert abs(np.trace(r["M"]) - r["E_x"]) < 1e-14
+    # M symmetric negative definite
+    assert np.abs(r["M"] - r["M"].T).max() < 1e-15
+    assert np.linalg.eigvalsh(r["M"]).max() < 0
+    # an independent route: W M^-1 W^T psi
+    K1 = oracle.ace_apply(r["xi"], s["trials"], s["m"])
+    K2 = oracle.ace_apply_lu(r["W_G"], r["M"], s["trials"], s["m"])
+    assert np.abs(K1 - K2).max() < 1e-14 * np.abs(K1).max() + 1e-18
+
+
+def test_cholesky_against_numpy():
+    rng = np.random.default_rng(0)
+    B = rng.standard_normal((9, 9))
+    A = B @ B.T + 9 * np.eye(9)
+    assert np.abs(oracle.cholesky(A) - np.linalg.cholesky(A)).max() < 1e-13
+    with pytest.raises(RuntimeError):
+        oracle.cholesky(-A)
+
+
+def test_unitary_invariance(small):
+    s = small
+    rng = np.random.default_rng(5)
+    U, _ = np.linalg.qr(rng.standard_normal((5, 5)))
+    r1 = oracle.ace_build(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    r2 = oracle.ace_build(U.T @ s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    assert abs(r1["E_x"] - r2["E_x"]) < 1e-14
+    K1 = oracle.ace_apply(r1["xi"], s["trials"], s["m"])
+    K2 = oracle.ace_apply(r2["xi"], s["trials"], s["m"])
+    assert np.abs(K1 - K2).max() < 1e-13 * np.abs(K1).max()
+
+
+def test_exact_cell_scaling(small):
+    """Same coefficients and grid, cell scaled by s: every Coulomb energy scales as 1/s."""
+    s = small
+    r1 = oracle.ace_build(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    sc = 1.7
+    r2 = oracle.ace_build(s["psi"], s["cell"] * sc, s["grid"], s["ecut"] / sc ** 2, s["alpha"])
+    assert abs(r2["E_x"] - r1["E_x"] / sc) < 1e-14
+    assert np.abs(r2["W_G"] - r1["W_G"] / sc).max() < 1e-15
+
+
+def test_screened_lists(small):
+    s = small
+    n = len(s["psi"])
+    full = gen.all_pairs_csr(n)
+    r0 = oracle.exchange(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    r1 = oracle.exchange(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"], pairs=full)
+    assert np.abs(r0[0] - r1[0]).max() < 1e-16 and abs(r0[1] - r1[1]) < 1e-15
+    diag = (np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32))
+    W, E = oracle.exchange(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"], pairs=diag)
+    e = sum(oracle.pair_energy(p, p, s["cell"], s["grid"], s["ecut"]) for p in s["psi"])
+    assert abs(E + s["alpha"] * e) < 1e-15
+
+
+def test_grid_too_small_rejected():
+    cell = gen.cubic_cell(10.0)
+    psi = gen.random_orbitals(cell, 30.0, 2, seed=1)
+    with pytest.raises(RuntimeError):
+        oracle.exchange(psi, cell, (12, 12, 12), 30.0, 0.25)
