@@ -1,0 +1,137 @@
+/*
+ * ace.h -- C ABI of the GB300 library that builds and applies the adaptively
+ * compressed exchange (ACE) operator, the data-parallel hot path of the
+ * MTACE / s-MTACE schemes of arXiv:2110.07670 (Mandal, Kar, Kloeffel, Meyer,
+ * Nair).
+ *
+ * What the calls compute (Section 2.1-2.2 of the paper, Eq. 1-5):
+ *   V_X phi_i   = -sum_j v_ij(r) phi_j(r)                         (Eq. 2)
+ *   v_ij(r)     = <phi_j| 1/r12 |phi_i>, solved in reciprocal space  (Eq. 3)
+ *   E_X         = -sum_{i,j} <phi_i| v_ij |phi_j>                  (Eq. 4)
+ *   V_X^ACE     = -sum_k |P_k><P_k|                                (Section 2.2)
+ *   V_X^ACE psi = -sum_k P_k <P_k|psi>                             (Eq. 5)
+ * with every exchange quantity scaled by the exact-exchange fraction alpha
+ * (PBE0: 0.25).  The ACE vectors are xi = P = W L^-T, where W = alpha V_X Phi,
+ * M = Phi^T W and -M = L L^T; the operator K = -xi xi^T equals alpha V_X on
+ * the span of the occupied orbitals.
+ *
+ * Conventions (all arrays row-major, C order):
+ *  - cell[9]: lattice vectors a1, a2, a3 as rows, bohr.  Reciprocal vectors
+ *    b = 2 pi inv(A)^T.  G = h b1 + k b2 + l b3.
+ *  - Plane waves: |G|^2 <= ecut_ry (bohr^-2; Ry units make |G|^2 the kinetic
+ *    energy), the convention that reproduces the plane-wave counts of the
+ *    paper's Table 1.
+ *  - Gamma point: orbitals are real, c(-G) = c(G)^*, and only the half sphere
+ *    {h>0} U {h=0,k>0} U {h=k=0,l>=0} is stored, in lexicographic (h,k,l)
+ *    order (G = 0 is entry 0).  n_pw_half entries per vector.  Im c(0) must be
+ *    zero (|Im c(0)| > 1e-6 is ACE_ERR_INVALID_ARG).
+ *  - psi(r) = Omega^-1/2 sum_G c(G) e^{iG.r}; a normalised orbital has full-
+ *    sphere sum |c|^2 = 1.
+ *  - Real-space grid grid[3] = (n0, n1, n2) along (a1, a2, a3); each n is a
+ *    product of 2, 3, 5 and n_d >= 2 max|Miller_d| + 1.
+ *  - Coulomb kernel 4 pi / |G|^2 on every G of the FFT box (folded to
+ *    -n/2..n/2-1), G = 0 term dropped.
+ *  - Vectors are complex, interleaved (re, im): complex128 for ACE_FP64 plans,
+ *    complex64 for ACE_MIXED plans.  [rows][n_pw_half].
+ *
+ * Ownership: every vector argument is a DEVICE pointer owned by the caller;
+ * pair lists and E_x are HOST pointers.  The library owns only the plan (its
+ * workspace, FFT plans and device-side pair lists), created and destroyed
+ * explicitly.  Work is enqueued on the given CUDA stream (a cudaStream_t
+ * passed as void*, NULL = legacy default stream); calls that return a host
+ * scalar (E_x) synchronise that stream.  A plan may be used by one host
+ * thread at a time.
+ *
+ * Errors: every call returns ACE_OK (0) or a negative code; ace_last_error()
+ * gives the message of the calling thread's last failure.
+ */
+#ifndef ACE_H
+#define ACE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ACE_OK = 0,
+    ACE_ERR_INVALID_ARG = -1,
+    ACE_ERR_GRID_TOO_SMALL = -2, /* n_d < 2 max|Miller_d| + 1, or a prime factor above 5 */
+    ACE_ERR_NOT_POSDEF = -3,     /* -M is not positive definite (dependent or zero orbitals) */
+    ACE_ERR_OOM = -4,
+    ACE_ERR_CUDA = -5,
+    ACE_ERR_TIMEOUT = -6 /* a bounded device-side wait gave up */
+};
+
+enum { ACE_FP64 = 0, ACE_MIXED = 1 };
+
+typedef struct ace_plan ace_plan;
+
+typedef struct {
+    int pair_batch;    /* packed pair transforms per pass launch; 0 = automatic */
+    int deterministic; /* reserved: 1 = atomic-free accumulation of W */
+} ace_opts;
+
+/*
+ * Create a plan for one system: grid, cell, cutoff, the largest occupied set
+ * it will see, and the precision (ACE_FP64: every step in double; ACE_MIXED:
+ * FFTs, pair products and W in float, M / Cholesky / triangular solve / E_x
+ * in double).  opts may be NULL.  Allocates the plan's device workspace on the
+ * current device.
+ */
+int ace_plan_create(ace_plan** plan, const int grid[3], const double cell[9], double ecut_ry, int n_occ_max,
+                    int precision, const ace_opts* opts);
+
+void ace_plan_destroy(ace_plan* plan);
+
+/* Number of half-sphere plane waves and, when miller != NULL, their Miller
+ * indices [n_pw_half][3] (host memory, canonical order). */
+int ace_gvec(const ace_plan* plan, int* n_pw_half, int32_t* miller);
+
+/*
+ * Build the ACE operator (an outer MTS step, Section 2.3): every listed pair
+ * density phi_i phi_j, its Poisson solve (Eq. 3), W = alpha V_X Phi (Eq. 2),
+ * M = Phi^T W, -M = L L^T, xi = W L^-T, and E_x = -alpha sum (2 - d_ij) e_ij
+ * over the listed pairs i <= j (Eq. 4).
+ *   psi_G  [n_occ][n_pw_half] device, orthonormal occupied orbitals
+ *   pair_row_ptr[n_occ+1], pair_col[]: host CSR of the kept pairs (row i lists
+ *          columns j >= i, ascending); both NULL = every pair i <= j
+ *   xi     [n_occ][n_pw_half] device output
+ *   E_x    host output (may be NULL)
+ * ACE_ERR_NOT_POSDEF if -M is not positive definite.
+ */
+int ace_build(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const int32_t* pair_row_ptr,
+              const int32_t* pair_col, void* xi, double* E_x, void* stream);
+
+/*
+ * Apply the compressed operator (Eq. 5, an inner MTS step):
+ *   Kpsi = -xi (xi^T psi), with the Gamma-point inner product
+ *   <a|b> = 2 Re sum_{half} a^* b - a(0) b(0).
+ *   xi [n_occ][n_pw_half], psi [T][n_pw_half], Kpsi [T][n_pw_half]: device.
+ */
+int ace_apply(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T, void* Kpsi, void* stream);
+
+/*
+ * Exact exchange on trial vectors (Eq. 2 with the occupied set psi_occ):
+ *   Vx_psi[t] = -alpha sum_j v_{t j} phi_j, projected on the half sphere.
+ *   psi_occ [n_occ][n_pw_half], psi [T][n_pw_half], Vx_psi [T][n_pw_half].
+ */
+int hfx_apply_exact(ace_plan* plan, const void* psi_occ, int n_occ, double alpha, const void* psi, int T,
+                    void* Vx_psi, void* stream);
+
+/*
+ * Intermediates of the last ace_build on this plan (for checking):
+ *   W_G [n_occ][n_pw_half] device (alpha-scaled V_X Phi), may be NULL;
+ *   M   [n_occ][n_occ] host doubles, may be NULL.  Synchronises the stream.
+ */
+int ace_last_intermediates(ace_plan* plan, void* W_G, double* M, void* stream);
+
+/* Message of this thread's last error ("" if none); returns its length. */
+int ace_last_error(char* buf, int len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACE_H */

@@ -1,0 +1,204 @@
+"""GB300 library for the adaptively compressed exchange (ACE) operator.
+
+The data-parallel hot path of the MTACE / s-MTACE schemes of arXiv:2110.07670
+(Sections 2.1-2.2, Eq. 1-5): pair densities, their FFT Poisson solves, the
+exchange accumulation W = alpha V_X Phi, M = Phi^T W, the Cholesky factor of
+-M, the ACE vectors xi = W L^-T and the inner-step apply K psi = -xi (xi^T psi).
+
+All arithmetic runs in the CUDA library libace_gb300.so (C ABI in
+include/ace.h).  This module only marshals arguments: PyTorch tensors supply
+device memory and the current CUDA stream.  There is no CPU fallback; calls
+fail loudly when the library is missing.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ACE_FP64 = 0
+ACE_MIXED = 1
+_ERRORS = {-1: "ACE_ERR_INVALID_ARG", -2: "ACE_ERR_GRID_TOO_SMALL", -3: "ACE_ERR_NOT_POSDEF", -4: "ACE_ERR_OOM",
+           -5: "ACE_ERR_CUDA", -6: "ACE_ERR_TIMEOUT"}
+SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_apply", "hfx_apply_exact",
+           "ace_last_intermediates", "ace_last_error")
+
+_lib = None
+
+
+class AceError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("pair_batch", ctypes.c_int), ("deterministic", ctypes.c_int)]
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load libace_gb300.so (raises when it is missing unless asked to build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: build it with paper_2110_07670_gb300.build.build_library()")
+        _build.build_library()
+    lib = ctypes.CDLL(path)
+    P, i32, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.ace_plan_create.argtypes = [ctypes.POINTER(P), P, P, f64, i32, i32, ctypes.POINTER(_Opts)]
+    lib.ace_plan_destroy.argtypes = [P]
+    lib.ace_plan_destroy.restype = None
+    lib.ace_gvec.argtypes = [P, ctypes.POINTER(i32), P]
+    lib.ace_build.argtypes = [P, P, i32, f64, P, P, P, ctypes.POINTER(f64), P]
+    lib.ace_apply.argtypes = [P, P, i32, P, i32, P, P]
+    lib.hfx_apply_exact.argtypes = [P, P, i32, f64, P, i32, P, P]
+    lib.ace_last_intermediates.argtypes = [P, P, P, P]
+    lib.ace_last_error.argtypes = [ctypes.c_char_p, i32]
+    for name in SYMBOLS:
+        if name != "ace_plan_destroy":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != 0:
+        buf = ctypes.create_string_buffer(512)
+        load().ace_last_error(buf, 512)
+        raise AceError(code, buf.value.decode())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Plan:
+    """One system: grid, cell (rows = lattice vectors, bohr), cutoff (Ry),
+    the largest occupied set, and the precision ("mixed" or "fp64")."""
+
+    def __init__(self, grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0):
+        lib = load()
+        self.precision = precision
+        self.prec = ACE_MIXED if precision == "mixed" else ACE_FP64
+        g = np.ascontiguousarray(np.asarray(grid, dtype=np.int32).reshape(3))
+        c = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(9))
+        h = ctypes.c_void_p()
+        opts = _Opts(int(pair_batch), 0)
+        _check(lib.ace_plan_create(ctypes.byref(h), g.ctypes.data_as(ctypes.c_void_p),
+                                   c.ctypes.data_as(ctypes.c_void_p), float(ecut), int(n_occ_max), self.prec,
+                                   ctypes.byref(opts)))
+        self.handle = h
+        self.grid = tuple(int(x) for x in g)
+        self.n_occ_max = int(n_occ_max)
+        n = ctypes.c_int(0)
+        _check(lib.ace_gvec(h, ctypes.byref(n), None))
+        self.n_pw_half = n.value
+
+    @property
+    def cdtype(self):
+        import torch
+        return torch.complex64 if self.prec == ACE_MIXED else torch.complex128
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().ace_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _vec(self, t, name):
+        if t.dtype != self.cdtype or not t.is_cuda or not t.is_contiguous() or t.dim() != 2 \
+                or t.shape[1] != self.n_pw_half:
+            raise ValueError(f"{name}: expected a contiguous CUDA {self.cdtype} tensor [rows][{self.n_pw_half}]")
+        return t
+
+
+def ace_plan_create(grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0):
+    return Plan(grid, cell, ecut, n_occ_max, precision, pair_batch)
+
+
+def ace_plan_destroy(plan):
+    plan.close()
+
+
+def ace_gvec(plan):
+    """Miller indices [n_pw_half, 3] of the plan's half sphere, canonical order."""
+    m = np.zeros((plan.n_pw_half, 3), dtype=np.int32)
+    n = ctypes.c_int(0)
+    _check(load().ace_gvec(plan.handle, ctypes.byref(n), m.ctypes.data_as(ctypes.c_void_p)))
+    return m
+
+
+def ace_build(plan, psi_G, alpha, pairs=None, xi=None, stream=None):
+    """Build the ACE vectors; returns (xi, E_x).  pairs = (row_ptr, col) CSR of
+    kept pairs i <= j, or None for every pair."""
+    import torch
+    psi_G = plan._vec(psi_G, "psi_G")
+    n_occ = psi_G.shape[0]
+    if xi is None:
+        xi = torch.empty_like(psi_G)
+    plan._vec(xi, "xi")
+    rp = col = None
+    if pairs is not None:
+        rp = np.ascontiguousarray(pairs[0], dtype=np.int32)
+        col = np.ascontiguousarray(pairs[1], dtype=np.int32)
+    E = ctypes.c_double(0.0)
+    _check(load().ace_build(plan.handle, _ptr(psi_G), n_occ, float(alpha),
+                            rp.ctypes.data_as(ctypes.c_void_p) if rp is not None else None,
+                            col.ctypes.data_as(ctypes.c_void_p) if col is not None else None,
+                            _ptr(xi), ctypes.byref(E), _stream(stream)))
+    return xi, E.value
+
+
+def ace_apply(plan, xi, psi, out=None, stream=None):
+    """K psi = -xi (xi^T psi)."""
+    import torch
+    plan._vec(xi, "xi")
+    plan._vec(psi, "psi")
+    if out is None:
+        out = torch.empty_like(psi)
+    plan._vec(out, "out")
+    _check(load().ace_apply(plan.handle, _ptr(xi), xi.shape[0], _ptr(psi), psi.shape[0], _ptr(out),
+                            _stream(stream)))
+    return out
+
+
+def hfx_apply_exact(plan, psi_occ, alpha, psi, out=None, stream=None):
+    """alpha V_X psi with the exact exchange operator of the occupied set."""
+    import torch
+    plan._vec(psi_occ, "psi_occ")
+    plan._vec(psi, "psi")
+    if out is None:
+        out = torch.empty_like(psi)
+    plan._vec(out, "out")
+    _check(load().hfx_apply_exact(plan.handle, _ptr(psi_occ), psi_occ.shape[0], float(alpha), _ptr(psi),
+                                  psi.shape[0], _ptr(out), _stream(stream)))
+    return out
+
+
+def ace_last_intermediates(plan, n_occ, stream=None):
+    """(W_G, M) of the last ace_build: W_G on the device, M as a numpy array."""
+    import torch
+    W = torch.empty((n_occ, plan.n_pw_half), dtype=plan.cdtype, device="cuda")
+    M = np.zeros((n_occ, n_occ))
+    _check(load().ace_last_intermediates(plan.handle, _ptr(W), M.ctypes.data_as(ctypes.c_void_p),
+                                         _stream(stream)))
+    return W, M

@@ -1,0 +1,643 @@
+// ace_abi.cu -- the C ABI of include/ace.h: plans, workspace, and the order in
+// which the kernels run for the ACE build, the ACE apply and the exact
+// exchange apply (arXiv:2110.07670 Sections 2.1-2.2, Eq. 2-5).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ace.h"
+#include "internal.h"
+
+using namespace ace;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define ACE_CK(expr)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = (expr);                                                                      \
+        if (e_ != cudaSuccess) return fail(ACE_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define ACE_TRY(expr)          \
+    do {                       \
+        int s_ = (expr);       \
+        if (s_ != ACE_OK) return s_; \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool reciprocal(const double a[9], double b[9], double* omega) {
+    const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                       a[2] * (a[3] * a[7] - a[4] * a[6]);
+    if (!(std::fabs(det) > 0)) return false;
+    *omega = std::fabs(det);
+    // b_i = 2 pi (a_j x a_k) / det, rows
+    const double* r[3] = {a, a + 3, a + 6};
+    for (int i = 0; i < 3; ++i) {
+        const double* u = r[(i + 1) % 3];
+        const double* v = r[(i + 2) % 3];
+        b[3 * i + 0] = 2 * M_PI * (u[1] * v[2] - u[2] * v[1]) / det;
+        b[3 * i + 1] = 2 * M_PI * (u[2] * v[0] - u[0] * v[2]) / det;
+        b[3 * i + 2] = 2 * M_PI * (u[0] * v[1] - u[1] * v[0]) / det;
+    }
+    return true;
+}
+
+int roundup(int x, int m) { return (x + m - 1) / m * m; }
+
+int largest_divisor_at_most(int n, int cap) {
+    for (int d = std::min(n, std::max(cap, 1)); d >= 1; --d)
+        if (n % d == 0) return d;
+    return 1;
+}
+
+}  // namespace
+
+struct ace_plan {
+    int dev = 0;
+    int prec = ACE_MIXED;
+    int n[3] = {0, 0, 0};
+    long long N = 0;
+    double cell[9], b[9], omega = 0, ecut = 0;
+    int n_occ_max = 0;
+    std::vector<int32_t> miller;
+    int npw = 0;
+    int* d_ip = nullptr;
+    int* d_in = nullptr;
+    AxisPlan ax[3];
+    void* d_tw[3] = {nullptr, nullptr, nullptr};
+    int* d_freq[3] = {nullptr, nullptr, nullptr};
+    bool fused_xy = false;
+    PassShape s_xy{}, s_x{}, s_y{}, s_z{};
+    int ntiles_last = 1;  // tiles of the pass that accumulates W
+    int batch = 1;
+    size_t esz = 8;  // bytes of one real
+    void* d_phi = nullptr;
+    void* d_acc = nullptr;
+    void* d_spec = nullptr;
+    void* d_WG = nullptr;
+    double* d_M = nullptr;
+    double* d_L = nullptr;
+    double* d_Linv = nullptr;
+    double* d_E = nullptr;
+    int* d_status = nullptr;
+    double* d_part = nullptr;
+    size_t part_cap = 0;
+    Quad* d_quads = nullptr;
+    size_t quads_cap = 0;
+    double* d_epart = nullptr;
+    size_t epart_cap = 0;
+    void* d_tphi = nullptr;
+    void* d_tacc = nullptr;
+    size_t t_cap = 0;
+    double* d_C = nullptr;
+    size_t C_cap = 0;
+    int last_n_occ = 0;
+};
+
+namespace {
+
+template <typename T>
+int grow(T** p, size_t* cap, size_t need) {
+    if (need <= *cap) return ACE_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc((void**)p, need * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ACE_ERR_OOM, "device allocation of " + std::to_string(need * sizeof(T)) + " bytes failed");
+    }
+    *cap = need;
+    return ACE_OK;
+}
+
+int dalloc(void** p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ACE_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    return ACE_OK;
+}
+
+void half_sphere(const double cell[9], const double b[9], double ecut, std::vector<int32_t>& m) {
+    int lim[3];
+    for (int i = 0; i < 3; ++i) {
+        const double len = std::sqrt(cell[3 * i] * cell[3 * i] + cell[3 * i + 1] * cell[3 * i + 1] +
+                                     cell[3 * i + 2] * cell[3 * i + 2]);
+        lim[i] = (int)std::floor(std::sqrt(ecut) * len / (2 * M_PI)) + 1;
+    }
+    m.clear();
+    for (int h = 0; h <= lim[0]; ++h)
+        for (int k = -lim[1]; k <= lim[1]; ++k)
+            for (int l = -lim[2]; l <= lim[2]; ++l) {
+                if (!(h > 0 || (h == 0 && k > 0) || (h == 0 && k == 0 && l >= 0))) continue;
+                double g2 = 0;
+                for (int j = 0; j < 3; ++j) {
+                    const double g = h * b[j] + k * b[3 + j] + l * b[6 + j];
+                    g2 += g * g;
+                }
+                if (g2 > ecut) continue;
+                m.push_back(h);
+                m.push_back(k);
+                m.push_back(l);
+            }
+}
+
+template <typename R>
+int setup_shapes(ace_plan* P) {
+    int smax = 0;
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->dev);
+    if (smax <= 0) smax = 227 * 1024;
+    const size_t c = sizeof(cx<R>);
+    const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
+    auto mk_shape = [&](int tz, int ty, int tx, int axes) {
+        PassShape s{};
+        s.tz = tz;
+        s.ty = ty;
+        s.tx = tx;
+        s.axes = axes;
+        const int e = tz * ty * tx;
+        s.threads = std::min(512, std::max(128, roundup(e / 16, 32)));
+        const int tw = ((axes & 1) ? n2 : 0) + ((axes & 2) ? n1 : 0) + ((axes & 4) ? n0 : 0);
+        s.smem = (size_t)e * c + (size_t)tw * c + ((axes & 4) ? (size_t)(n0 + n1 + n2) * sizeof(int) : 0);
+        const size_t red = (size_t)(s.threads / 32) * 2 * sizeof(double);
+        if (s.smem < red) s.smem = red;
+        return s;
+    };
+    const int target = (int)((64 * 1024) / c);  // elements of a one-axis tile (64 KB)
+    const long long plane = (long long)n1 * n2;
+    P->fused_xy = (size_t)(plane + n1 + n2) * c <= (size_t)std::min(smax, 160 * 1024);
+    if (P->fused_xy) P->s_xy = mk_shape(1, n1, n2, 3);
+    {
+        const int ty = largest_divisor_at_most(n1, std::max(1, target / n2));
+        P->s_x = mk_shape(1, ty, n2, 1);
+        const int tx = largest_divisor_at_most(n2, std::max(1, std::min(32, target / n1)));
+        P->s_y = mk_shape(1, n1, tx, 2);
+    }
+    {
+        const int tx = largest_divisor_at_most(n2, std::max(1, std::min(32, target / n0)));
+        const int ty = largest_divisor_at_most(n1, std::max(1, target / (n0 * tx)));
+        P->s_z = mk_shape(n0, ty, tx, 4);
+    }
+    for (const PassShape* s : {&P->s_xy, &P->s_x, &P->s_y, &P->s_z}) {
+        if (s == &P->s_xy && !P->fused_xy) continue;
+        if (s->smem > (size_t)smax) return fail(ACE_ERR_GRID_TOO_SMALL, "grid axis too long for one thread block tile");
+    }
+    P->ntiles_last = P->fused_xy ? n0 : n0 * (n1 / P->s_x.ty);
+    return ACE_OK;
+}
+
+template <typename R>
+PassArgs base_args(const ace_plan* P) {
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n0 = P->n[0];
+    a.n1 = P->n[1];
+    a.n2 = P->n[2];
+    a.pz = P->ax[0];
+    a.py = P->ax[1];
+    a.px = P->ax[2];
+    a.twz = P->d_tw[0];
+    a.twy = P->d_tw[1];
+    a.twx = P->d_tw[2];
+    a.src_tstride = a.dst_tstride = P->N;
+    a.src = a.dst = P->d_spec;
+    for (int i = 0; i < 9; ++i) a.b[i] = P->b[i];
+    a.kscale = 1.0 / (double)P->N;
+    for (int d = 0; d < 3; ++d) a.freq[d] = P->d_freq[d];
+    return a;
+}
+
+#define ACE_CKL(expr)                                                                                         \
+    do {                                                                                                      \
+        cudaError_t e_ = (expr);                                                                              \
+        if (e_ != cudaSuccess) return fail(ACE_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+// psi (half sphere) -> real-space functions out[a] (quads (a, a, c, c)).
+template <typename R>
+int run_to_real(ace_plan* P, const cx<R>* psi, const Quad* dq, int ntrans, R* out, cudaStream_t st) {
+    PassArgs a = base_args<R>(P);
+    a.quads = dq;
+    a.accl = out;
+    a.scale = 1.0 / std::sqrt(P->omega);
+    cx<R>* spec = (cx<R>*)P->d_spec;
+    for (int t0 = 0; t0 < ntrans; t0 += P->batch) {
+        const int nb = std::min(P->batch, ntrans - t0);
+        a.t0 = t0;
+        ACE_CK(cudaMemsetAsync(spec, 0, (size_t)nb * P->N * sizeof(cx<R>), st));
+        ACE_CKL(launch_scatter<R>(psi, dq, t0, nb, P->npw, P->d_ip, P->d_in, spec, P->N, st));
+        ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_NONE, +1, nb, st));
+        if (P->fused_xy) {
+            ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_LOAD, EPI_SPLIT, MID_NONE, +1, nb, st));
+        } else {
+            ACE_CKL(launch_pass<R>(a, P->s_y, PRO_LOAD, EPI_STORE, MID_NONE, +1, nb, st));
+            ACE_CKL(launch_pass<R>(a, P->s_x, PRO_LOAD, EPI_SPLIT, MID_NONE, +1, nb, st));
+        }
+    }
+    return ACE_OK;
+}
+
+// real-space accumulators acc[a] -> half-sphere coefficients out[a] * s.
+template <typename R>
+int run_to_recip(ace_plan* P, const R* acc, const Quad* dq, int ntrans, double s, cx<R>* out, cudaStream_t st) {
+    PassArgs a = base_args<R>(P);
+    a.quads = dq;
+    a.fl = acc;
+    cx<R>* spec = (cx<R>*)P->d_spec;
+    for (int t0 = 0; t0 < ntrans; t0 += P->batch) {
+        const int nb = std::min(P->batch, ntrans - t0);
+        a.t0 = t0;
+        if (P->fused_xy) {
+            ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_PACK2, EPI_STORE, MID_NONE, -1, nb, st));
+        } else {
+            ACE_CKL(launch_pass<R>(a, P->s_x, PRO_PACK2, EPI_STORE, MID_NONE, -1, nb, st));
+            ACE_CKL(launch_pass<R>(a, P->s_y, PRO_LOAD, EPI_STORE, MID_NONE, -1, nb, st));
+        }
+        ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_NONE, -1, nb, st));
+        ACE_CKL(launch_gather<R>(spec, dq, t0, nb, P->npw, P->d_ip, P->d_in, P->N, s, out, st));
+    }
+    return ACE_OK;
+}
+
+// Pair Poisson solves with fused exchange accumulation (Eq. 2-4).
+template <typename R>
+int run_pairs(ace_plan* P, const R* fl, const R* fr, R* accl, R* accr, int symmetric, const Quad* dq, int ntrans,
+              double* e_part, cudaStream_t st) {
+    PassArgs a = base_args<R>(P);
+    a.fl = fl;
+    a.fr = fr;
+    a.accl = accl;
+    a.accr = accr;
+    a.symmetric = symmetric;
+    a.quads = dq;
+    a.e_part = e_part;
+    for (int t0 = 0; t0 < ntrans; t0 += P->batch) {
+        const int nb = std::min(P->batch, ntrans - t0);
+        a.t0 = t0;
+        if (P->fused_xy) {
+            ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_PAIR, EPI_STORE, MID_NONE, -1, nb, st));
+            ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_COULOMB, -1, nb, st));
+            ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_LOAD, EPI_ACCUM, MID_NONE, +1, nb, st));
+        } else {
+            ACE_CKL(launch_pass<R>(a, P->s_x, PRO_PAIR, EPI_STORE, MID_NONE, -1, nb, st));
+            ACE_CKL(launch_pass<R>(a, P->s_y, PRO_LOAD, EPI_STORE, MID_NONE, -1, nb, st));
+            ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_COULOMB, -1, nb, st));
+            ACE_CKL(launch_pass<R>(a, P->s_y, PRO_LOAD, EPI_STORE, MID_NONE, +1, nb, st));
+            ACE_CKL(launch_pass<R>(a, P->s_x, PRO_LOAD, EPI_ACCUM, MID_NONE, +1, nb, st));
+        }
+    }
+    return ACE_OK;
+}
+
+// G[i][j] = <A_i|B_j> (Gamma inner product), double [m][n].
+template <typename R>
+int gram(ace_plan* P, const cx<R>* A, int m, const cx<R>* B, int n, double* G, cudaStream_t st) {
+    const long long K = 2LL * P->npw;
+    const int tiles = ((m + 63) / 64) * ((n + 63) / 64);
+    int nchunk = std::max(1, (2 * 152 + tiles - 1) / tiles);
+    nchunk = (int)std::min<long long>(nchunk, std::max<long long>(1, K / 256));
+    ACE_TRY(grow(&P->d_part, &P->part_cap, (size_t)nchunk * m * n));
+    ACE_CKL(launch_gram_partial<R>((const R*)A, (const R*)B, m, n, K, nchunk, P->d_part, st));
+    ACE_CKL(launch_gram_finish<R>(P->d_part, nchunk, (const R*)A, (const R*)B, m, n, K, G, n, st));
+    return ACE_OK;
+}
+
+std::vector<Quad> orbital_quads(int n) {
+    std::vector<Quad> q;
+    for (int a = 0; a < n; a += 2) q.push_back(Quad{a, a, a + 1 < n ? a + 1 : -1, a + 1 < n ? a + 1 : -1});
+    return q;
+}
+
+void pack_pairs(const std::vector<int>& pa, const std::vector<int>& pb, std::vector<Quad>& q) {
+    for (size_t p = 0; p < pa.size(); p += 2) {
+        Quad x{pa[p], pb[p], -1, -1};
+        if (p + 1 < pa.size()) {
+            x.c = pa[p + 1];
+            x.d = pb[p + 1];
+        }
+        q.push_back(x);
+    }
+}
+
+template <typename R>
+int check_gamma(ace_plan* P, const void* psi, int n, cudaStream_t st) {
+    std::vector<cx<R>> c0(n);
+    ACE_CK(cudaMemcpy2DAsync(c0.data(), sizeof(cx<R>), psi, (size_t)P->npw * sizeof(cx<R>), sizeof(cx<R>), n,
+                             cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i)
+        if (std::fabs((double)c0[i].im) > 1e-6)
+            return fail(ACE_ERR_INVALID_ARG, "Im c(G=0) of vector " + std::to_string(i) + " is not zero");
+    return ACE_OK;
+}
+
+int upload_quads(ace_plan* P, const std::vector<Quad>& q, cudaStream_t st) {
+    ACE_TRY(grow(&P->d_quads, &P->quads_cap, q.size()));
+    ACE_CK(cudaMemcpyAsync(P->d_quads, q.data(), q.size() * sizeof(Quad), cudaMemcpyHostToDevice, st));
+    return ACE_OK;
+}
+
+template <typename R>
+int build_impl(ace_plan* P, const void* psi_G, int n_occ, double alpha, const int32_t* rp, const int32_t* col,
+               void* xi, double* E_x, cudaStream_t st) {
+    ACE_TRY(check_gamma<R>(P, psi_G, n_occ, st));
+    std::vector<int> pa, pb;
+    if (rp) {
+        if (rp[0] != 0) return fail(ACE_ERR_INVALID_ARG, "pair_row_ptr[0] must be 0");
+        for (int i = 0; i < n_occ; ++i) {
+            if (rp[i + 1] < rp[i]) return fail(ACE_ERR_INVALID_ARG, "pair_row_ptr not monotone");
+            for (int t = rp[i]; t < rp[i + 1]; ++t) {
+                if (col[t] < i || col[t] >= n_occ) return fail(ACE_ERR_INVALID_ARG, "pair column out of range");
+                pa.push_back(i);
+                pb.push_back(col[t]);
+            }
+        }
+    } else {
+        for (int i = 0; i < n_occ; ++i)
+            for (int j = i; j < n_occ; ++j) {
+                pa.push_back(i);
+                pb.push_back(j);
+            }
+    }
+    std::vector<Quad> oq = orbital_quads(n_occ), q = oq;
+    const int n_orb_t = (int)oq.size();
+    pack_pairs(pa, pb, q);
+    const int n_pair_t = (int)q.size() - n_orb_t;
+    ACE_TRY(upload_quads(P, q, st));
+    const Quad* d_oq = P->d_quads;
+    const Quad* d_pq = P->d_quads + n_orb_t;
+
+    const cx<R>* psi = (const cx<R>*)psi_G;
+    R* phi = (R*)P->d_phi;
+    R* acc = (R*)P->d_acc;
+    ACE_TRY(run_to_real<R>(P, psi, d_oq, n_orb_t, phi, st));
+    ACE_CK(cudaMemsetAsync(acc, 0, (size_t)n_occ * P->N * sizeof(R), st));
+    ACE_TRY(grow(&P->d_epart, &P->epart_cap, (size_t)std::max(n_pair_t, 1) * P->ntiles_last * 2));
+    ACE_TRY(run_pairs<R>(P, phi, phi, acc, acc, 1, d_pq, n_pair_t, P->d_epart, st));
+    ACE_CKL(launch_energy_reduce(P->d_epart, d_pq, n_pair_t, P->ntiles_last, -alpha * P->omega / (double)P->N,
+                                 P->d_E, st));
+    cx<R>* WG = (cx<R>*)P->d_WG;
+    ACE_TRY(run_to_recip<R>(P, acc, d_oq, n_orb_t, -alpha * std::sqrt(P->omega) / (double)P->N, WG, st));
+    ACE_TRY(gram<R>(P, psi, n_occ, WG, n_occ, P->d_M, st));
+    ACE_CKL(launch_neg_cholesky_inverse(P->d_M, n_occ, P->d_L, P->d_Linv, P->d_status, st));
+    ACE_CKL(launch_gemm_nn<R>(P->d_Linv, n_occ, n_occ, (const R*)WG, 2LL * P->npw, 1.0, (R*)xi, true, st));
+    int status = 0;
+    double E = 0;
+    ACE_CK(cudaMemcpyAsync(&status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaMemcpyAsync(&E, P->d_E, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaStreamSynchronize(st));
+    P->last_n_occ = n_occ;
+    if (E_x) *E_x = E;
+    if (status) return fail(ACE_ERR_NOT_POSDEF, "-M is not positive definite (dependent or zero orbitals)");
+    return ACE_OK;
+}
+
+template <typename R>
+int hfx_impl(ace_plan* P, const void* psi_occ, int n_occ, double alpha, const void* psi, int T, void* out,
+             cudaStream_t st) {
+    ACE_TRY(check_gamma<R>(P, psi_occ, n_occ, st));
+    ACE_TRY(check_gamma<R>(P, psi, T, st));
+    std::vector<Quad> oq = orbital_quads(n_occ), tq = orbital_quads(T), q = oq;
+    q.insert(q.end(), tq.begin(), tq.end());
+    std::vector<int> pa, pb;
+    for (int t = 0; t < T; ++t)
+        for (int j = 0; j < n_occ; ++j) {
+            pa.push_back(t);
+            pb.push_back(j);
+        }
+    pack_pairs(pa, pb, q);
+    const int no = (int)oq.size(), nt = (int)tq.size(), np = (int)q.size() - no - nt;
+    ACE_TRY(upload_quads(P, q, st));
+    size_t tcap_elems = P->t_cap;
+    void* tphi = P->d_tphi;
+    if ((size_t)T * P->N > tcap_elems) {
+        if (P->d_tphi) cudaFree(P->d_tphi);
+        if (P->d_tacc) cudaFree(P->d_tacc);
+        P->d_tphi = P->d_tacc = nullptr;
+        P->t_cap = 0;
+        ACE_TRY(dalloc(&P->d_tphi, (size_t)T * P->N * sizeof(R)));
+        ACE_TRY(dalloc(&P->d_tacc, (size_t)T * P->N * sizeof(R)));
+        P->t_cap = (size_t)T * P->N;
+        tphi = P->d_tphi;
+    }
+    R* phi = (R*)P->d_phi;
+    ACE_TRY(run_to_real<R>(P, (const cx<R>*)psi_occ, P->d_quads, no, phi, st));
+    ACE_TRY(run_to_real<R>(P, (const cx<R>*)psi, P->d_quads + no, nt, (R*)tphi, st));
+    ACE_CK(cudaMemsetAsync(P->d_tacc, 0, (size_t)T * P->N * sizeof(R), st));
+    ACE_TRY(run_pairs<R>(P, (const R*)tphi, phi, (R*)P->d_tacc, nullptr, 0, P->d_quads + no + nt, np, nullptr, st));
+    ACE_TRY(run_to_recip<R>(P, (const R*)P->d_tacc, P->d_quads + no, nt, -alpha * std::sqrt(P->omega) / (double)P->N,
+                            (cx<R>*)out, st));
+    ACE_CK(cudaGetLastError());
+    return ACE_OK;
+}
+
+template <typename R>
+int apply_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, void* out, cudaStream_t st) {
+    ACE_TRY(grow(&P->d_C, &P->C_cap, (size_t)T * n_occ));
+    ACE_TRY(gram<R>(P, (const cx<R>*)psi, T, (const cx<R>*)xi, n_occ, P->d_C, st));  // C[t][k] = <psi_t|xi_k>
+    ACE_CKL(launch_gemm_nn<R>(P->d_C, T, n_occ, (const R*)xi, 2LL * P->npw, -1.0, (R*)out, false, st));
+    return ACE_OK;
+}
+
+void free_plan(ace_plan* P) {
+    void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
+                    P->d_WG, P->d_M, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_part, P->d_quads,
+                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete P;
+}
+
+template <typename R>
+int create_impl(ace_plan* P, const ace_opts* opts) {
+    P->esz = sizeof(R);
+    for (int d = 0; d < 3; ++d) {
+        if (!make_axis_plan(P->n[d], P->ax[d]))
+            return fail(ACE_ERR_GRID_TOO_SMALL, "grid extents must be products of 2, 3 and 5");
+        std::vector<cx<R>> tw(P->n[d]);
+        for (int j = 0; j < P->n[d]; ++j) {
+            tw[j].re = (R)std::cos(2 * M_PI * j / P->n[d]);
+            tw[j].im = (R)-std::sin(2 * M_PI * j / P->n[d]);
+        }
+        ACE_TRY(dalloc(&P->d_tw[d], tw.size() * sizeof(cx<R>)));
+        ACE_CK(cudaMemcpy(P->d_tw[d], tw.data(), tw.size() * sizeof(cx<R>), cudaMemcpyHostToDevice));
+    }
+    // digit-reversed positions of every frequency, per axis, and their inverse
+    std::vector<int> pos[3];
+    for (int d = 0; d < 3; ++d) {
+        pos[d].resize(P->n[d]);
+        std::vector<int> fr(P->n[d]);
+        for (int k = 0; k < P->n[d]; ++k) {
+            pos[d][k] = digit_reversed_position(P->ax[d], k);
+            fr[pos[d][k]] = k;
+        }
+        ACE_TRY(dalloc((void**)&P->d_freq[d], P->n[d] * sizeof(int)));
+        ACE_CK(cudaMemcpy(P->d_freq[d], fr.data(), P->n[d] * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    std::vector<int> ip(P->npw), in(P->npw);
+    for (int p = 0; p < P->npw; ++p) {
+        int m[3], mn[3];
+        for (int d = 0; d < 3; ++d) {
+            const int v = P->miller[3 * p + d];
+            m[d] = pos[d][((v % P->n[d]) + P->n[d]) % P->n[d]];
+            mn[d] = pos[d][((-v % P->n[d]) + P->n[d]) % P->n[d]];
+        }
+        ip[p] = (m[0] * P->n[1] + m[1]) * P->n[2] + m[2];
+        in[p] = (mn[0] * P->n[1] + mn[1]) * P->n[2] + mn[2];
+    }
+    ACE_TRY(dalloc((void**)&P->d_ip, P->npw * sizeof(int)));
+    ACE_TRY(dalloc((void**)&P->d_in, P->npw * sizeof(int)));
+    ACE_CK(cudaMemcpy(P->d_ip, ip.data(), P->npw * sizeof(int), cudaMemcpyHostToDevice));
+    ACE_CK(cudaMemcpy(P->d_in, in.data(), P->npw * sizeof(int), cudaMemcpyHostToDevice));
+    ACE_TRY(setup_shapes<R>(P));
+    int ntrans_min = (P->n_occ_max + 1) / 2;
+    int batch = opts && opts->pair_batch > 0 ? opts->pair_batch
+                                             : (int)std::max<long long>(1, (512LL << 20) / (P->N * (long long)sizeof(cx<R>)));
+    batch = std::min(batch, 64);
+    (void)ntrans_min;
+    P->batch = std::max(1, batch);
+    const size_t N = (size_t)P->N;
+    ACE_TRY(dalloc(&P->d_phi, (size_t)P->n_occ_max * N * sizeof(R)));
+    ACE_TRY(dalloc(&P->d_acc, (size_t)P->n_occ_max * N * sizeof(R)));
+    ACE_TRY(dalloc(&P->d_spec, (size_t)P->batch * N * sizeof(cx<R>)));
+    ACE_TRY(dalloc(&P->d_WG, (size_t)P->n_occ_max * P->npw * sizeof(cx<R>)));
+    const size_t nn = (size_t)P->n_occ_max * P->n_occ_max;
+    ACE_TRY(dalloc((void**)&P->d_M, nn * sizeof(double)));
+    ACE_TRY(dalloc((void**)&P->d_L, nn * sizeof(double)));
+    ACE_TRY(dalloc((void**)&P->d_Linv, nn * sizeof(double)));
+    ACE_TRY(dalloc((void**)&P->d_E, sizeof(double)));
+    ACE_TRY(dalloc((void**)&P->d_status, sizeof(int)));
+    return ACE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ace_plan_create(ace_plan** plan, const int grid[3], const double cell[9], double ecut_ry, int n_occ_max,
+                    int precision, const ace_opts* opts) {
+    if (!plan || !grid || !cell) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    *plan = nullptr;
+    if (!(ecut_ry > 0) || n_occ_max < 1 || (precision != ACE_FP64 && precision != ACE_MIXED))
+        return fail(ACE_ERR_INVALID_ARG, "ecut must be > 0, n_occ_max >= 1, precision ACE_FP64 or ACE_MIXED");
+    for (int d = 0; d < 3; ++d)
+        if (grid[d] < 1 || grid[d] > 4096) return fail(ACE_ERR_INVALID_ARG, "grid extent out of range");
+    ace_plan* P = new ace_plan();
+    cudaGetDevice(&P->dev);
+    P->prec = precision;
+    for (int d = 0; d < 3; ++d) P->n[d] = grid[d];
+    P->N = (long long)grid[0] * grid[1] * grid[2];
+    std::memcpy(P->cell, cell, sizeof(P->cell));
+    P->ecut = ecut_ry;
+    P->n_occ_max = n_occ_max;
+    if (!reciprocal(cell, P->b, &P->omega)) {
+        delete P;
+        return fail(ACE_ERR_INVALID_ARG, "singular cell");
+    }
+    half_sphere(P->cell, P->b, ecut_ry, P->miller);
+    P->npw = (int)(P->miller.size() / 3);
+    for (int p = 0; p < P->npw; ++p)
+        for (int d = 0; d < 3; ++d)
+            if (2 * std::abs(P->miller[3 * p + d]) + 1 > P->n[d]) {
+                delete P;
+                return fail(ACE_ERR_GRID_TOO_SMALL, "grid too small for the cutoff sphere");
+            }
+    int st = precision == ACE_FP64 ? create_impl<double>(P, opts) : create_impl<float>(P, opts);
+    if (st != ACE_OK) {
+        free_plan(P);
+        return st;
+    }
+    *plan = P;
+    return ACE_OK;
+}
+
+void ace_plan_destroy(ace_plan* plan) {
+    if (!plan) return;
+    DeviceGuard g(plan->dev);
+    free_plan(plan);
+}
+
+int ace_gvec(const ace_plan* plan, int* n_pw_half, int32_t* miller) {
+    if (!plan || !n_pw_half) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    *n_pw_half = plan->npw;
+    if (miller) std::memcpy(miller, plan->miller.data(), plan->miller.size() * sizeof(int32_t));
+    return ACE_OK;
+}
+
+int ace_build(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const int32_t* pair_row_ptr,
+              const int32_t* pair_col, void* xi, double* E_x, void* stream) {
+    if (!plan || !psi_G || !xi) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (n_occ < 1 || n_occ > plan->n_occ_max) return fail(ACE_ERR_INVALID_ARG, "n_occ out of range");
+    if ((pair_row_ptr == nullptr) != (pair_col == nullptr))
+        return fail(ACE_ERR_INVALID_ARG, "pair_row_ptr and pair_col must both be set or both be NULL");
+    DeviceGuard g(plan->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->prec == ACE_FP64 ? build_impl<double>(plan, psi_G, n_occ, alpha, pair_row_ptr, pair_col, xi, E_x, st)
+                                  : build_impl<float>(plan, psi_G, n_occ, alpha, pair_row_ptr, pair_col, xi, E_x, st);
+}
+
+int ace_apply(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T, void* Kpsi, void* stream) {
+    if (!plan || !xi || (T > 0 && (!psi || !Kpsi))) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (n_occ < 1 || T < 0) return fail(ACE_ERR_INVALID_ARG, "n_occ must be >= 1 and T >= 0");
+    if (T == 0) return ACE_OK;
+    DeviceGuard g(plan->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->prec == ACE_FP64 ? apply_impl<double>(plan, xi, n_occ, psi, T, Kpsi, st)
+                                  : apply_impl<float>(plan, xi, n_occ, psi, T, Kpsi, st);
+}
+
+int hfx_apply_exact(ace_plan* plan, const void* psi_occ, int n_occ, double alpha, const void* psi, int T,
+                    void* Vx_psi, void* stream) {
+    if (!plan || !psi_occ || (T > 0 && (!psi || !Vx_psi))) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (n_occ < 1 || n_occ > plan->n_occ_max || T < 0) return fail(ACE_ERR_INVALID_ARG, "n_occ or T out of range");
+    if (T == 0) return ACE_OK;
+    DeviceGuard g(plan->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->prec == ACE_FP64 ? hfx_impl<double>(plan, psi_occ, n_occ, alpha, psi, T, Vx_psi, st)
+                                  : hfx_impl<float>(plan, psi_occ, n_occ, alpha, psi, T, Vx_psi, st);
+}
+
+int ace_last_intermediates(ace_plan* plan, void* W_G, double* M, void* stream) {
+    if (!plan) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (plan->last_n_occ == 0) return fail(ACE_ERR_INVALID_ARG, "no ace_build has run on this plan");
+    DeviceGuard g(plan->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = plan->last_n_occ;
+    if (W_G)
+        ACE_CK(cudaMemcpyAsync(W_G, plan->d_WG, (size_t)n * plan->npw * 2 * plan->esz, cudaMemcpyDeviceToDevice, st));
+    if (M) ACE_CK(cudaMemcpyAsync(M, plan->d_M, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaStreamSynchronize(st));
+    return ACE_OK;
+}
+
+int ace_last_error(char* buf, int len) {
+    const int n = (int)g_err.size();
+    if (buf && len > 0) {
+        std::strncpy(buf, g_err.c_str(), (size_t)len - 1);
+        buf[len - 1] = '\0';
+    }
+    return n;
+}
+
+}  // extern "C"

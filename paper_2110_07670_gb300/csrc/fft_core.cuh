@@ -1,0 +1,279 @@
+// fft_core.cuh -- complex arithmetic, radix-2/3/4/5/8 DFT codelets and the
+// in-place mixed-radix stages of the library's batched 1D transforms.
+//
+// The pair Poisson solves of the exchange operator (arXiv:2110.07670 Section
+// 2.1, Eq. 3, evaluated in reciprocal space as the paper describes) are 3D
+// FFTs; every pass kernel of this library is built from the stages below.
+//
+// Forward transform, decimation in frequency, in place.  With radices
+// r_1 .. r_m (product n), stage i works on blocks of length L_i = n / (r_1 ..
+// r_{i-1}) with m_i = L_i / r_i.  Butterfly (block beta, j < m_i) reads the
+// r_i elements at beta L_i + j + m_i q, forms
+//     y_s = w_{L_i}^{j s} sum_q x_q w_{r_i}^{q s},   w_L = exp(-2 pi i / L),
+// and writes y_s back to beta L_i + j + m_i s.  Frequency k with mixed-radix
+// digits k = s_1 + r_1 (s_2 + r_2 (s_3 + ...)) ends at position
+//     pos(k) = s_1 n / r_1 + s_2 n / (r_1 r_2) + ... + s_m.
+// Because the DFT matrix is symmetric, the inverse-direction transform of the
+// digit-reversed data is the product of the transposed stages in reverse
+// order: each stage multiplies by the conjugate twiddles first and then runs
+// the conjugate butterfly on the same positions, and the result comes out in
+// natural order.  Every thread writes back exactly the positions it read, so a
+// stage needs one barrier and no register staging of other threads' data.
+#pragma once
+
+#if defined(__CUDACC__)
+#define ACE_HD __host__ __device__ __forceinline__
+#else
+#define ACE_HD inline
+#endif
+
+namespace ace {
+
+template <typename R>
+struct alignas(2 * sizeof(R)) cx {
+    R re, im;
+};
+
+template <typename R>
+ACE_HD cx<R> mk(R a, R b) {
+    cx<R> c;
+    c.re = a;
+    c.im = b;
+    return c;
+}
+template <typename R>
+ACE_HD cx<R> operator+(cx<R> a, cx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename R>
+ACE_HD cx<R> operator-(cx<R> a, cx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename R>
+ACE_HD cx<R> cmul(cx<R> a, cx<R> b) { return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+template <typename R>
+ACE_HD cx<R> scale(cx<R> a, R s) { return mk(a.re * s, a.im * s); }
+// multiply by sgn * i  (sgn = +-1)
+template <int SGN, typename R>
+ACE_HD cx<R> mul_i(cx<R> a) { return SGN > 0 ? mk(-a.im, a.re) : mk(a.im, -a.re); }
+
+// ------------------------------------------------------------------ codelets
+// y_s = sum_q x_q w^{qs}, w = exp(SGN 2 pi i / RAD), in place on v[0..RAD).
+
+template <int RAD, int SGN, typename R>
+struct Dft;
+
+template <int SGN, typename R>
+struct Dft<2, SGN, R> {
+    static ACE_HD void run(cx<R>* v) {
+        cx<R> a = v[0], b = v[1];
+        v[0] = a + b;
+        v[1] = a - b;
+    }
+};
+
+template <int SGN, typename R>
+struct Dft<3, SGN, R> {
+    // w = -1/2 + SGN i sqrt(3)/2
+    static ACE_HD void run(cx<R>* v) {
+        const R h = R(0.86602540378443864676);  // sqrt(3)/2
+        cx<R> s = v[1] + v[2], d = v[1] - v[2];
+        cx<R> m = v[0] - scale(s, R(0.5));
+        cx<R> t = mul_i<SGN>(scale(d, h));
+        v[0] = v[0] + s;
+        v[1] = m + t;
+        v[2] = m - t;
+    }
+};
+
+template <int SGN, typename R>
+struct Dft<4, SGN, R> {
+    static ACE_HD void run(cx<R>* v) {
+        cx<R> a = v[0] + v[2], b = v[0] - v[2];
+        cx<R> c = v[1] + v[3], d = mul_i<SGN>(v[1] - v[3]);
+        v[0] = a + c;
+        v[2] = a - c;
+        v[1] = b + d;
+        v[3] = b - d;
+    }
+};
+
+template <int SGN, typename R>
+struct Dft<5, SGN, R> {
+    // c1 = cos(2pi/5), c2 = cos(4pi/5), s1 = sin(2pi/5), s2 = sin(4pi/5)
+    static ACE_HD void run(cx<R>* v) {
+        const R c1 = R(0.30901699437494742410), c2 = R(-0.80901699437494742410);
+        const R s1 = R(0.95105651629515357212), s2 = R(0.58778525229247312917);
+        cx<R> a1 = v[1] + v[4], b1 = v[1] - v[4];
+        cx<R> a2 = v[2] + v[3], b2 = v[2] - v[3];
+        cx<R> x0 = v[0];
+        cx<R> p1 = x0 + scale(a1, c1) + scale(a2, c2);
+        cx<R> p2 = x0 + scale(a1, c2) + scale(a2, c1);
+        cx<R> q1 = mul_i<SGN>(scale(b1, s1) + scale(b2, s2));
+        cx<R> q2 = mul_i<SGN>(scale(b1, s2) - scale(b2, s1));
+        v[0] = x0 + a1 + a2;
+        v[1] = p1 + q1;
+        v[4] = p1 - q1;
+        v[2] = p2 + q2;
+        v[3] = p2 - q2;
+    }
+};
+
+template <int SGN, typename R>
+struct Dft<8, SGN, R> {
+    // two radix-4 halves (even / odd inputs) joined by w8^k, k = 0..3
+    static ACE_HD void run(cx<R>* v) {
+        const R r = R(0.70710678118654752440);  // sqrt(2)/2
+        cx<R> e[4] = {v[0], v[2], v[4], v[6]};
+        cx<R> o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4, SGN, R>::run(e);
+        Dft<4, SGN, R>::run(o);
+        // w8 = exp(SGN i pi/4) = r (1 + SGN i)
+        cx<R> o1 = scale(o[1] + mul_i<SGN>(o[1]), r);
+        cx<R> o2 = mul_i<SGN>(o[2]);
+        cx<R> o3 = scale(mul_i<SGN>(o[3]) - o[3], r);  // w8^3 = r(-1 + SGN i)
+        v[0] = e[0] + o[0];
+        v[4] = e[0] - o[0];
+        v[1] = e[1] + o1;
+        v[5] = e[1] - o1;
+        v[2] = e[2] + o2;
+        v[6] = e[2] - o2;
+        v[3] = e[3] + o3;
+        v[7] = e[3] - o3;
+    }
+};
+
+// ------------------------------------------------------------------- plans
+
+constexpr int kMaxStages = 12;
+
+struct AxisPlan {
+    int n;  // line length
+    int nstages;
+    int radix[kMaxStages];  // radices in forward stage order
+};
+
+// Geometry of a set of lines inside a shared-memory tile.
+struct Lines {
+    int n;        // length
+    int nlines;   // number of lines
+    int estride;  // distance between consecutive elements of a line
+    int lstride;  // distance between consecutive lines
+};
+
+// Butterfly b of a stage -> (line, index within the line's butterflies).
+// When a line is contiguous, consecutive b walk along it; otherwise they
+// walk across lines, so a warp touches consecutive addresses either way.
+ACE_HD void butterfly_coords(const Lines& L, int nb, int b, int& line, int& i) {
+    if (L.estride == 1) {
+        line = b / nb;
+        i = b - line * nb;
+    } else {
+        i = b / L.nlines;
+        line = b - i * L.nlines;
+    }
+}
+
+// One butterfly of stage radix RAD on blocks of length Lb (= m RAD).
+// tw[t] = exp(-2 pi i t / n), t < n.  SGN < 0: forward DIF stage (butterfly
+// then twiddle).  SGN > 0: transposed conjugate stage (twiddle then butterfly).
+template <int RAD, int SGN, typename R>
+ACE_HD void stage_butterfly(cx<R>* buf, const Lines& L, const cx<R>* tw, int Lb, int b) {
+    const int m = Lb / RAD;
+    const int nb = L.n / RAD;
+    int line, i;
+    butterfly_coords(L, nb, b, line, i);
+    const int beta = i / m, j = i - beta * m;
+    cx<R>* base = buf + (long long)line * L.lstride + (long long)(beta * Lb + j) * L.estride;
+    const int tstep = (L.n / Lb) * j;  // twiddle index per unit of s: (n / Lb) j
+    cx<R> u[RAD];
+#pragma unroll
+    for (int q = 0; q < RAD; ++q) u[q] = base[(long long)q * m * L.estride];
+    if (SGN > 0) {
+#pragma unroll
+        for (int q = 1; q < RAD; ++q)
+            if (j > 0) {
+                cx<R> w = tw[q * tstep];
+                w.im = -w.im;
+                u[q] = cmul(u[q], w);
+            }
+    }
+    Dft<RAD, SGN, R>::run(u);
+    if (SGN < 0) {
+#pragma unroll
+        for (int s = 1; s < RAD; ++s)
+            if (j > 0) u[s] = cmul(u[s], tw[s * tstep]);
+    }
+#pragma unroll
+    for (int s = 0; s < RAD; ++s) base[(long long)s * m * L.estride] = u[s];
+}
+
+#if defined(__CUDACC__)
+template <int RAD, int SGN, typename R>
+__device__ __forceinline__ void block_stage(cx<R>* buf, const Lines& L, const cx<R>* tw, int Lb) {
+    const int total = (L.n / RAD) * L.nlines;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) stage_butterfly<RAD, SGN, R>(buf, L, tw, Lb, b);
+    __syncthreads();
+}
+
+// Full 1D transform of every line of the tile by the thread block.
+// SGN < 0: natural order in, digit-reversed out.  SGN > 0: digit-reversed in,
+// natural order out.
+template <int SGN, typename R>
+__device__ __forceinline__ void block_fft(cx<R>* buf, const Lines& L, const AxisPlan& P, const cx<R>* tw) {
+    if (SGN < 0) {
+        int Lb = L.n;
+        for (int s = 0; s < P.nstages; ++s) {
+            const int r = P.radix[s];
+            switch (r) {
+                case 2: block_stage<2, SGN, R>(buf, L, tw, Lb); break;
+                case 3: block_stage<3, SGN, R>(buf, L, tw, Lb); break;
+                case 4: block_stage<4, SGN, R>(buf, L, tw, Lb); break;
+                case 5: block_stage<5, SGN, R>(buf, L, tw, Lb); break;
+                default: block_stage<8, SGN, R>(buf, L, tw, Lb); break;
+            }
+            Lb /= r;
+        }
+    } else {
+        int Lb = 1;
+        for (int s = P.nstages - 1; s >= 0; --s) {
+            const int r = P.radix[s];
+            Lb *= r;
+            switch (r) {
+                case 2: block_stage<2, SGN, R>(buf, L, tw, Lb); break;
+                case 3: block_stage<3, SGN, R>(buf, L, tw, Lb); break;
+                case 4: block_stage<4, SGN, R>(buf, L, tw, Lb); break;
+                case 5: block_stage<5, SGN, R>(buf, L, tw, Lb); break;
+                default: block_stage<8, SGN, R>(buf, L, tw, Lb); break;
+            }
+        }
+    }
+}
+#endif
+
+// Factor n into stage radices, radix 8 first, then 4, 2, 3, 5.  Returns false
+// when n has a prime factor above 5 or needs too many stages.
+inline bool make_axis_plan(int n, AxisPlan& P) {
+    P.n = n;
+    P.nstages = 0;
+    int m = n;
+    const int order[5] = {8, 4, 2, 3, 5};
+    for (int r : order) {
+        while (m % r == 0) {
+            if (P.nstages == kMaxStages) return false;
+            P.radix[P.nstages++] = r;
+            m /= r;
+        }
+    }
+    return m == 1 && n >= 1;
+}
+
+// Position of frequency k after the forward transform (see the header note).
+inline int digit_reversed_position(const AxisPlan& P, int k) {
+    int pos = 0, span = P.n;
+    for (int s = 0; s < P.nstages; ++s) {
+        const int r = P.radix[s];
+        span /= r;
+        pos += (k % r) * span;
+        k /= r;
+    }
+    return pos;
+}
+
+}  // namespace ace

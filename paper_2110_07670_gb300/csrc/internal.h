@@ -1,0 +1,113 @@
+// internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_core.cuh"
+
+namespace ace {
+
+// Prologue: how a pass fills its shared-memory tile.
+enum Prologue {
+    PRO_LOAD = 0,   // complex source box of transform t
+    PRO_PAIR = 1,   // f_a phi_b + i f_c phi_d (two pair densities, Eq. 3)
+    PRO_PACK2 = 2,  // f_a + i f_c (two real functions in one complex transform)
+};
+// Epilogue: where the transformed tile goes.
+enum Epilogue {
+    EPI_STORE = 0,  // complex destination box of transform t
+    EPI_SPLIT = 1,  // real part -> out[a], imaginary part -> out[c], times scale
+    EPI_ACCUM = 2,  // exchange accumulation W_a += v phi_b (and W_b += v f_a), pair energies
+};
+// What happens between the transforms of the z axis.
+enum Middle {
+    MID_NONE = 0,
+    MID_COULOMB = 1,  // forward z, times 4 pi / |G|^2 / N (G = 0 -> 0), inverse z
+};
+
+// Quadruple of function indices for one packed transform: (a, b) and (c, d);
+// c < 0 when the imaginary half is empty.
+struct Quad {
+    int a, b, c, d;
+};
+
+struct PassArgs {
+    int n0, n1, n2;  // box extents (z, y, x); x is contiguous
+    int tz, ty, tx;  // tile extents (divide the box extents)
+    int axes;        // 1 = x, 2 = y (needs tz == 1), 4 = z
+    AxisPlan px, py, pz;
+    const void *twx, *twy, *twz;  // exp(-2 pi i j / n) per axis, cx<R>
+    // prologue
+    const void* src;
+    long long src_tstride;  // elements between transforms
+    const void* fl;         // left functions  [*][N] real
+    const void* fr;         // right functions [*][N] real
+    const Quad* quads;      // per transform (indexed from t0)
+    int t0;
+    // epilogue
+    void* dst;
+    long long dst_tstride;
+    void* accl;  // EPI_SPLIT: real outputs; EPI_ACCUM: left accumulators
+    void* accr;  // EPI_ACCUM: right accumulators (symmetric mode)
+    int symmetric;
+    double* e_part;  // EPI_ACCUM: [transform][tile][2]
+    double scale;    // EPI_SPLIT output scale
+    // Coulomb kernel
+    double b[9];  // reciprocal vectors as rows
+    double kscale;
+    const int* freq[3];  // per axis: frequency held at each position after the forward stages
+};
+
+struct PassShape {
+    int tz, ty, tx, axes, threads;
+    size_t smem;
+};
+
+// Launch one pass over `batch` transforms (gridDim.y) of the box.
+template <typename R>
+cudaError_t launch_pass(const PassArgs& a, const PassShape& s, int pro, int epi, int mid, int sgn, int batch,
+                        cudaStream_t st);
+
+
+// ---------------------------------------------------------- other kernels
+
+// box[t] (zeroed by the caller) <- c_a(G) + i c_b(G) at +G, conj at -G
+// (idx_pos / idx_neg: box positions of +G / -G in digit-reversed order).
+template <typename R>
+cudaError_t launch_scatter(const cx<R>* psi, const Quad* quads, int t0, int batch, int npw, const int* idx_pos,
+                           const int* idx_neg, cx<R>* box, long long N, cudaStream_t st);
+// out_a(G) = s (Z(G) + Z(-G)^*) / 2, out_c(G) = s (Z(G) - Z(-G)^*) / (2i) on the half sphere.
+template <typename R>
+cudaError_t launch_gather(const cx<R>* box, const Quad* quads, int t0, int batch, int npw, const int* idx_pos,
+                          const int* idx_neg, long long N, double s, cx<R>* out, cudaStream_t st);
+
+// Partial Gamma Gram products: P[chunk][i][j] = sum_{k in chunk} A[i][k] B[j][k]
+// over the real views A [m][K], B [n][K] (K = 2 n_pw_half), double partials.
+template <typename R>
+cudaError_t launch_gram_partial(const R* A, const R* B, int m, int n, long long K, int nchunk, double* P,
+                                cudaStream_t st);
+// G[i][j] = 2 sum_c P[c][i][j] - (A_i0 B_j0 + A_i1 B_j1)   (G = 0 counted once)
+template <typename R>
+cudaError_t launch_gram_finish(const double* P, int nchunk, const R* A, const R* B, int m, int n, long long K,
+                               double* G, int ldg, cudaStream_t st);
+
+// out[i][c] = alpha sum_k A[i][k] B[k][c]  (A double [m][k], B R [k][ncols], out R);
+// fp64_math: products and sums in double, else in R over 16-wide slices.
+template <typename R>
+cudaError_t launch_gemm_nn(const double* A, int m, int k, const R* B, long long ncols, double alpha, R* out,
+                           bool fp64_math, cudaStream_t st);
+
+// Cholesky of -M and the inverse of its factor, in double, one thread block.
+// status: 0 ok, 1 not positive definite.
+cudaError_t launch_neg_cholesky_inverse(const double* M, int n, double* L, double* Linv, int* status,
+                                        cudaStream_t st);
+
+// E = -alpha * wscale * sum_t sum_tile (w1 e1 + w2 e2), deterministic order.
+cudaError_t launch_energy_reduce(const double* e_part, const Quad* quads, int ntrans, int ntiles, double coef,
+                                 double* E, cudaStream_t st);
+
+template <typename R>
+cudaError_t launch_fill_zero(R* p, long long n, cudaStream_t st);
+
+}  // namespace ace

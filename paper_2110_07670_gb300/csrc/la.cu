@@ -1,0 +1,327 @@
+// la.cu -- sphere scatter/gather, Gamma-point Gram products, the dense
+// products of the ACE construction and apply, the FP64 Cholesky, and the
+// exchange-energy reduction (arXiv:2110.07670 Section 2.2 and Eq. 4-5).
+#include "internal.h"
+
+namespace ace {
+
+namespace {
+
+// ------------------------------------------------------------ scatter/gather
+
+template <typename R>
+__global__ void scatter_kernel(const cx<R>* __restrict__ psi, const Quad* __restrict__ quads, int t0, int npw,
+                               const int* __restrict__ ip, const int* __restrict__ in, cx<R>* __restrict__ box,
+                               long long N) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    if (p >= npw) return;
+    const Quad q = quads[t0 + t];
+    const cx<R> ca = psi[(long long)q.a * npw + p];
+    const cx<R> cb = q.c >= 0 ? psi[(long long)q.c * npw + p] : mk(R(0), R(0));
+    cx<R>* b = box + (long long)t * N;
+    // Z(G) = c_a + i c_b ; Z(-G) = c_a^* + i c_b^*
+    b[ip[p]] = mk(ca.re - cb.im, ca.im + cb.re);
+    if (in[p] != ip[p]) b[in[p]] = mk(ca.re + cb.im, cb.re - ca.im);
+}
+
+template <typename R>
+__global__ void gather_kernel(const cx<R>* __restrict__ box, const Quad* __restrict__ quads, int t0, int npw,
+                              const int* __restrict__ ip, const int* __restrict__ in, long long N, R s,
+                              cx<R>* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    if (p >= npw) return;
+    const Quad q = quads[t0 + t];
+    const cx<R>* b = box + (long long)t * N;
+    const cx<R> z = b[ip[p]], zm = b[in[p]];
+    const R h = R(0.5) * s;
+    // out_a = s (Z + Zm^*)/2 ; out_c = s (Z - Zm^*)/(2i)
+    out[(long long)q.a * npw + p] = mk(h * (z.re + zm.re), h * (z.im - zm.im));
+    if (q.c >= 0) out[(long long)q.c * npw + p] = mk(h * (z.im + zm.im), -h * (z.re - zm.re));
+}
+
+// ---------------------------------------------------------- Gram partials
+// P[c][i][j] = sum_{k in chunk c} A[i][k] B[j][k].  64 x 64 output tile per
+// block, 256 threads x (4 x 4) outputs.  Products are summed in R over
+// 32-wide k slices and each slice is added into double accumulators, which
+// keeps float rounding to about eps * sqrt(32) of a slice.
+
+constexpr int GT = 64, GK = 32;
+
+template <typename R>
+__global__ void __launch_bounds__(256) gram_partial_kernel(const R* __restrict__ A, const R* __restrict__ B, int m,
+                                                           int n, long long K, long long kchunk,
+                                                           double* __restrict__ P) {
+    __shared__ R As[GK][GT + 1];
+    __shared__ R Bs[GK][GT + 1];
+    const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+    const long long kbeg = (long long)blockIdx.z * kchunk;
+    const long long kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (long long k0 = kbeg; k0 < kend; k0 += GK) {
+        for (int e = threadIdx.x; e < GT * GK; e += 256) {
+            const int r = e / GK, c = e % GK;
+            const long long k = k0 + c;
+            As[c][r] = (i0 + r < m && k < kend) ? A[(long long)(i0 + r) * K + k] : R(0);
+            Bs[c][r] = (j0 + r < n && k < kend) ? B[(long long)(j0 + r) * K + k] : R(0);
+        }
+        __syncthreads();
+        R s[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) s[a][b] = R(0);
+#pragma unroll 8
+        for (int c = 0; c < GK; ++c) {
+            R av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[c][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[c][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) s[a][b] += av[a] * bv[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += double(s[a][b]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * b;
+            if (i < m && j < n) P[((long long)blockIdx.z * m + i) * n + j] = acc[a][b];
+        }
+}
+
+template <typename R>
+__global__ void gram_finish_kernel(const double* __restrict__ P, int nchunk, const R* __restrict__ A,
+                                   const R* __restrict__ B, int m, int n, long long K, double* __restrict__ G,
+                                   int ldg) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * n) return;
+    const int i = e / n, j = e % n;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += P[((long long)c * m + i) * n + j];
+    const double g0 = double(A[(long long)i * K]) * double(B[(long long)j * K]) +
+                      double(A[(long long)i * K + 1]) * double(B[(long long)j * K + 1]);
+    G[(long long)i * ldg + j] = 2.0 * s - g0;
+}
+
+// ------------------------------------------------------------ NN product
+// out[i][c] = alpha sum_k A[i][k] B[k][c], A double [m][k].  Block: 32 rows x
+// 128 columns, 256 threads, each 4 rows x 4 columns (columns strided by 32).
+// C = double: every product and sum in double (the triangular solve).
+// C = float:  A rounded to float, products summed in float over 16-wide k
+//             slices, slices summed in double (the ACE apply).
+constexpr int NM = 32, NC = 128, NK = 16;
+
+template <typename R, typename C>
+__global__ void __launch_bounds__(256) gemm_nn_kernel(const double* __restrict__ A, int m, int kdim,
+                                                      const R* __restrict__ B, long long ncols, double alpha,
+                                                      R* __restrict__ out) {
+    __shared__ C As[NK][NM];
+    __shared__ C Bs[NK][NC];
+    const int i0 = blockIdx.y * NM;
+    const long long c0 = (long long)blockIdx.x * NC;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // ty: 0..7
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int k0 = 0; k0 < kdim; k0 += NK) {
+        for (int e = threadIdx.x; e < NK * NM; e += 256) {
+            const int r = e / NK, c = e % NK;
+            As[c][r] = (i0 + r < m && k0 + c < kdim) ? C(A[(long long)(i0 + r) * kdim + k0 + c]) : C(0);
+        }
+        for (int e = threadIdx.x; e < NK * NC; e += 256) {
+            const int r = e / NC, c = e % NC;
+            Bs[r][c] = (k0 + r < kdim && c0 + c < ncols) ? C(B[(long long)(k0 + r) * ncols + c0 + c]) : C(0);
+        }
+        __syncthreads();
+        C s[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) s[a][b] = C(0);
+#pragma unroll
+        for (int c = 0; c < NK; ++c) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const C av = As[c][ty + 8 * a];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) s[a][b] += av * Bs[c][tx + 32 * b];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += double(s[a][b]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = i0 + ty + 8 * a;
+            const long long c = c0 + tx + 32 * b;
+            if (i < m && c < ncols) out[(long long)i * ncols + c] = R(alpha * acc[a][b]);
+        }
+}
+
+// ------------------------------------------------ Cholesky and inverse (FP64)
+// -M = L L^T (right-looking, one block), then Linv = L^-1 column by column.
+
+__global__ void __launch_bounds__(1024) neg_cholesky_inverse_kernel(const double* __restrict__ M, int n,
+                                                                     double* __restrict__ L,
+                                                                     double* __restrict__ Linv,
+                                                                     int* __restrict__ status) {
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    // lower triangle of -M, symmetrised
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        L[e] = i >= j ? -0.5 * (M[(long long)i * n + j] + M[(long long)j * n + i]) : 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            const double d = L[(long long)k * n + k];
+            if (!(d > 0.0)) bad = 1;
+            L[(long long)k * n + k] = d > 0.0 ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        const double dkk = L[(long long)k * n + k];
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) L[(long long)i * n + k] /= dkk;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = k + 1 + e / m, j = k + 1 + e % m;
+            if (j <= i) L[(long long)i * n + j] -= L[(long long)i * n + k] * L[(long long)j * n + k];
+        }
+        __syncthreads();
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        for (int i = 0; i < j; ++i) Linv[(long long)i * n + j] = 0.0;
+        Linv[(long long)j * n + j] = 1.0 / L[(long long)j * n + j];
+        for (int i = j + 1; i < n; ++i) {
+            double s = 0.0;
+            for (int k = j; k < i; ++k) s += L[(long long)i * n + k] * Linv[(long long)k * n + j];
+            Linv[(long long)i * n + j] = -s / L[(long long)i * n + i];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *status = bad;
+}
+
+// ------------------------------------------------------------ energy
+__global__ void __launch_bounds__(1024) energy_reduce_kernel(const double* __restrict__ e_part,
+                                                              const Quad* __restrict__ quads, int ntrans,
+                                                              int ntiles, double coef, double* __restrict__ E) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int t = threadIdx.x; t < ntrans; t += blockDim.x) {
+        const Quad q = quads[t];
+        double e1 = 0.0, e2 = 0.0;
+        for (int k = 0; k < ntiles; ++k) {
+            e1 += e_part[((long long)t * ntiles + k) * 2];
+            e2 += e_part[((long long)t * ntiles + k) * 2 + 1];
+        }
+        s += (q.a != q.b ? 2.0 : 1.0) * e1;
+        if (q.c >= 0) s += (q.c != q.d ? 2.0 : 1.0) * e2;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *E = coef * red[0];
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_scatter(const cx<R>* psi, const Quad* quads, int t0, int batch, int npw, const int* ip,
+                           const int* in, cx<R>* box, long long N, cudaStream_t st) {
+    dim3 grid((npw + 255) / 256, batch);
+    scatter_kernel<R><<<grid, 256, 0, st>>>(psi, quads, t0, npw, ip, in, box, N);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gather(const cx<R>* box, const Quad* quads, int t0, int batch, int npw, const int* ip,
+                          const int* in, long long N, double s, cx<R>* out, cudaStream_t st) {
+    dim3 grid((npw + 255) / 256, batch);
+    gather_kernel<R><<<grid, 256, 0, st>>>(box, quads, t0, npw, ip, in, N, R(s), out);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gram_partial(const R* A, const R* B, int m, int n, long long K, int nchunk, double* P,
+                                cudaStream_t st) {
+    long long kc = (K + nchunk - 1) / nchunk;
+    kc = (kc + GK - 1) / GK * GK;
+    dim3 grid((m + GT - 1) / GT, (n + GT - 1) / GT, nchunk);
+    gram_partial_kernel<R><<<grid, 256, 0, st>>>(A, B, m, n, K, kc, P);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gram_finish(const double* P, int nchunk, const R* A, const R* B, int m, int n, long long K,
+                               double* G, int ldg, cudaStream_t st) {
+    const int tot = m * n;
+    gram_finish_kernel<R><<<(tot + 255) / 256, 256, 0, st>>>(P, nchunk, A, B, m, n, K, G, ldg);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gemm_nn(const double* A, int m, int k, const R* B, long long ncols, double alpha, R* out,
+                           bool fp64_math, cudaStream_t st) {
+    dim3 grid((unsigned)((ncols + NC - 1) / NC), (m + NM - 1) / NM);
+    if (fp64_math)
+        gemm_nn_kernel<R, double><<<grid, 256, 0, st>>>(A, m, k, B, ncols, alpha, out);
+    else
+        gemm_nn_kernel<R, R><<<grid, 256, 0, st>>>(A, m, k, B, ncols, alpha, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_neg_cholesky_inverse(const double* M, int n, double* L, double* Linv, int* status,
+                                        cudaStream_t st) {
+    neg_cholesky_inverse_kernel<<<1, 1024, 0, st>>>(M, n, L, Linv, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_reduce(const double* e_part, const Quad* quads, int ntrans, int ntiles, double coef,
+                                 double* E, cudaStream_t st) {
+    energy_reduce_kernel<<<1, 1024, 0, st>>>(e_part, quads, ntrans, ntiles, coef, E);
+    return cudaGetLastError();
+}
+
+#define ACE_INST(R)                                                                                             \
+    template cudaError_t launch_scatter<R>(const cx<R>*, const Quad*, int, int, int, const int*, const int*,   \
+                                           cx<R>*, long long, cudaStream_t);                                    \
+    template cudaError_t launch_gather<R>(const cx<R>*, const Quad*, int, int, int, const int*, const int*,    \
+                                          long long, double, cx<R>*, cudaStream_t);                             \
+    template cudaError_t launch_gram_partial<R>(const R*, const R*, int, int, long long, int, double*,          \
+                                                cudaStream_t);                                                  \
+    template cudaError_t launch_gram_finish<R>(const double*, int, const R*, const R*, int, int, long long,     \
+                                               double*, int, cudaStream_t);                                     \
+    template cudaError_t launch_gemm_nn<R>(const double*, int, int, const R*, long long, double, R*, bool,      \
+                                           cudaStream_t);
+ACE_INST(float)
+ACE_INST(double)
+#undef ACE_INST
+
+}  // namespace ace

@@ -1,0 +1,145 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle,
+element by element on the same seeded inputs.
+
+Tolerances (written here, derived in the design notes):
+  fp64 form : relative 1e-10 on every output (only rounding order differs);
+  mixed form: |dE_x| <= 1e-6 Ha per atom (n_atom = 3 n_occ / 4) and
+              max |K psi - K_oracle psi| / max |K_oracle psi| <= 1e-6;
+              intermediates (W_G, M, V_X psi) to 2e-6 relative to their maximum.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_2110_07670_gb300 as ace
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(E=1e-10, K=1e-10, W=1e-10), "mixed": dict(E=1e-6, K=1e-6, W=2e-6)}
+
+
+def dev(a, plan):
+    dt = np.complex64 if plan.prec == ace.ACE_MIXED else np.complex128
+    return torch.from_numpy(np.ascontiguousarray(a.astype(dt))).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2110_07670_gb300 import build
+    build.build_library()
+    ace.load()
+
+
+def small_system(n=5, seed=11):
+    cell = gen.cubic_cell(7.0)
+    return dict(cell=cell, ecut=14.0, grid=(16, 16, 16), alpha=0.25, psi=gen.random_orbitals(cell, 14.0, n, seed),
+                trials=gen.random_trials(cell, 14.0, 3, seed + 1), n_atom=3 * n / 4)
+
+
+def check_build(s, prec, pairs=None, trials=None):
+    tol = TOL[prec]
+    n = len(s["psi"])
+    ref = oracle.ace_build(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"], pairs=pairs)
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, prec)
+    assert np.array_equal(ace.ace_gvec(plan), ref["miller"])
+    xi, E = ace.ace_build(plan, dev(s["psi"], plan), s["alpha"], pairs=pairs)
+    W, M = ace.ace_last_intermediates(plan, n)
+    assert abs(E - ref["E_x"]) / s["n_atom"] <= tol["E"] * (1 if prec == "mixed" else abs(ref["E_x"]) + 1e-300)
+    assert rel(host(W), ref["W_G"]) <= tol["W"]
+    assert np.abs(M - ref["M"]).max() <= tol["W"] * np.abs(ref["M"]).max()
+    tr = trials if trials is not None else gen.random_trials(s["cell"], s["ecut"], 6, seed=99)
+    Kref = oracle.ace_apply(ref["xi"], tr, ref["miller"])
+    K = host(ace.ace_apply(plan, xi, dev(tr, plan)))
+    assert rel(K, Kref) <= tol["K"]
+    # exactness on the occupied span with the GPU's own vectors
+    Kphi = host(ace.ace_apply(plan, xi, dev(s["psi"], plan)))
+    assert rel(Kphi, ref["W_G"]) <= tol["K"] * 2
+    return E, ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_hfx_exact_matches_oracle(prec):
+    s = small_system()
+    ref = oracle.vx_apply(s["psi"], s["trials"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], len(s["psi"]), prec)
+    out = host(ace.hfx_apply_exact(plan, dev(s["psi"], plan), s["alpha"], dev(s["trials"], plan)))
+    assert rel(out, ref) <= TOL[prec]["W"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_build_small_random(prec):
+    check_build(gen.config_small(), prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_build_odd_count_noncubic(prec):
+    """7 orbitals (last packed transform half empty), a skewed cell and a
+    16 x 18 x 20 grid (radices 2, 3, 4, 5, 8 on different axes)."""
+    cell = np.array([[7.0, 0.0, 0.0], [0.6, 7.5, 0.0], [0.3, -0.4, 8.0]])
+    ecut = 9.0
+    psi = gen.random_orbitals(cell, ecut, 7, seed=31)
+    s = dict(cell=cell, ecut=ecut, grid=(16, 18, 20), alpha=0.25, psi=psi, n_atom=3 * 7 / 4)
+    check_build(s, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_build_single_orbital(prec):
+    s = small_system(n=1, seed=41)
+    check_build(s, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_build_screened_pairs(prec):
+    s = small_system(n=6, seed=51)
+    rng = np.random.default_rng(3)
+    row_ptr, cols = [0], []
+    for i in range(6):
+        js = [j for j in range(i, 6) if j == i or rng.random() < 0.5]
+        cols += js
+        row_ptr.append(len(cols))
+    pairs = (np.array(row_ptr, dtype=np.int32), np.array(cols, dtype=np.int32))
+    check_build(s, prec, pairs=pairs)
+
+
+def test_apply_empty_and_shapes():
+    s = small_system()
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], 5, "mixed")
+    xi, _ = ace.ace_build(plan, dev(s["psi"], plan), s["alpha"])
+    out = ace.ace_apply(plan, xi, dev(s["trials"][:0], plan))
+    assert out.shape[0] == 0
+
+
+def test_error_paths():
+    s = small_system()
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], 5, "mixed")
+    dup = s["psi"].copy()
+    dup[1] = dup[0]
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_build(plan, dev(dup, plan), s["alpha"])
+    assert e.value.code == -3
+    bad = s["psi"].copy()
+    bad[2, 0] += 1e-3j
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_build(plan, dev(bad, plan), s["alpha"])
+    assert e.value.code == -1
+    with pytest.raises(ace.AceError) as e:
+        ace.Plan((8, 8, 8), s["cell"], s["ecut"], 5, "mixed")
+    assert e.value.code == -2
+    with pytest.raises(ace.AceError) as e:
+        ace.Plan((21, 21, 21), s["cell"], s["ecut"], 5, "mixed")
+    assert e.value.code == -2
+    with pytest.raises(ace.AceError):
+        ace.ace_build(plan, dev(gen.random_orbitals(s["cell"], s["ecut"], 6, 1), plan), s["alpha"])
+    # the plan stays usable after errors
+    xi, E = ace.ace_build(plan, dev(s["psi"], plan), s["alpha"])
+    assert np.isfinite(E)
