@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Throughput of the ACE build + apply hot path on GB300.
+
+One step = one pass of the whole hot path over one synthetic system: orbitals
+to real space, every pair density and its FFT Poisson solve with the exchange
+accumulation, W to reciprocal space, M = Phi^T W, the FP64 Cholesky of -M,
+xi = W L^-T, E_x, and one ACE apply K psi = -xi (xi^T psi) on n_occ trial
+vectors (an inner MTS step).  Workload: 128 occupied real orbitals of a
+32-water-box-shaped cell (18.6 bohr, 96^3 grid, 80 Ry, 8256 pairs), seeded
+synthetic Gaussian-sum orbitals.
+
+Prints one JSON line.  value = pair Poisson solves per second (whole job);
+the line also carries ACE builds per second, the FP64 GPU form of the same
+step, the roofline of the dominant kernel, a CPU-oracle baseline, the
+end-to-end number through the public API with host buffers, and the SM
+clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair Poisson solves/sec + ACE builds/sec, mixed vs FP64 GPU at |dE_x|<=1e-6 Ha/atom"
+WORKLOAD = "water32: 128 occupied real orbitals, 96^3 grid, cubic 18.6 bohr, 80 Ry, 8256 pairs, alpha 0.25"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+L2_BYTES = 129 * 1024 * 1024
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[4 + i] and "Not" not in r[4 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(seed_trials=77):
+    import gen
+    cfg = gen.config_water32()
+    trials = gen.random_trials(cfg["cell"], cfg["ecut"], cfg["psi"].shape[0], seed_trials)
+    return cfg, trials
+
+
+# algorithmic bytes of the pair passes per packed transform (two pairs), FP32:
+# spectrum write / read+write / read, plus the function reads and W updates
+# that each kernel's tiling implies (see the design notes)
+def pass_bytes(N, esz):
+    c = 2 * esz
+    return {"pair_fwd": N * (4 * esz + c), "pair_coulomb": 2 * N * c, "pair_inv": N * (c + 4 * esz + 4 * 2 * esz)}
+
+
+def cpu_baseline(cfg, seconds_target=15.0):
+    """The FP64 oracle on a bounded sample of the workload's pairs, all host cores."""
+    import oracle
+    n = cfg["psi"].shape[0]
+    # sample: the pairs of row 0 of the pair list (all of the orbital and W
+    # transforms still run; the rate counts the pair-solve time only)
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    row_ptr[1:] = n
+    cols = np.arange(n, dtype=np.int32)
+    _, _, t = oracle.exchange(cfg["psi"], cfg["cell"], cfg["grid"], cfg["ecut"], cfg["alpha"],
+                              pairs=(row_ptr, cols), times=True)
+    npairs = len(cols)
+    return {"value": npairs / t[1], "unit": "pairs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 oracle on {npairs} pairs (row 0 of the 8256-pair list): pair solves {t[1]:.1f} s, "
+                      f"orbital transforms {t[0]:.1f} s, W back-transforms {t[2]:.1f} s (not counted)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    cfg, _ = workload()
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    sample = None
+    for _ in range(max(1, args.steps)):
+        cb = cpu_baseline(cfg)
+        vals.append(cb["value"])
+        sample = cb
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 8256 / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample["sample"]},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": sample["cores"], "kind": "oracle",
+                             "sample": sample["sample"]},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2110_07670_gb300 as ace
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cfg, trials = workload()
+    n = cfg["psi"].shape[0]
+    npairs = n * (n + 1) // 2
+    N = int(np.prod(cfg["grid"]))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def setup(prec):
+        plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, prec)
+        dt = np.complex64 if prec == "mixed" else np.complex128
+        psi = torch.from_numpy(cfg["psi"].astype(dt)).cuda()
+        tr = torch.from_numpy(trials.astype(dt)).cuda()
+        xi = torch.empty_like(psi)
+        K = torch.empty_like(tr)
+        return plan, psi, tr, xi, K
+
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed_steps(plan, psi, tr, xi, K, steps, warmup, with_timing=False):
+        E = None
+        for _ in range(warmup):
+            xi, E = ace.ace_build(plan, psi, cfg["alpha"], xi=xi)
+            ace.ace_apply(plan, xi, tr, out=K)
+        torch.cuda.synchronize()
+        ace.ace_get_stats(plan)
+        ace.ace_set_timing(plan, with_timing)
+        barrier()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()  # L2 flush between timed steps, outside the timed interval
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            xi, E = ace.ace_build(plan, psi, cfg["alpha"], xi=xi)
+            ace.ace_apply(plan, xi, tr, out=K)
+            b.record()
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+        barrier()
+        torch.cuda.synchronize()
+        stats = ace.ace_get_stats(plan)
+        ace.ace_set_timing(plan, False)
+        return total, E, stats
+
+    # ---- mixed form, device-resident inputs (the headline value)
+    plan, psi, tr, xi, K = setup("mixed")
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, E_mixed, stats = timed_steps(plan, psi, tr, xi, K, args.steps, args.warmup, with_timing=True)
+    clocks = sampler.stop()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = npairs * args.steps * world / (total_ms / 1e3)
+    builds = args.steps * world / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (pass with the largest share of the step)
+    hbm, peak_kind = peaks()
+    pb = pass_bytes(N, 4)
+    ntrans = stats["pair_transforms"]
+    phase_ms = {"pair_fwd": stats["pair_fwd_ms"], "pair_coulomb": stats["pair_coulomb_ms"],
+                "pair_inv": stats["pair_inv_ms"]}
+    dom = max(phase_ms, key=phase_ms.get)
+    achieved = pb[dom] * ntrans / (phase_ms[dom] / 1e3) / 1e9 if phase_ms[dom] > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                "bytes_per_transform": pb[dom], "transforms": ntrans,
+                "share_of_step": phase_ms[dom] / max(stats["total_ms"], 1e-9)}
+    gpu_launches = int(stats["launches"]) + 0
+
+    # ---- end to end through the public API with host buffers
+    psi_h = torch.from_numpy(cfg["psi"].astype(np.complex64)).pin_memory()
+    tr_h = torch.from_numpy(trials.astype(np.complex64)).pin_memory()
+    xi_h = torch.empty_like(psi_h).pin_memory()
+    K_h = torch.empty_like(tr_h).pin_memory()
+    for _ in range(1):
+        psi.copy_(psi_h, non_blocking=True)
+        xi, _ = ace.ace_build(plan, psi, cfg["alpha"], xi=xi)
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        psi.copy_(psi_h, non_blocking=True)
+        tr.copy_(tr_h, non_blocking=True)
+        xi, _ = ace.ace_build(plan, psi, cfg["alpha"], xi=xi)
+        ace.ace_apply(plan, xi, tr, out=K)
+        xi_h.copy_(xi, non_blocking=True)
+        K_h.copy_(K, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    h2d = psi_h.numel() * 8 + tr_h.numel() * 8
+    d2h = xi_h.numel() * 8 + K_h.numel() * 8 + 8
+    e2e = {"value": npairs * args.steps * world / (e2e_ms / 1e3), "unit": "pairs/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    plan.close()
+    del psi, tr, xi, K
+
+    # ---- plain FP64 GPU form of the same step (comparison point of the metric)
+    fp64 = None
+    if not args.no_fp64:
+        p64, psi64, tr64, xi64, K64 = setup("fp64")
+        t64, E64, _ = timed_steps(p64, psi64, tr64, xi64, K64, 1, 1)
+        fp64 = {"pairs_per_s": npairs / (t64 / 1e3), "builds_per_s": 1e3 / t64, "ms_per_step": t64,
+                "E_x": E64, "dE_x_per_atom_mixed_vs_fp64": abs(E_mixed - E64) / cfg["n_atom"]}
+        p64.close()
+        del psi64, tr64, xi64, K64
+
+    if rank != 0:
+        return
+    cb = None if args.no_cpu_baseline or world > 1 else cpu_baseline(cfg)
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 FFT/pairs/W, FP64 M/Cholesky/xi/E_x)",
+                       "apply_trials": int(trials.shape[0]), "l2": "flushed between timed steps",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "ace_builds_per_s": builds, "E_x": E_mixed, "fp64_gpu": fp64,
+            "phases_ms_per_step": {k: v / args.steps for k, v in stats.items() if k.endswith("_ms")},
+            "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    if int(os.environ.get("WORLD_SIZE", 1)) > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -127,6 +127,31 @@ int hfx_apply_exact(ace_plan* plan, const void* psi_occ, int n_occ, double alpha
  */
 int ace_last_intermediates(ace_plan* plan, void* W_G, double* M, void* stream);
 
+/*
+ * Per-phase device time, from CUDA events recorded on the call's stream while
+ * timing is enabled (ace_set_timing), summed over the calls since the last
+ * ace_get_stats.  ace_get_stats synchronises with the recorded events and
+ * resets the sums.  Counters (transforms, launches) are kept whether timing
+ * is on or not.
+ */
+typedef struct {
+    double orbitals_ms;       /* psi_G -> phi(r): scatter and inverse FFT passes */
+    double pair_fwd_ms;       /* pair densities and forward FFT passes (Eq. 3) */
+    double pair_coulomb_ms;   /* Coulomb passes: forward z, 4 pi / |G|^2, inverse z */
+    double pair_inv_ms;       /* inverse FFT passes fused with W accumulation (Eq. 2, 4) */
+    double w_to_g_ms;         /* W(r) -> W(G) */
+    double gram_ms;           /* Gamma Gram products (M, and xi^T psi in the apply) */
+    double factor_ms;         /* Cholesky of -M and the inverse factor */
+    double xi_ms;             /* xi = L^-1 W, and -xi C in the apply */
+    double energy_ms;         /* E_x reduction */
+    double total_ms;          /* all of the above */
+    long long pair_transforms;  /* packed pair transforms (two pairs each) */
+    long long launches;         /* kernels launched by the library */
+} ace_stats;
+
+int ace_set_timing(ace_plan* plan, int enable);
+int ace_get_stats(ace_plan* plan, ace_stats* stats);
+
 /* Message of this thread's last error ("" if none); returns its length. */
 int ace_last_error(char* buf, int len);
 

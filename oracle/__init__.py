@@ -44,6 +44,7 @@ def _load():
             "orc_half_sphere": [P, f64, i32, P, P],
             "orc_fft3d": [P, P, i32],
             "orc_exchange": [P, i32, i32, P, P, P, f64, P, P, i32, P, P],
+            "orc_exchange_timed": [P, i32, i32, P, P, P, f64, P, P, i32, P, P, P],
             "orc_vx_apply": [P, i32, P, i32, i32, P, P, P, f64, i32, P],
             "orc_pair_energy": [P, P, i32, P, P, P, P],
             "orc_to_real": [P, i32, i32, P, P, P, P],
@@ -107,18 +108,20 @@ def _csr(pairs):
     return np.ascontiguousarray(rp, dtype=np.int32), np.ascontiguousarray(col, dtype=np.int32)
 
 
-def exchange(psi, cell, grid, ecut, alpha, pairs=None, nthreads=0):
-    """(W_G, E_x): W_G[i] = alpha-scaled V_X phi_i on the half sphere, E_x = -alpha sum (ij|ji)."""
+def exchange(psi, cell, grid, ecut, alpha, pairs=None, nthreads=0, times=False):
+    """(W_G, E_x): W_G[i] = alpha-scaled V_X phi_i on the half sphere, E_x = -alpha sum (ij|ji).
+    times=True adds the wall seconds (orbital transforms, pair solves, back transforms)."""
     psi = _c128(psi)
     m = half_sphere(cell, ecut)
     n, npw = psi.shape
     assert npw == len(m)
     W = np.zeros_like(psi)
     E = ctypes.c_double(0)
+    t = np.zeros(3)
     rp, col = _csr(pairs)
-    _check(_load().orc_exchange(_p(psi), n, npw, _p(m), _p(_grid(grid)), _p(_cell(cell)), float(alpha),
-                                _p(rp), _p(col), int(nthreads), _p(W), ctypes.byref(E)))
-    return W, E.value
+    _check(_load().orc_exchange_timed(_p(psi), n, npw, _p(m), _p(_grid(grid)), _p(_cell(cell)), float(alpha),
+                                      _p(rp), _p(col), int(nthreads), _p(W), ctypes.byref(E), _p(t)))
+    return (W, E.value, t) if times else (W, E.value)
 
 
 def vx_apply(psi_occ, trials, cell, grid, ecut, alpha, nthreads=0):

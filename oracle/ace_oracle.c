@@ -35,6 +35,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #include <unistd.h>
 
 typedef double complex cplx;
@@ -370,6 +371,68 @@ static void free_locks(pthread_mutex_t *l, int n)
     free(l);
 }
 
+/* Run fn(ctx, i, scratch) for i < n over nthreads threads (static round robin). */
+typedef struct {
+    void (*fn)(void *, int, cplx *);
+    void *ctx;
+    int n, nt, tid;
+    long scratch;
+} pfor_t;
+
+static void *pfor_worker(void *arg)
+{
+    pfor_t *p = arg;
+    cplx *scratch = malloc(sizeof(cplx) * p->scratch);
+    for (int i = p->tid; i < p->n; i += p->nt) p->fn(p->ctx, i, scratch);
+    free(scratch);
+    return NULL;
+}
+
+static void parallel_for(int n, int nthreads, long scratch, void (*fn)(void *, int, cplx *), void *ctx)
+{
+    if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > n) nthreads = n > 0 ? n : 1;
+    pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
+    pfor_t *args = malloc(sizeof(pfor_t) * nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        args[t] = (pfor_t){fn, ctx, n, nthreads, t, scratch};
+        pthread_create(&th[t], NULL, pfor_worker, &args[t]);
+    }
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    free(args);
+}
+
+typedef struct {
+    const grid_t *g;
+    const cplx *c;
+    double *f;
+    cplx *cout;
+    double scale;
+} map_t;
+
+static void to_real_one(void *ctx, int i, cplx *box)
+{
+    map_t *m = ctx;
+    to_real(m->g, m->c + (long)i * m->g->npw, box, m->f + (long)i * m->g->N);
+}
+
+static void to_recip_one(void *ctx, int i, cplx *box)
+{
+    map_t *m = ctx;
+    double *f = m->f + (long)i * m->g->N;
+    for (long r = 0; r < m->g->N; ++r) f[r] *= m->scale;
+    to_recip(m->g, f, box, m->cout + (long)i * m->g->npw);
+}
+
+static double wall(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return ts.tv_sec + 1e-9 * ts.tv_nsec;
+}
+
 /* Expand a CSR list (row i: cols j >= i), or every i <= j when row_ptr is NULL. */
 static long expand_pairs(int n, const int32_t *row_ptr, const int32_t *col, int32_t **pa, int32_t **pb)
 {
@@ -396,11 +459,24 @@ static long expand_pairs(int n, const int32_t *row_ptr, const int32_t *col, int3
 /*
  * Exchange of the occupied set with itself (Eq. 2 and 4), restricted to the
  * listed pairs: W_G[i] = half-sphere coefficients of (V_X phi_i), scaled by
- * alpha, and E_X = -alpha sum (2 - delta_ij) e_ij.
+ * alpha, and E_X = -alpha sum (2 - delta_ij) e_ij.  times (may be NULL)
+ * receives the wall seconds of the orbital transforms, the pair solves and
+ * the back transforms.
  */
+int orc_exchange_timed(const double *psi_G, int n_occ, int npw, const int32_t *miller, const int grid[3],
+                       const double cell[9], double alpha, const int32_t *row_ptr, const int32_t *col,
+                       int nthreads, double *W_G, double *E_x, double *times);
+
 int orc_exchange(const double *psi_G, int n_occ, int npw, const int32_t *miller, const int grid[3],
                  const double cell[9], double alpha, const int32_t *row_ptr, const int32_t *col,
                  int nthreads, double *W_G, double *E_x)
+{
+    return orc_exchange_timed(psi_G, n_occ, npw, miller, grid, cell, alpha, row_ptr, col, nthreads, W_G, E_x, NULL);
+}
+
+int orc_exchange_timed(const double *psi_G, int n_occ, int npw, const int32_t *miller, const int grid[3],
+                       const double cell[9], double alpha, const int32_t *row_ptr, const int32_t *col,
+                       int nthreads, double *W_G, double *E_x, double *times)
 {
     grid_t g;
     int st = grid_init(&g, grid, cell, npw, miller);
@@ -412,23 +488,29 @@ int orc_exchange(const double *psi_G, int n_occ, int npw, const int32_t *miller,
     double *phi = malloc(sizeof(double) * N * n_occ), *acc = calloc((size_t)N * n_occ, sizeof(double));
     cplx *box = malloc(sizeof(cplx) * N);
     if (!phi || !acc || !box) return ORC_ERR_OOM;
-    for (int i = 0; i < n_occ; ++i) to_real(&g, c + (long)i * npw, box, phi + (long)i * N);
+    double t0 = wall();
+    map_t mp = {.g = &g, .c = c, .f = phi};
+    parallel_for(n_occ, nthreads, N, to_real_one, &mp);
+    double t1 = wall();
     int32_t *pa, *pb;
     long np = expand_pairs(n_occ, row_ptr, col, &pa, &pb);
     pthread_mutex_t *locks = new_locks(n_occ);
     xwork_t w = {.g = &g, .left = phi, .right = phi, .acc_left = acc, .acc_right = acc, .symmetric = 1,
                  .pa = pa, .pb = pb, .npairs = np, .lock_left = locks, .lock_right = locks};
     run_pairs(&w, nthreads);
+    double t2 = wall();
     free_locks(locks, n_occ);
     free(pa);
     free(pb);
     if (E_x) *E_x = -alpha * w.e_sum;
     if (W_G) {
-        for (int i = 0; i < n_occ; ++i) {
-            double *f = acc + (long)i * N;
-            for (long r = 0; r < N; ++r) f[r] *= -alpha;
-            to_recip(&g, f, box, (cplx *)W_G + (long)i * npw);
-        }
+        map_t mb = {.g = &g, .f = acc, .cout = (cplx *)W_G, .scale = -alpha};
+        parallel_for(n_occ, nthreads, N, to_recip_one, &mb);
+    }
+    if (times) {
+        times[0] = t1 - t0;
+        times[1] = t2 - t1;
+        times[2] = wall() - t2;
     }
     free(phi);
     free(acc);
@@ -451,8 +533,10 @@ int orc_vx_apply(const double *psi_occ, int n_occ, const double *psi_trial, int 
     double *acc = calloc((size_t)N * T, sizeof(double));
     cplx *box = malloc(sizeof(cplx) * N);
     if (!phi || !f || !acc || !box) return ORC_ERR_OOM;
-    for (int i = 0; i < n_occ; ++i) to_real(&g, (const cplx *)psi_occ + (long)i * npw, box, phi + (long)i * N);
-    for (int t = 0; t < T; ++t) to_real(&g, (const cplx *)psi_trial + (long)t * npw, box, f + (long)t * N);
+    map_t m1 = {.g = &g, .c = (const cplx *)psi_occ, .f = phi};
+    parallel_for(n_occ, nthreads, N, to_real_one, &m1);
+    map_t m2 = {.g = &g, .c = (const cplx *)psi_trial, .f = f};
+    parallel_for(T, nthreads, N, to_real_one, &m2);
     long np = (long)T * n_occ;
     int32_t *pa = malloc(sizeof(int32_t) * np), *pb = malloc(sizeof(int32_t) * np);
     for (long q = 0; q < np; ++q) {
@@ -464,11 +548,8 @@ int orc_vx_apply(const double *psi_occ, int n_occ, const double *psi_trial, int 
                  .pa = pa, .pb = pb, .npairs = np, .lock_left = locks, .lock_right = NULL};
     run_pairs(&w, nthreads);
     free_locks(locks, T);
-    for (int t = 0; t < T; ++t) {
-        double *a = acc + (long)t * N;
-        for (long r = 0; r < N; ++r) a[r] *= -alpha;
-        to_recip(&g, a, box, (cplx *)out + (long)t * npw);
-    }
+    map_t m3 = {.g = &g, .f = acc, .cout = (cplx *)out, .scale = -alpha};
+    parallel_for(T, nthreads, N, to_recip_one, &m3);
     free(pa);
     free(pb);
     free(phi);

@@ -22,7 +22,7 @@ ACE_MIXED = 1
 _ERRORS = {-1: "ACE_ERR_INVALID_ARG", -2: "ACE_ERR_GRID_TOO_SMALL", -3: "ACE_ERR_NOT_POSDEF", -4: "ACE_ERR_OOM",
            -5: "ACE_ERR_CUDA", -6: "ACE_ERR_TIMEOUT"}
 SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_apply", "hfx_apply_exact",
-           "ace_last_intermediates", "ace_last_error")
+           "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error")
 
 _lib = None
 
@@ -35,6 +35,15 @@ class AceError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("pair_batch", ctypes.c_int), ("deterministic", ctypes.c_int)]
+
+
+STAT_FIELDS = ("orbitals_ms", "pair_fwd_ms", "pair_coulomb_ms", "pair_inv_ms", "w_to_g_ms", "gram_ms", "factor_ms",
+               "xi_ms", "energy_ms", "total_ms")
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in STAT_FIELDS] + [("pair_transforms", ctypes.c_longlong),
+                                                               ("launches", ctypes.c_longlong)]
 
 
 def library_path():
@@ -61,6 +70,8 @@ def load(build_if_missing=False):
     lib.ace_apply.argtypes = [P, P, i32, P, i32, P, P]
     lib.hfx_apply_exact.argtypes = [P, P, i32, f64, P, i32, P, P]
     lib.ace_last_intermediates.argtypes = [P, P, P, P]
+    lib.ace_set_timing.argtypes = [P, i32]
+    lib.ace_get_stats.argtypes = [P, ctypes.POINTER(_Stats)]
     lib.ace_last_error.argtypes = [ctypes.c_char_p, i32]
     for name in SYMBOLS:
         if name != "ace_plan_destroy":
@@ -202,3 +213,18 @@ def ace_last_intermediates(plan, n_occ, stream=None):
     _check(load().ace_last_intermediates(plan.handle, _ptr(W), M.ctypes.data_as(ctypes.c_void_p),
                                          _stream(stream)))
     return W, M
+
+
+def ace_set_timing(plan, enable=True):
+    """Record CUDA events at phase boundaries of the following calls."""
+    _check(load().ace_set_timing(plan.handle, 1 if enable else 0))
+
+
+def ace_get_stats(plan):
+    """Per-phase device milliseconds and counters since the last call (resets them)."""
+    st = _Stats()
+    _check(load().ace_get_stats(plan.handle, ctypes.byref(st)))
+    d = {f: getattr(st, f) for f in STAT_FIELDS}
+    d["pair_transforms"] = st.pair_transforms
+    d["launches"] = st.launches
+    return d

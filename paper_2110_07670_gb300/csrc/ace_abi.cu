@@ -112,9 +112,32 @@ struct ace_plan {
     double* d_C = nullptr;
     size_t C_cap = 0;
     int last_n_occ = 0;
+    // timing: events recorded at phase boundaries; each interval belongs to the
+    // phase of the event that opens it (PH_IDLE closes a call)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, cudaEvent_t>> marks;
+    long long pair_transforms = 0;
+    long long launches = 0;
 };
 
 namespace {
+
+enum Phase { PH_IDLE = -1, PH_ORB = 0, PH_PFWD, PH_PCOUL, PH_PINV, PH_W2G, PH_GRAM, PH_FACTOR, PH_XI, PH_ENERGY, PH_N };
+
+void mark(ace_plan* P, int phase, cudaStream_t st) {
+    if (!P->timing) return;
+    cudaEvent_t e;
+    if (!P->ev_pool.empty()) {
+        e = P->ev_pool.back();
+        P->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaEventRecord(e, st);
+    P->marks.push_back({phase, e});
+}
 
 template <typename T>
 int grow(T** p, size_t* cap, size_t need) {
@@ -231,6 +254,7 @@ PassArgs base_args(const ace_plan* P) {
 #define ACE_CKL(expr)                                                                                         \
     do {                                                                                                      \
         cudaError_t e_ = (expr);                                                                              \
+        ++P->launches;                                                                                        \
         if (e_ != cudaSuccess) return fail(ACE_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
     } while (0)
 
@@ -242,6 +266,7 @@ int run_to_real(ace_plan* P, const cx<R>* psi, const Quad* dq, int ntrans, R* ou
     a.accl = out;
     a.scale = 1.0 / std::sqrt(P->omega);
     cx<R>* spec = (cx<R>*)P->d_spec;
+    mark(P, PH_ORB, st);
     for (int t0 = 0; t0 < ntrans; t0 += P->batch) {
         const int nb = std::min(P->batch, ntrans - t0);
         a.t0 = t0;
@@ -265,6 +290,7 @@ int run_to_recip(ace_plan* P, const R* acc, const Quad* dq, int ntrans, double s
     a.quads = dq;
     a.fl = acc;
     cx<R>* spec = (cx<R>*)P->d_spec;
+    mark(P, PH_W2G, st);
     for (int t0 = 0; t0 < ntrans; t0 += P->batch) {
         const int nb = std::min(P->batch, ntrans - t0);
         a.t0 = t0;
@@ -295,14 +321,20 @@ int run_pairs(ace_plan* P, const R* fl, const R* fr, R* accl, R* accr, int symme
     for (int t0 = 0; t0 < ntrans; t0 += P->batch) {
         const int nb = std::min(P->batch, ntrans - t0);
         a.t0 = t0;
+        P->pair_transforms += nb;
+        mark(P, PH_PFWD, st);
         if (P->fused_xy) {
             ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_PAIR, EPI_STORE, MID_NONE, -1, nb, st));
+            mark(P, PH_PCOUL, st);
             ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_COULOMB, -1, nb, st));
+            mark(P, PH_PINV, st);
             ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_LOAD, EPI_ACCUM, MID_NONE, +1, nb, st));
         } else {
             ACE_CKL(launch_pass<R>(a, P->s_x, PRO_PAIR, EPI_STORE, MID_NONE, -1, nb, st));
             ACE_CKL(launch_pass<R>(a, P->s_y, PRO_LOAD, EPI_STORE, MID_NONE, -1, nb, st));
+            mark(P, PH_PCOUL, st);
             ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_COULOMB, -1, nb, st));
+            mark(P, PH_PINV, st);
             ACE_CKL(launch_pass<R>(a, P->s_y, PRO_LOAD, EPI_STORE, MID_NONE, +1, nb, st));
             ACE_CKL(launch_pass<R>(a, P->s_x, PRO_LOAD, EPI_ACCUM, MID_NONE, +1, nb, st));
         }
@@ -318,6 +350,7 @@ int gram(ace_plan* P, const cx<R>* A, int m, const cx<R>* B, int n, double* G, c
     int nchunk = std::max(1, (2 * 152 + tiles - 1) / tiles);
     nchunk = (int)std::min<long long>(nchunk, std::max<long long>(1, K / 256));
     ACE_TRY(grow(&P->d_part, &P->part_cap, (size_t)nchunk * m * n));
+    mark(P, PH_GRAM, st);
     ACE_CKL(launch_gram_partial<R>((const R*)A, (const R*)B, m, n, K, nchunk, P->d_part, st));
     ACE_CKL(launch_gram_finish<R>(P->d_part, nchunk, (const R*)A, (const R*)B, m, n, K, G, n, st));
     return ACE_OK;
@@ -395,13 +428,17 @@ int build_impl(ace_plan* P, const void* psi_G, int n_occ, double alpha, const in
     ACE_CK(cudaMemsetAsync(acc, 0, (size_t)n_occ * P->N * sizeof(R), st));
     ACE_TRY(grow(&P->d_epart, &P->epart_cap, (size_t)std::max(n_pair_t, 1) * P->ntiles_last * 2));
     ACE_TRY(run_pairs<R>(P, phi, phi, acc, acc, 1, d_pq, n_pair_t, P->d_epart, st));
+    mark(P, PH_ENERGY, st);
     ACE_CKL(launch_energy_reduce(P->d_epart, d_pq, n_pair_t, P->ntiles_last, -alpha * P->omega / (double)P->N,
                                  P->d_E, st));
     cx<R>* WG = (cx<R>*)P->d_WG;
     ACE_TRY(run_to_recip<R>(P, acc, d_oq, n_orb_t, -alpha * std::sqrt(P->omega) / (double)P->N, WG, st));
     ACE_TRY(gram<R>(P, psi, n_occ, WG, n_occ, P->d_M, st));
+    mark(P, PH_FACTOR, st);
     ACE_CKL(launch_neg_cholesky_inverse(P->d_M, n_occ, P->d_L, P->d_Linv, P->d_status, st));
+    mark(P, PH_XI, st);
     ACE_CKL(launch_gemm_nn<R>(P->d_Linv, n_occ, n_occ, (const R*)WG, 2LL * P->npw, 1.0, (R*)xi, true, st));
+    mark(P, PH_IDLE, st);
     int status = 0;
     double E = 0;
     ACE_CK(cudaMemcpyAsync(&status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -448,6 +485,7 @@ int hfx_impl(ace_plan* P, const void* psi_occ, int n_occ, double alpha, const vo
     ACE_TRY(run_pairs<R>(P, (const R*)tphi, phi, (R*)P->d_tacc, nullptr, 0, P->d_quads + no + nt, np, nullptr, st));
     ACE_TRY(run_to_recip<R>(P, (const R*)P->d_tacc, P->d_quads + no, nt, -alpha * std::sqrt(P->omega) / (double)P->N,
                             (cx<R>*)out, st));
+    mark(P, PH_IDLE, st);
     ACE_CK(cudaGetLastError());
     return ACE_OK;
 }
@@ -456,11 +494,15 @@ template <typename R>
 int apply_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, void* out, cudaStream_t st) {
     ACE_TRY(grow(&P->d_C, &P->C_cap, (size_t)T * n_occ));
     ACE_TRY(gram<R>(P, (const cx<R>*)psi, T, (const cx<R>*)xi, n_occ, P->d_C, st));  // C[t][k] = <psi_t|xi_k>
+    mark(P, PH_XI, st);
     ACE_CKL(launch_gemm_nn<R>(P->d_C, T, n_occ, (const R*)xi, 2LL * P->npw, -1.0, (R*)out, false, st));
+    mark(P, PH_IDLE, st);
     return ACE_OK;
 }
 
 void free_plan(ace_plan* P) {
+    for (auto& m : P->marks) cudaEventDestroy(m.second);
+    for (auto e : P->ev_pool) cudaEventDestroy(e);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
                     P->d_WG, P->d_M, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_part, P->d_quads,
                     P->d_epart, P->d_tphi, P->d_tacc, P->d_C};
@@ -628,6 +670,45 @@ int ace_last_intermediates(ace_plan* plan, void* W_G, double* M, void* stream) {
         ACE_CK(cudaMemcpyAsync(W_G, plan->d_WG, (size_t)n * plan->npw * 2 * plan->esz, cudaMemcpyDeviceToDevice, st));
     if (M) ACE_CK(cudaMemcpyAsync(M, plan->d_M, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToHost, st));
     ACE_CK(cudaStreamSynchronize(st));
+    return ACE_OK;
+}
+
+int ace_set_timing(ace_plan* plan, int enable) {
+    if (!plan) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    plan->timing = enable != 0;
+    return ACE_OK;
+}
+
+int ace_get_stats(ace_plan* plan, ace_stats* out) {
+    if (!plan || !out) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    DeviceGuard g(plan->dev);
+    double ph[PH_N] = {0};
+    auto& mk = plan->marks;
+    for (size_t i = 0; i + 1 < mk.size(); ++i) {
+        if (mk[i].first < 0) continue;
+        ACE_CK(cudaEventSynchronize(mk[i + 1].second));
+        float ms = 0;
+        ACE_CK(cudaEventElapsedTime(&ms, mk[i].second, mk[i + 1].second));
+        ph[mk[i].first] += ms;
+    }
+    if (!mk.empty()) ACE_CK(cudaEventSynchronize(mk.back().second));
+    for (auto& m : mk) plan->ev_pool.push_back(m.second);
+    mk.clear();
+    std::memset(out, 0, sizeof(*out));
+    out->orbitals_ms = ph[PH_ORB];
+    out->pair_fwd_ms = ph[PH_PFWD];
+    out->pair_coulomb_ms = ph[PH_PCOUL];
+    out->pair_inv_ms = ph[PH_PINV];
+    out->w_to_g_ms = ph[PH_W2G];
+    out->gram_ms = ph[PH_GRAM];
+    out->factor_ms = ph[PH_FACTOR];
+    out->xi_ms = ph[PH_XI];
+    out->energy_ms = ph[PH_ENERGY];
+    for (int i = 0; i < PH_N; ++i) out->total_ms += ph[i];
+    out->pair_transforms = plan->pair_transforms;
+    out->launches = plan->launches;
+    plan->pair_transforms = 0;
+    plan->launches = 0;
     return ACE_OK;
 }
 

@@ -61,9 +61,11 @@ def check_build(s, prec, pairs=None, trials=None):
     Kref = oracle.ace_apply(ref["xi"], tr, ref["miller"])
     K = host(ace.ace_apply(plan, xi, dev(tr, plan)))
     assert rel(K, Kref) <= tol["K"]
-    # exactness on the occupied span with the GPU's own vectors
-    Kphi = host(ace.ace_apply(plan, xi, dev(s["psi"], plan)))
-    assert rel(Kphi, ref["W_G"]) <= tol["K"] * 2
+    if pairs is None:
+        # exactness on the occupied span with the GPU's own vectors (a screened
+        # list makes M unsymmetric, and exactness holds only without screening)
+        Kphi = host(ace.ace_apply(plan, xi, dev(s["psi"], plan)))
+        assert rel(Kphi, ref["W_G"]) <= tol["K"] * 2
     return E, ref
 
 
