@@ -100,6 +100,7 @@ struct ace_plan {
     double* d_Linv = nullptr;
     double* d_E = nullptr;
     int* d_status = nullptr;
+    int* d_err = nullptr;
     double* d_part = nullptr;
     size_t part_cap = 0;
     Quad* d_quads = nullptr;
@@ -200,7 +201,10 @@ int setup_shapes(ace_plan* P) {
         s.tx = tx;
         s.axes = axes;
         const int e = tz * ty * tx;
-        s.threads = std::min(512, std::max(128, roundup(e / 16, 32)));
+        s.threads = std::min(512, std::max(128, roundup(e / 24, 32)));
+        // bulk copies need 16-byte aligned runs; vectors need 4 consecutive reals
+        s.bulk = (c == 16 || (n2 % 2 == 0 && tx % 2 == 0)) ? 1 : 0;
+        s.vec = (tx % 4 == 0 && n2 % 4 == 0) ? 1 : 0;
         const int tw = ((axes & 1) ? n2 : 0) + ((axes & 2) ? n1 : 0) + ((axes & 4) ? n0 : 0);
         s.smem = (size_t)e * c + (size_t)tw * c + ((axes & 4) ? (size_t)(n0 + n1 + n2) * sizeof(int) : 0);
         const size_t red = (size_t)(s.threads / 32) * 2 * sizeof(double);
@@ -247,6 +251,7 @@ PassArgs base_args(const ace_plan* P) {
     a.src = a.dst = P->d_spec;
     for (int i = 0; i < 9; ++i) a.b[i] = P->b[i];
     a.kscale = 1.0 / (double)P->N;
+    a.err = P->d_err;
     for (int d = 0; d < 3; ++d) a.freq[d] = P->d_freq[d];
     return a;
 }
@@ -373,6 +378,18 @@ void pack_pairs(const std::vector<int>& pa, const std::vector<int>& pb, std::vec
     }
 }
 
+// A bounded device-side wait that gave up leaves a flag; report and clear it.
+int check_device_error(ace_plan* P, cudaStream_t st) {
+    int err = 0;
+    ACE_CK(cudaMemcpyAsync(&err, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaStreamSynchronize(st));
+    if (err) {
+        ACE_CK(cudaMemsetAsync(P->d_err, 0, sizeof(int), st));
+        return fail(ACE_ERR_TIMEOUT, "a bounded wait for a bulk copy timed out on the device");
+    }
+    return ACE_OK;
+}
+
 template <typename R>
 int check_gamma(ace_plan* P, const void* psi, int n, cudaStream_t st) {
     std::vector<cx<R>> c0(n);
@@ -444,6 +461,7 @@ int build_impl(ace_plan* P, const void* psi_G, int n_occ, double alpha, const in
     ACE_CK(cudaMemcpyAsync(&status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     ACE_CK(cudaMemcpyAsync(&E, P->d_E, sizeof(double), cudaMemcpyDeviceToHost, st));
     ACE_CK(cudaStreamSynchronize(st));
+    ACE_TRY(check_device_error(P, st));
     P->last_n_occ = n_occ;
     if (E_x) *E_x = E;
     if (status) return fail(ACE_ERR_NOT_POSDEF, "-M is not positive definite (dependent or zero orbitals)");
@@ -504,7 +522,7 @@ void free_plan(ace_plan* P) {
     for (auto& m : P->marks) cudaEventDestroy(m.second);
     for (auto e : P->ev_pool) cudaEventDestroy(e);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
-                    P->d_WG, P->d_M, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_part, P->d_quads,
+                    P->d_WG, P->d_M, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
                     P->d_epart, P->d_tphi, P->d_tacc, P->d_C};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -570,6 +588,8 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     ACE_TRY(dalloc((void**)&P->d_Linv, nn * sizeof(double)));
     ACE_TRY(dalloc((void**)&P->d_E, sizeof(double)));
     ACE_TRY(dalloc((void**)&P->d_status, sizeof(int)));
+    ACE_TRY(dalloc((void**)&P->d_err, sizeof(int)));
+    ACE_CK(cudaMemset(P->d_err, 0, sizeof(int)));
     return ACE_OK;
 }
 

@@ -36,6 +36,9 @@ struct PassArgs {
     int n0, n1, n2;  // box extents (z, y, x); x is contiguous
     int tz, ty, tx;  // tile extents (divide the box extents)
     int axes;        // 1 = x, 2 = y (needs tz == 1), 4 = z
+    int bulk;        // spectrum tiles by bulk async copies (16-byte aligned runs)
+    int vec;         // real functions as 4-wide vectors (tx, n2 multiples of 4)
+    int* err;        // device error flag (1: a bounded wait timed out)
     AxisPlan px, py, pz;
     const void *twx, *twy, *twz;  // exp(-2 pi i j / n) per axis, cx<R>
     // prologue
@@ -60,7 +63,7 @@ struct PassArgs {
 };
 
 struct PassShape {
-    int tz, ty, tx, axes, threads;
+    int tz, ty, tx, axes, threads, bulk, vec;
     size_t smem;
 };
 

@@ -84,13 +84,15 @@ def test_build_small_random(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_build_odd_count_noncubic(prec):
-    """7 orbitals (last packed transform half empty), a skewed cell and a
-    16 x 18 x 20 grid (radices 2, 3, 4, 5, 8 on different axes)."""
+@pytest.mark.parametrize("grid", [(16, 18, 20), (20, 16, 18), (18, 20, 15)])
+def test_build_odd_count_noncubic(prec, grid):
+    """7 orbitals (last packed transform half empty), a skewed cell and
+    non-cubic grids with radices 2, 3, 4, 5, 8 on different axes; x extents
+    20 / 18 / 15 exercise the vector, scalar and non-bulk tile paths."""
     cell = np.array([[7.0, 0.0, 0.0], [0.6, 7.5, 0.0], [0.3, -0.4, 8.0]])
     ecut = 9.0
     psi = gen.random_orbitals(cell, ecut, 7, seed=31)
-    s = dict(cell=cell, ecut=ecut, grid=(16, 18, 20), alpha=0.25, psi=psi, n_atom=3 * 7 / 4)
+    s = dict(cell=cell, ecut=ecut, grid=grid, alpha=0.25, psi=psi, n_atom=3 * 7 / 4)
     check_build(s, prec)
 
 
@@ -124,10 +126,10 @@ def test_apply_empty_and_shapes():
 def test_error_paths():
     s = small_system()
     plan = ace.Plan(s["grid"], s["cell"], s["ecut"], 5, "mixed")
-    dup = s["psi"].copy()
-    dup[1] = dup[0]
+    zero = s["psi"].copy()
+    zero[1] = 0.0  # a zero orbital makes M exactly singular
     with pytest.raises(ace.AceError) as e:
-        ace.ace_build(plan, dev(dup, plan), s["alpha"])
+        ace.ace_build(plan, dev(zero, plan), s["alpha"])
     assert e.value.code == -3
     bad = s["psi"].copy()
     bad[2, 0] += 1e-3j
