@@ -87,6 +87,7 @@ struct ace_plan {
     void* d_tw[3] = {nullptr, nullptr, nullptr};
     int* d_freq[3] = {nullptr, nullptr, nullptr};
     bool fused_xy = false;
+    bool cube_kernels = true;  // compile-time kernels for supported N^3 boxes
     PassShape s_xy{}, s_x{}, s_y{}, s_z{};
     int ntiles_last = 1;  // tiles of the pass that accumulates W
     int batch = 1;
@@ -194,14 +195,14 @@ int setup_shapes(ace_plan* P) {
     if (smax <= 0) smax = 227 * 1024;
     const size_t c = sizeof(cx<R>);
     const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
-    auto mk_shape = [&](int tz, int ty, int tx, int axes) {
+    auto mk_shape = [&](int tz, int ty, int tx, int axes, int threads = 0) {
         PassShape s{};
         s.tz = tz;
         s.ty = ty;
         s.tx = tx;
         s.axes = axes;
         const int e = tz * ty * tx;
-        s.threads = std::min(512, std::max(128, roundup(e / 24, 32)));
+        s.threads = threads > 0 ? threads : std::min(512, std::max(128, roundup(e / 24, 32)));
         // bulk copies need 16-byte aligned runs; vectors need 4 consecutive reals
         s.bulk = (c == 16 || (n2 % 2 == 0 && tx % 2 == 0)) ? 1 : 0;
         s.vec = (tx % 4 == 0 && n2 % 4 == 0) ? 1 : 0;
@@ -213,6 +214,18 @@ int setup_shapes(ace_plan* P) {
     };
     const int target = (int)((64 * 1024) / c);  // elements of a one-axis tile (64 KB)
     const long long plane = (long long)n1 * n2;
+    if (P->cube_kernels && c == 8 && n0 == n1 && n1 == n2 && cube_supported(n0)) {
+        // compile-time kernels: whole planes and n x ty x tx pencil tiles
+        const int n = n0;
+        P->fused_xy = true;
+        P->s_xy = mk_shape(1, n, n, 3, cube_xy_threads(n));
+        P->s_z = mk_shape(n, cube_z_ty(n), cube_z_tx(n), 4, cube_z_threads(n));
+        P->s_xy.cube = P->s_z.cube = 1;
+        if (P->s_xy.smem > (size_t)smax || P->s_z.smem > (size_t)smax)
+            return fail(ACE_ERR_GRID_TOO_SMALL, "plane tile exceeds shared memory");
+        P->ntiles_last = n;
+        return ACE_OK;
+    }
     P->fused_xy = (size_t)(plane + n1 + n2) * c <= (size_t)std::min(smax, 160 * 1024);
     if (P->fused_xy) P->s_xy = mk_shape(1, n1, n2, 3);
     {
@@ -570,6 +583,7 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     ACE_TRY(dalloc((void**)&P->d_in, P->npw * sizeof(int)));
     ACE_CK(cudaMemcpy(P->d_ip, ip.data(), P->npw * sizeof(int), cudaMemcpyHostToDevice));
     ACE_CK(cudaMemcpy(P->d_in, in.data(), P->npw * sizeof(int), cudaMemcpyHostToDevice));
+    if (opts && opts->deterministic == 2) P->cube_kernels = false;  // generic kernels only (testing)
     ACE_TRY(setup_shapes<R>(P));
     int ntrans_min = (P->n_occ_max + 1) / 2;
     int batch = opts && opts->pair_batch > 0 ? opts->pair_batch

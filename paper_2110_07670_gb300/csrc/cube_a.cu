@@ -1,0 +1,13 @@
+// cube_a.cu -- compile-time pass kernels for the N^3 boxes N = 32, 60, 80.
+#include "pass_kernel.cuh"
+
+namespace ace {
+
+template cudaError_t pass_detail::dispatch_cube<32>(const PassArgs&, const PassShape&, int, int, int, int, int,
+                                                  cudaStream_t);
+template cudaError_t pass_detail::dispatch_cube<60>(const PassArgs&, const PassShape&, int, int, int, int, int,
+                                                  cudaStream_t);
+template cudaError_t pass_detail::dispatch_cube<80>(const PassArgs&, const PassShape&, int, int, int, int, int,
+                                                  cudaStream_t);
+
+}  // namespace ace

@@ -1,0 +1,13 @@
+// cube_b.cu -- compile-time pass kernels for the N^3 boxes N = 90, 96, 100.
+#include "pass_kernel.cuh"
+
+namespace ace {
+
+template cudaError_t pass_detail::dispatch_cube<90>(const PassArgs&, const PassShape&, int, int, int, int, int,
+                                                  cudaStream_t);
+template cudaError_t pass_detail::dispatch_cube<96>(const PassArgs&, const PassShape&, int, int, int, int, int,
+                                                  cudaStream_t);
+template cudaError_t pass_detail::dispatch_cube<100>(const PassArgs&, const PassShape&, int, int, int, int, int,
+                                                  cudaStream_t);
+
+}  // namespace ace

@@ -1,0 +1,13 @@
+// cube_c.cu -- compile-time pass kernels for the N^3 boxes N = 108, 120, 160.
+#include "pass_kernel.cuh"
+
+namespace ace {
+
+template cudaError_t pass_detail::dispatch_cube<108>(const PassArgs&, const PassShape&, int, int, int, int, int,
+                                                  cudaStream_t);
+template cudaError_t pass_detail::dispatch_cube<120>(const PassArgs&, const PassShape&, int, int, int, int, int,
+                                                  cudaStream_t);
+template cudaError_t pass_detail::dispatch_cube<160>(const PassArgs&, const PassShape&, int, int, int, int, int,
+                                                  cudaStream_t);
+
+}  // namespace ace

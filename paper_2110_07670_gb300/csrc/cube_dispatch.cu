@@ -1,0 +1,39 @@
+// cube_dispatch.cu -- route a pass to the compile-time kernel of its N^3 box.
+#include "pass_kernel.cuh"
+
+namespace ace {
+
+namespace pass_detail {
+#define ACE_CUBE_DECL(N)                                                                                      \
+    extern template cudaError_t dispatch_cube<N>(const PassArgs&, const PassShape&, int, int, int, int, int, \
+                                                 cudaStream_t);
+ACE_CUBE_DECL(32)
+ACE_CUBE_DECL(60)
+ACE_CUBE_DECL(80)
+ACE_CUBE_DECL(90)
+ACE_CUBE_DECL(96)
+ACE_CUBE_DECL(100)
+ACE_CUBE_DECL(108)
+ACE_CUBE_DECL(120)
+ACE_CUBE_DECL(160)
+#undef ACE_CUBE_DECL
+}  // namespace pass_detail
+
+cudaError_t cube_pass_launch(int n, const PassArgs& a, const PassShape& s, int pro, int epi, int mid, int sgn,
+                             int batch, cudaStream_t st) {
+    using namespace pass_detail;
+    switch (n) {
+        case 32: return dispatch_cube<32>(a, s, pro, epi, mid, sgn, batch, st);
+        case 60: return dispatch_cube<60>(a, s, pro, epi, mid, sgn, batch, st);
+        case 80: return dispatch_cube<80>(a, s, pro, epi, mid, sgn, batch, st);
+        case 90: return dispatch_cube<90>(a, s, pro, epi, mid, sgn, batch, st);
+        case 96: return dispatch_cube<96>(a, s, pro, epi, mid, sgn, batch, st);
+        case 100: return dispatch_cube<100>(a, s, pro, epi, mid, sgn, batch, st);
+        case 108: return dispatch_cube<108>(a, s, pro, epi, mid, sgn, batch, st);
+        case 120: return dispatch_cube<120>(a, s, pro, epi, mid, sgn, batch, st);
+        case 160: return dispatch_cube<160>(a, s, pro, epi, mid, sgn, batch, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ace

@@ -21,6 +21,8 @@
 // stage needs one barrier and no register staging of other threads' data.
 #pragma once
 
+#include <type_traits>
+
 #if defined(__CUDACC__)
 #define ACE_HD __host__ __device__ __forceinline__
 #else
@@ -139,6 +141,103 @@ struct Dft<8, SGN, R> {
     }
 };
 
+// --------------------------------------------------- compile-time twiddles
+// sin and cos by their Taylor series after reduction to [-pi, pi]; evaluated
+// only in constant expressions (the angles below are rational multiples of
+// 2 pi known at compile time), accurate to a few ulps of double.
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+constexpr double ce_reduce(double x) {
+    while (x > kPi) x -= 2 * kPi;
+    while (x < -kPi) x += 2 * kPi;
+    return x;
+}
+constexpr double ce_sin(double x) {
+    x = ce_reduce(x);
+    double term = x, sum = x;
+    for (int k = 1; k < 30; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double ce_cos(double x) {
+    x = ce_reduce(x);
+    double term = 1, sum = 1;
+    for (int k = 1; k < 30; ++k) {
+        term *= -x * x / ((2.0 * k - 1) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+
+// exp(SGN 2 pi i M / N) as compile-time constants
+template <int N, int M, int SGN>
+struct Twiddle {
+    static constexpr double re = ce_cos(2 * kPi * M / N);
+    static constexpr double im = SGN * ce_sin(2 * kPi * M / N);
+};
+
+// compile-time loop: f(std::integral_constant<int, I>) for I in [B, E)
+template <int B, int E>
+struct CLoop {
+    template <class F>
+    static ACE_HD void run(F&& f) {
+        if constexpr (B < E) {
+            f(std::integral_constant<int, B>{});
+            CLoop<B + 1, E>::run(f);
+        }
+    }
+};
+
+// Composite codelet DFT of size A*B in registers: A-point transforms over
+// the B interleaved subsequences, twiddles w_{AB}^{j s}, then B-point
+// transforms; output in natural order.
+template <int A, int B, int SGN, typename R>
+struct DftNested {
+    static ACE_HD void run(cx<R>* v) {
+        cx<R> t[A * B];
+        CLoop<0, B>::run([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            cx<R> u[A];
+#pragma unroll
+            for (int q = 0; q < A; ++q) u[q] = v[j + B * q];
+            Dft<A, SGN, R>::run(u);
+            CLoop<0, A>::run([&](auto sc) {
+                constexpr int s = decltype(sc)::value;
+                if constexpr (j * s == 0) {
+                    t[j + B * s] = u[s];
+                } else {
+                    const cx<R> w = mk(R(Twiddle<A * B, j * s, SGN>::re), R(Twiddle<A * B, j * s, SGN>::im));
+                    t[j + B * s] = cmul(u[s], w);
+                }
+            });
+        });
+#pragma unroll
+        for (int s = 0; s < A; ++s) {
+            cx<R> u[B];
+#pragma unroll
+            for (int j = 0; j < B; ++j) u[j] = t[j + B * s];
+            Dft<B, SGN, R>::run(u);
+#pragma unroll
+            for (int k = 0; k < B; ++k) v[s + A * k] = u[k];
+        }
+    }
+};
+
+template <int SGN, typename R>
+struct Dft<6, SGN, R> : DftNested<2, 3, SGN, R> {};
+template <int SGN, typename R>
+struct Dft<9, SGN, R> : DftNested<3, 3, SGN, R> {};
+template <int SGN, typename R>
+struct Dft<10, SGN, R> : DftNested<2, 5, SGN, R> {};
+template <int SGN, typename R>
+struct Dft<12, SGN, R> : DftNested<4, 3, SGN, R> {};
+template <int SGN, typename R>
+struct Dft<15, SGN, R> : DftNested<5, 3, SGN, R> {};
+template <int SGN, typename R>
+struct Dft<16, SGN, R> : DftNested<4, 4, SGN, R> {};
+
 // ------------------------------------------------------------------- plans
 
 constexpr int kMaxStages = 12;
@@ -170,9 +269,33 @@ ACE_HD void butterfly_coords(const Lines& L, int nb, int b, int& line, int& i) {
     }
 }
 
-// One butterfly of stage radix RAD on blocks of length Lb (= m RAD).
-// tw[t] = exp(-2 pi i t / n), t < n.  SGN < 0: forward DIF stage (butterfly
-// then twiddle).  SGN > 0: transposed conjugate stage (twiddle then butterfly).
+// One butterfly in place: the RAD elements base[q * qstride].  tw[t] =
+// exp(-2 pi i t / n); the stage's twiddles are tw[q * tstep] (tw_on = j > 0).
+// SGN < 0: forward DIF (butterfly, then twiddle); SGN > 0: transposed
+// conjugate stage (conjugate twiddle, then butterfly).
+template <int RAD, int SGN, typename R>
+ACE_HD void butterfly_core(cx<R>* base, int qstride, const cx<R>* tw, int tstep, bool tw_on) {
+    cx<R> u[RAD];
+#pragma unroll
+    for (int q = 0; q < RAD; ++q) u[q] = base[q * qstride];
+    if (SGN > 0 && tw_on) {
+#pragma unroll
+        for (int q = 1; q < RAD; ++q) {
+            cx<R> w = tw[q * tstep];
+            w.im = -w.im;
+            u[q] = cmul(u[q], w);
+        }
+    }
+    Dft<RAD, SGN, R>::run(u);
+    if (SGN < 0 && tw_on) {
+#pragma unroll
+        for (int s = 1; s < RAD; ++s) u[s] = cmul(u[s], tw[s * tstep]);
+    }
+#pragma unroll
+    for (int s = 0; s < RAD; ++s) base[s * qstride] = u[s];
+}
+
+// Butterfly b of a stage with radix RAD on blocks of length Lb (= m RAD).
 template <int RAD, int SGN, typename R>
 ACE_HD void stage_butterfly(cx<R>* buf, const Lines& L, const cx<R>* tw, int Lb, int b) {
     const int m = Lb / RAD;
@@ -181,28 +304,9 @@ ACE_HD void stage_butterfly(cx<R>* buf, const Lines& L, const cx<R>* tw, int Lb,
     butterfly_coords(L, nb, b, line, i);
     const int beta = i / m, j = i - beta * m;
     cx<R>* base = buf + (long long)line * L.lstride + (long long)(beta * Lb + j) * L.estride;
-    const int tstep = (L.n / Lb) * j;  // twiddle index per unit of s: (n / Lb) j
-    cx<R> u[RAD];
-#pragma unroll
-    for (int q = 0; q < RAD; ++q) u[q] = base[(long long)q * m * L.estride];
-    if (SGN > 0) {
-#pragma unroll
-        for (int q = 1; q < RAD; ++q)
-            if (j > 0) {
-                cx<R> w = tw[q * tstep];
-                w.im = -w.im;
-                u[q] = cmul(u[q], w);
-            }
-    }
-    Dft<RAD, SGN, R>::run(u);
-    if (SGN < 0) {
-#pragma unroll
-        for (int s = 1; s < RAD; ++s)
-            if (j > 0) u[s] = cmul(u[s], tw[s * tstep]);
-    }
-#pragma unroll
-    for (int s = 0; s < RAD; ++s) base[(long long)s * m * L.estride] = u[s];
+    butterfly_core<RAD, SGN, R>(base, m * L.estride, tw, (L.n / Lb) * j, j > 0);
 }
+
 
 #if defined(__CUDACC__)
 template <int RAD, int SGN, typename R>
@@ -210,6 +314,23 @@ __device__ __forceinline__ void block_stage(cx<R>* buf, const Lines& L, const cx
     const int total = (L.n / RAD) * L.nlines;
     for (int b = threadIdx.x; b < total; b += blockDim.x) stage_butterfly<RAD, SGN, R>(buf, L, tw, Lb, b);
     __syncthreads();
+}
+
+template <int SGN, typename R>
+__device__ __forceinline__ void stage_dispatch(int r, cx<R>* buf, const Lines& L, const cx<R>* tw, int Lb) {
+    switch (r) {
+        case 2: block_stage<2, SGN, R>(buf, L, tw, Lb); break;
+        case 3: block_stage<3, SGN, R>(buf, L, tw, Lb); break;
+        case 4: block_stage<4, SGN, R>(buf, L, tw, Lb); break;
+        case 5: block_stage<5, SGN, R>(buf, L, tw, Lb); break;
+        case 6: block_stage<6, SGN, R>(buf, L, tw, Lb); break;
+        case 8: block_stage<8, SGN, R>(buf, L, tw, Lb); break;
+        case 9: block_stage<9, SGN, R>(buf, L, tw, Lb); break;
+        case 10: block_stage<10, SGN, R>(buf, L, tw, Lb); break;
+        case 12: block_stage<12, SGN, R>(buf, L, tw, Lb); break;
+        case 15: block_stage<15, SGN, R>(buf, L, tw, Lb); break;
+        default: block_stage<16, SGN, R>(buf, L, tw, Lb); break;
+    }
 }
 
 // Full 1D transform of every line of the tile by the thread block.
@@ -221,13 +342,7 @@ __device__ __forceinline__ void block_fft(cx<R>* buf, const Lines& L, const Axis
         int Lb = L.n;
         for (int s = 0; s < P.nstages; ++s) {
             const int r = P.radix[s];
-            switch (r) {
-                case 2: block_stage<2, SGN, R>(buf, L, tw, Lb); break;
-                case 3: block_stage<3, SGN, R>(buf, L, tw, Lb); break;
-                case 4: block_stage<4, SGN, R>(buf, L, tw, Lb); break;
-                case 5: block_stage<5, SGN, R>(buf, L, tw, Lb); break;
-                default: block_stage<8, SGN, R>(buf, L, tw, Lb); break;
-            }
+            stage_dispatch<SGN, R>(r, buf, L, tw, Lb);
             Lb /= r;
         }
     } else {
@@ -235,37 +350,113 @@ __device__ __forceinline__ void block_fft(cx<R>* buf, const Lines& L, const Axis
         for (int s = P.nstages - 1; s >= 0; --s) {
             const int r = P.radix[s];
             Lb *= r;
-            switch (r) {
-                case 2: block_stage<2, SGN, R>(buf, L, tw, Lb); break;
-                case 3: block_stage<3, SGN, R>(buf, L, tw, Lb); break;
-                case 4: block_stage<4, SGN, R>(buf, L, tw, Lb); break;
-                case 5: block_stage<5, SGN, R>(buf, L, tw, Lb); break;
-                default: block_stage<8, SGN, R>(buf, L, tw, Lb); break;
-            }
+            stage_dispatch<SGN, R>(r, buf, L, tw, Lb);
         }
     }
 }
 #endif
 
-// Factor n into stage radices, radix 8 first, then 4, 2, 3, 5.  Returns false
-// when n has a prime factor above 5 or needs too many stages.
-inline bool make_axis_plan(int n, AxisPlan& P) {
-    P.n = n;
-    P.nstages = 0;
-    int m = n;
-    const int order[5] = {8, 4, 2, 3, 5};
-    for (int r : order) {
-        while (m % r == 0) {
-            if (P.nstages == kMaxStages) return false;
-            P.radix[P.nstages++] = r;
-            m /= r;
-        }
-    }
-    return m == 1 && n >= 1;
+// Stage radices with a register codelet.
+constexpr bool is_codelet(int r) {
+    return r == 2 || r == 3 || r == 4 || r == 5 || r == 6 || r == 8 || r == 9 || r == 10 || r == 12 || r == 15 ||
+           r == 16;
 }
 
+// Factor n into as few codelet radices as possible, preferring the largest
+// smallest radix (balanced stages); the larger radix goes first.  Returns
+// false when n has a prime factor above 5 or needs more than kMaxStages.
+constexpr bool make_axis_plan(int n, AxisPlan& P) {
+    P.n = n;
+    P.nstages = 0;
+    if (n < 1) return false;
+    if (n == 1) return true;
+    if (is_codelet(n)) {
+        P.radix[P.nstages++] = n;
+        return true;
+    }
+    int best1 = 0, best2 = 0;
+    for (int r1 = 16; r1 >= 2; --r1)
+        if (is_codelet(r1) && n % r1 == 0 && is_codelet(n / r1)) {
+            const int r2 = n / r1, lo = r1 < r2 ? r1 : r2;
+            const int blo = best1 < best2 ? best1 : best2;
+            if (best1 == 0 || lo > blo || (lo == blo && r1 > best1)) {
+                best1 = r1;
+                best2 = r2;
+            }
+        }
+    if (best1) {
+        P.radix[P.nstages++] = best1;
+        P.radix[P.nstages++] = best2;
+        return true;
+    }
+    int m = n;
+    const int order[11] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+    while (m > 1) {
+        int pick = 0;
+        for (int r : order)
+            if (m % r == 0) {
+                pick = r;
+                break;
+            }
+        if (pick == 0 || P.nstages == kMaxStages) return false;
+        P.radix[P.nstages++] = pick;
+        m /= pick;
+    }
+    return true;
+}
+
+// Compile-time plan of an axis of length N.
+template <int N>
+struct CPlan {
+    static constexpr AxisPlan P = [] {
+        AxisPlan p{};
+        make_axis_plan(N, p);
+        return p;
+    }();
+    static constexpr int stages = P.nstages;
+    static constexpr int radix(int s) { return P.radix[s]; }
+    static constexpr int block_len(int s) {
+        int L = N;
+        for (int t = 0; t < s; ++t) L /= P.radix[t];
+        return L;
+    }
+};
+
+#if defined(__CUDACC__)
+// The same stages with every size known at compile time (N, line count and
+// strides, thread count NT): index arithmetic folds to shifts and multiplies.
+template <int RAD, int SGN, int N, int LB, int NLINES, int ESTRIDE, int LSTRIDE, int NT, typename R>
+__device__ __forceinline__ void static_stage(cx<R>* buf, const cx<R>* tw) {
+    constexpr int M = LB / RAD, NB = N / RAD, TOTAL = NB * NLINES, TS = N / LB;
+#pragma unroll 2
+    for (int b = threadIdx.x; b < TOTAL; b += NT) {
+        int line, i;
+        if constexpr (ESTRIDE == 1) {
+            line = b / NB;
+            i = b - line * NB;
+        } else {
+            i = b / NLINES;
+            line = b - i * NLINES;
+        }
+        const int beta = i / M, j = i - beta * M;
+        butterfly_core<RAD, SGN, R>(buf + line * LSTRIDE + (beta * LB + j) * ESTRIDE, M * ESTRIDE, tw, TS * j,
+                                    M > 1 && j > 0);
+    }
+    __syncthreads();
+}
+
+template <int SGN, int N, int NLINES, int ESTRIDE, int LSTRIDE, int NT, typename R>
+__device__ __forceinline__ void static_fft(cx<R>* buf, const cx<R>* tw) {
+    using PL = CPlan<N>;
+    CLoop<0, PL::stages>::run([&](auto sc) {
+        constexpr int s = SGN < 0 ? decltype(sc)::value : PL::stages - 1 - decltype(sc)::value;
+        static_stage<PL::radix(s), SGN, N, PL::block_len(s), NLINES, ESTRIDE, LSTRIDE, NT, R>(buf, tw);
+    });
+}
+#endif
+
 // Position of frequency k after the forward transform (see the header note).
-inline int digit_reversed_position(const AxisPlan& P, int k) {
+constexpr int digit_reversed_position(const AxisPlan& P, int k) {
     int pos = 0, span = P.n;
     for (int s = 0; s < P.nstages; ++s) {
         const int r = P.radix[s];

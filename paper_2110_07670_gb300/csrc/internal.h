@@ -64,8 +64,31 @@ struct PassArgs {
 
 struct PassShape {
     int tz, ty, tx, axes, threads, bulk, vec;
+    int cube;  // 1: use the compile-time kernel of this N^3 box (single precision)
     size_t smem;
 };
+
+// N^3 boxes with compile-time pass kernels, and their tile geometry (shared by
+// the host planner and the kernel instantiations).
+constexpr bool cube_supported(int n) {
+    return n == 32 || n == 60 || n == 80 || n == 90 || n == 96 || n == 100 || n == 108 || n == 120 || n == 160;
+}
+constexpr int cube_xy_threads(int n) { return n * n >= 12000 ? 512 : 256; }
+constexpr int cube_z_threads(int) { return 256; }
+constexpr int cube_z_tx(int n) {  // largest even divisor of n up to 32
+    for (int d = 32; d >= 2; d -= 2)
+        if (n % d == 0) return d;
+    return 1;
+}
+constexpr int cube_z_ty(int n) {  // largest divisor keeping the tile within 8192 elements
+    for (int d = n; d >= 1; --d)
+        if (n % d == 0 && n * d * cube_z_tx(n) <= 8192) return d;
+    return 1;
+}
+
+// compile-time cube passes (cube_*.cu), single precision
+cudaError_t cube_pass_launch(int n, const PassArgs& a, const PassShape& s, int pro, int epi, int mid, int sgn,
+                             int batch, cudaStream_t st);
 
 // Launch one pass over `batch` transforms (gridDim.y) of the box.
 template <typename R>
