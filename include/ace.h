@@ -113,6 +113,27 @@ int ace_build(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const 
 int ace_apply(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T, void* Kpsi, void* stream);
 
 /*
+ * ace_apply for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a deployment variant of the Eq. 5 apply above).
+ * Callers in an inner loop that must not stall on cudaMalloc / cudaFree
+ * (both synchronise the device), or whose device memory belongs to another
+ * allocator, get the same result as ace_apply without a plan and without any
+ * allocation: the working memory is a fixed 8 MiB __device__ array inside the
+ * library, held on every device that loads the library until the process
+ * exits.
+ *   xi [n_occ][n_pw_half], psi [T][n_pw_half], Kpsi [T][n_pw_half]: device,
+ *   complex128 for precision ACE_FP64, complex64 for ACE_MIXED.
+ * Limit: T * n_occ <= 524288, else ACE_ERR_INVALID_ARG and nothing runs.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  All calls share
+ * the one array and every call overwrites what it uses, so calls that
+ * overlap on the GPU (other streams, other host threads) race: keep them
+ * ordered.
+ */
+int ace_apply_noalloc(const void* xi, int n_occ, const void* psi, int T, int n_pw_half, int precision, void* Kpsi,
+                      void* stream);
+
+/*
  * Exact exchange on trial vectors (Eq. 2 with the occupied set psi_occ):
  *   Vx_psi[t] = -alpha sum_j v_{t j} phi_j, projected on the half sphere.
  *   psi_occ [n_occ][n_pw_half], psi [T][n_pw_half], Vx_psi [T][n_pw_half].

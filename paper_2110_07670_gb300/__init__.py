@@ -22,7 +22,7 @@ ACE_MIXED = 1
 _ERRORS = {-1: "ACE_ERR_INVALID_ARG", -2: "ACE_ERR_GRID_TOO_SMALL", -3: "ACE_ERR_NOT_POSDEF", -4: "ACE_ERR_OOM",
            -5: "ACE_ERR_CUDA", -6: "ACE_ERR_TIMEOUT"}
 SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_apply", "hfx_apply_exact",
-           "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error")
+           "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc")
 
 _lib = None
 
@@ -68,6 +68,7 @@ def load(build_if_missing=False):
     lib.ace_gvec.argtypes = [P, ctypes.POINTER(i32), P]
     lib.ace_build.argtypes = [P, P, i32, f64, P, P, P, ctypes.POINTER(f64), P]
     lib.ace_apply.argtypes = [P, P, i32, P, i32, P, P]
+    lib.ace_apply_noalloc.argtypes = [P, i32, P, i32, i32, i32, P, P]
     lib.hfx_apply_exact.argtypes = [P, P, i32, f64, P, i32, P, P]
     lib.ace_last_intermediates.argtypes = [P, P, P, P]
     lib.ace_set_timing.argtypes = [P, i32]
@@ -228,3 +229,20 @@ def ace_get_stats(plan):
     d["pair_transforms"] = st.pair_transforms
     d["launches"] = st.launches
     return d
+
+
+def ace_apply_noalloc(xi, psi, out, stream=None):
+    """K psi = -xi (xi^T psi) without a plan and without device allocation in
+    the library (for callers that must not allocate).  xi, psi and out are
+    caller-owned contiguous CUDA tensors: complex64 (mixed) or complex128
+    (fp64) of shape [rows][n_pw_half]; T * n_occ <= 524288."""
+    import torch
+    prec = ACE_MIXED if xi.dtype == torch.complex64 else ACE_FP64
+    for t in (xi, psi, out):
+        if not t.is_cuda or not t.is_contiguous() or t.dim() != 2 or t.dtype != xi.dtype or t.shape[1] != xi.shape[1]:
+            raise ValueError("ace_apply_noalloc: contiguous CUDA complex tensors of one dtype and width")
+    if out.shape != psi.shape:
+        raise ValueError("ace_apply_noalloc: out must have the shape of psi")
+    _check(load().ace_apply_noalloc(_ptr(xi), xi.shape[0], _ptr(psi), psi.shape[0], xi.shape[1], prec, _ptr(out),
+                                    _stream(stream)))
+    return out

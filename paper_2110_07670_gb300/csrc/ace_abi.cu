@@ -746,6 +746,13 @@ int ace_get_stats(ace_plan* plan, ace_stats* out) {
     return ACE_OK;
 }
 
+}  // extern "C"
+
+// Record an error for ace_last_error from another translation unit.
+int ace::set_last_error(int code, const char* msg) { return fail(code, msg); }
+
+extern "C" {
+
 int ace_last_error(char* buf, int len) {
     const int n = (int)g_err.size();
     if (buf && len > 0) {

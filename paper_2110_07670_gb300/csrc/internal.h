@@ -133,7 +133,7 @@ cudaError_t launch_neg_cholesky_inverse(const double* M, int n, double* L, doubl
 cudaError_t launch_energy_reduce(const double* e_part, const Quad* quads, int ntrans, int ntiles, double coef,
                                  double* E, cudaStream_t st);
 
-template <typename R>
-cudaError_t launch_fill_zero(R* p, long long n, cudaStream_t st);
+// Record an ACE_ERR_* code and message for ace_last_error(); returns code.
+int set_last_error(int code, const char* msg);
 
 }  // namespace ace
