@@ -207,7 +207,7 @@ int setup_shapes(ace_plan* P) {
         s.bulk = (c == 16 || (n2 % 2 == 0 && tx % 2 == 0)) ? 1 : 0;
         s.vec = (tx % 4 == 0 && n2 % 4 == 0) ? 1 : 0;
         const int tw = ((axes & 1) ? n2 : 0) + ((axes & 2) ? n1 : 0) + ((axes & 4) ? n0 : 0);
-        s.smem = (size_t)e * c + (size_t)tw * c + ((axes & 4) ? (size_t)(n0 + n1 + n2) * sizeof(int) : 0);
+        s.smem = (size_t)e * c + (size_t)tw * c + ((axes & 4) ? (size_t)(n0 + n1 + n2) * 3 * (c / 2) : 0);
         const size_t red = (size_t)(s.threads / 32) * 2 * sizeof(double);
         if (s.smem < red) s.smem = red;
         return s;
@@ -568,6 +568,10 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
         ACE_TRY(dalloc((void**)&P->d_freq[d], P->n[d] * sizeof(int)));
         ACE_CK(cudaMemcpy(P->d_freq[d], fr.data(), P->n[d] * sizeof(int), cudaMemcpyHostToDevice));
     }
+    if (opts && opts->deterministic == 2) P->cube_kernels = false;  // generic kernels only (testing)
+    ACE_TRY(setup_shapes<R>(P));
+    // the compile-time plane kernels of N % 16 == 0 boxes keep x swizzled per row
+    const bool swz = P->s_xy.cube && cube_swizzle(P->n[2]);
     std::vector<int> ip(P->npw), in(P->npw);
     for (int p = 0; p < P->npw; ++p) {
         int m[3], mn[3];
@@ -576,6 +580,10 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
             m[d] = pos[d][((v % P->n[d]) + P->n[d]) % P->n[d]];
             mn[d] = pos[d][((-v % P->n[d]) + P->n[d]) % P->n[d]];
         }
+        if (swz) {
+            m[2] = plane_swizzle(m[2], m[1]);
+            mn[2] = plane_swizzle(mn[2], mn[1]);
+        }
         ip[p] = (m[0] * P->n[1] + m[1]) * P->n[2] + m[2];
         in[p] = (mn[0] * P->n[1] + mn[1]) * P->n[2] + mn[2];
     }
@@ -583,8 +591,6 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     ACE_TRY(dalloc((void**)&P->d_in, P->npw * sizeof(int)));
     ACE_CK(cudaMemcpy(P->d_ip, ip.data(), P->npw * sizeof(int), cudaMemcpyHostToDevice));
     ACE_CK(cudaMemcpy(P->d_in, in.data(), P->npw * sizeof(int), cudaMemcpyHostToDevice));
-    if (opts && opts->deterministic == 2) P->cube_kernels = false;  // generic kernels only (testing)
-    ACE_TRY(setup_shapes<R>(P));
     int ntrans_min = (P->n_occ_max + 1) / 2;
     int batch = opts && opts->pair_batch > 0 ? opts->pair_batch
                                              : (int)std::max<long long>(1, (512LL << 20) / (P->N * (long long)sizeof(cx<R>)));

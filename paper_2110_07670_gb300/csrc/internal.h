@@ -74,6 +74,13 @@ constexpr bool cube_supported(int n) {
     return n == 32 || n == 60 || n == 80 || n == 90 || n == 96 || n == 100 || n == 108 || n == 120 || n == 160;
 }
 constexpr int cube_xy_threads(int n) { return n * n >= 12000 ? 512 : 256; }
+// Plane layout of N % 16 == 0 cubes: within each 16-element block of a row,
+// x position p sits in slot p ^ (((p >> 4) & 7) | ((y & 1) << 3)); the
+// permutation is its own inverse, keeps blocks in place, spreads the
+// butterflies of the contiguous x stages over all shared-memory banks, and
+// alternates bank halves between neighbouring rows.
+constexpr bool cube_swizzle(int n) { return n % 16 == 0; }
+__host__ __device__ constexpr int plane_swizzle(int p, int y) { return p ^ (((p >> 4) & 7) | ((y & 1) << 3)); }
 constexpr int cube_z_threads(int) { return 256; }
 constexpr int cube_z_tx(int n) {  // largest even divisor of n up to 32
     for (int d = 32; d >= 2; d -= 2)

@@ -115,6 +115,8 @@ struct DynShape {
     __device__ explicit DynShape(const PassArgs& a)
         : n0(a.n0), n1(a.n1), n2(a.n2), tz(a.tz), ty(a.ty), tx(a.tx), axes(a.axes) {}
     __device__ int nt() const { return blockDim.x; }
+    __device__ static int slot(int e) { return e; }             // tile slot of tile element e
+    __device__ static int xpos(int s, int) { return s; }        // x position held in global x slot s
     template <int SGN, typename R>
     __device__ void fft_x(cx<R>* t, const cx<R>* tw, const PassArgs& a) const {
         block_fft<SGN, R>(t, Lines{tx, tz * ty, 1, tx}, a.px, tw);
@@ -129,6 +131,85 @@ struct DynShape {
     }
 };
 
+// Stages along the x lines of a swizzled N x N plane (row stride N): the same
+// butterflies as static_stage, with each element addressed through
+// plane_swizzle so that neither the strided first stage nor the contiguous last
+// stage (each butterfly on RAD adjacent positions) collides in the banks.
+template <int RAD, int SGN, typename R>
+__device__ __forceinline__ void butterfly_at(cx<R>* row, const int (&idx)[RAD], const cx<R>* tw, int tstep,
+                                             bool tw_on) {
+    cx<R> u[RAD];
+#pragma unroll
+    for (int q = 0; q < RAD; ++q) u[q] = row[idx[q]];
+    if (SGN > 0 && tw_on) {
+#pragma unroll
+        for (int q = 1; q < RAD; ++q) {
+            cx<R> w = tw[q * tstep];
+            w.im = -w.im;
+            u[q] = cmul(u[q], w);
+        }
+    }
+    Dft<RAD, SGN, R>::run(u);
+    if (SGN < 0 && tw_on) {
+#pragma unroll
+        for (int s = 1; s < RAD; ++s) u[s] = cmul(u[s], tw[s * tstep]);
+    }
+#pragma unroll
+    for (int s = 0; s < RAD; ++s) row[idx[s]] = u[s];
+}
+
+template <int RAD, int SGN, int N, int LB, int NT, typename R>
+__device__ __forceinline__ void static_stage_rows_swizzled(cx<R>* buf, const cx<R>* tw) {
+    constexpr int M = LB / RAD, NB = N / RAD, TOTAL = NB * N, TS = N / LB;
+#pragma unroll 2
+    for (int b = threadIdx.x; b < TOTAL; b += NT) {
+        const int line = b / NB, i = b - line * NB;
+        const int beta = i / M, j = i - beta * M;
+        const int p0 = beta * LB + j;
+        int idx[RAD];
+#pragma unroll
+        for (int q = 0; q < RAD; ++q) idx[q] = plane_swizzle(p0 + q * M, line);
+        butterfly_at<RAD, SGN, R>(buf + line * N, idx, tw, TS * j, M > 1 && j > 0);
+    }
+    __syncthreads();
+}
+
+// y lines of the same swizzled plane: line p holds x position p of every row,
+// which sits in slot plane_swizzle(p, y) of row y.
+template <int RAD, int SGN, int N, int LB, int NT, typename R>
+__device__ __forceinline__ void static_stage_cols_swizzled(cx<R>* buf, const cx<R>* tw) {
+    constexpr int M = LB / RAD, NB = N / RAD, TOTAL = NB * N, TS = N / LB;
+#pragma unroll 2
+    for (int b = threadIdx.x; b < TOTAL; b += NT) {
+        const int i = b / N, p = b - i * N;
+        const int beta = i / M, j = i - beta * M;
+        const int y0 = beta * LB + j;
+        int idx[RAD];
+#pragma unroll
+        for (int q = 0; q < RAD; ++q) idx[q] = (y0 + q * M) * N + plane_swizzle(p, y0 + q * M);
+        butterfly_at<RAD, SGN, R>(buf, idx, tw, TS * j, M > 1 && j > 0);
+    }
+    __syncthreads();
+}
+
+template <int SGN, int N, int NT, typename R>
+__device__ __forceinline__ void static_fft_cols_swizzled(cx<R>* buf, const cx<R>* tw) {
+    using PL = CPlan<N>;
+    CLoop<0, PL::stages>::run([&](auto sc) {
+        constexpr int s = SGN < 0 ? decltype(sc)::value : PL::stages - 1 - decltype(sc)::value;
+        static_stage_cols_swizzled<PL::radix(s), SGN, N, PL::block_len(s), NT, R>(buf, tw);
+    });
+}
+
+template <int SGN, int N, int NT, typename R>
+__device__ __forceinline__ void static_fft_rows_swizzled(cx<R>* buf, const cx<R>* tw) {
+    using PL = CPlan<N>;
+    CLoop<0, PL::stages>::run([&](auto sc) {
+        constexpr int s = SGN < 0 ? decltype(sc)::value : PL::stages - 1 - decltype(sc)::value;
+        static_stage_rows_swizzled<PL::radix(s), SGN, N, PL::block_len(s), NT, R>(buf, tw);
+    });
+}
+
 // ... and compile-time geometry of an N^3 box with NT threads per block: every
 // index division becomes a multiply-shift and every stage loop a fixed count.
 template <int N, int TZ, int TY, int TX, int NT>
@@ -136,15 +217,37 @@ struct CubeShape {
     static constexpr int kMaxThreads = NT;
     static constexpr int n0 = N, n1 = N, n2 = N, tz = TZ, ty = TY, tx = TX;
     static constexpr int axes = (TZ == 1 && TY == N && TX == N) ? 3 : (TZ == N ? 4 : (TZ == 1 && TX == N ? 1 : 2));
+    // Plane tiles of N % 16 == 0 boxes are stored (in shared and global memory)
+    // with x position p of row y in slot swizzle_x(p, y); see plane_swizzle.
+    static constexpr bool kSwzLayout = cube_swizzle(N);
+    static constexpr bool kSwzTile = kSwzLayout && TZ == 1 && TY == N && TX == N;
     __device__ explicit CubeShape(const PassArgs&) {}
     __device__ static constexpr int nt() { return NT; }
+    __device__ static int slot(int e) {
+        if constexpr (kSwzTile) {
+            const int row = e / N, col = e - row * N;
+            return row * N + plane_swizzle(col, row);
+        } else {
+            return e;
+        }
+    }
+    __device__ static int xpos(int s, int y) {
+        if constexpr (kSwzLayout) return plane_swizzle(s, y);
+        else return s;
+    }
     template <int SGN, typename R>
     __device__ void fft_x(cx<R>* t, const cx<R>* tw, const PassArgs&) const {
-        static_fft<SGN, N, TZ * TY, 1, TX, NT, R>(t, tw);
+        if constexpr (kSwzTile)
+            static_fft_rows_swizzled<SGN, N, NT, R>(t, tw);
+        else
+            static_fft<SGN, N, TZ * TY, 1, TX, NT, R>(t, tw);
     }
     template <int SGN, typename R>
     __device__ void fft_y(cx<R>* t, const cx<R>* tw, const PassArgs&) const {
-        static_fft<SGN, N, TX, TX, 1, NT, R>(t, tw);
+        if constexpr (kSwzTile)
+            static_fft_cols_swizzled<SGN, N, NT, R>(t, tw);
+        else
+            static_fft<SGN, N, TX, TX, 1, NT, R>(t, tw);
     }
     template <int SGN, typename R>
     __device__ void fft_z(cx<R>* t, const cx<R>* tw, const PassArgs&) const {
@@ -163,7 +266,9 @@ __global__ void __launch_bounds__(Shape::kMaxThreads) tile_pass(PassArgs a) {
     cx<R>* twx = tile + tile_elems;
     cx<R>* twy = twx + ((S.axes & 1) ? S.n2 : 0);
     cx<R>* twz = twy + ((S.axes & 2) ? S.n1 : 0);
-    int* fq = reinterpret_cast<int*>(twz + ((S.axes & 4) ? S.n0 : 0));  // frequency of each position (Coulomb)
+    // Coulomb: G-vector component of every position along each axis
+    // (gt[3 j + c] axis 0, then axis 1, then axis 2; positions hold digit-reversed frequencies)
+    R* gt = reinterpret_cast<R*>(twz + ((S.axes & 4) ? S.n0 : 0));
 
     const int t = blockIdx.y;
     const int tiles_x = S.n2 / S.tx, tiles_y = S.n1 / S.ty;
@@ -196,9 +301,16 @@ __global__ void __launch_bounds__(Shape::kMaxThreads) tile_pass(PassArgs a) {
     }
 
     if (MID == MID_COULOMB) {
-        for (int j = threadIdx.x; j < S.n0; j += S.nt()) fq[j] = a.freq[0][j];
-        for (int j = threadIdx.x; j < S.n1; j += S.nt()) fq[S.n0 + j] = a.freq[1][j];
-        for (int j = threadIdx.x; j < S.n2; j += S.nt()) fq[S.n0 + S.n1 + j] = a.freq[2][j];
+        const int nsum = S.n0 + S.n1 + S.n2;
+        for (int j = threadIdx.x; j < nsum; j += S.nt()) {
+            const int ax = j < S.n0 ? 0 : (j < S.n0 + S.n1 ? 1 : 2);
+            const int jj = j - (ax == 0 ? 0 : (ax == 1 ? S.n0 : S.n0 + S.n1));
+            const int n = ax == 0 ? S.n0 : (ax == 1 ? S.n1 : S.n2);
+            const R h = R(fold_index(a.freq[ax][jj], n));
+            gt[3 * j] = h * R(a.b[3 * ax]);
+            gt[3 * j + 1] = h * R(a.b[3 * ax + 1]);
+            gt[3 * j + 2] = h * R(a.b[3 * ax + 2]);
+        }
     }
     if (S.axes & 1)
         for (int j = threadIdx.x; j < S.n2; j += S.nt()) twx[j] = reinterpret_cast<const cx<R>*>(a.twx)[j];
@@ -250,11 +362,10 @@ __global__ void __launch_bounds__(Shape::kMaxThreads) tile_pass(PassArgs a) {
                 V4<R> re = PRO == PRO_PAIR ? mul4(va[u], vb[u]) : va[u];
                 V4<R> im = V4<R>{R(0), R(0), R(0), R(0)};
                 if (q.c >= 0) im = PRO == PRO_PAIR ? mul4(vc[u], vd[u]) : vc[u];
-                cx<R>* d = tile + ee[u];
-                d[0] = mk(re.x, im.x);
-                d[1] = mk(re.y, im.y);
-                d[2] = mk(re.z, im.z);
-                d[3] = mk(re.w, im.w);
+                tile[S.slot(ee[u])] = mk(re.x, im.x);
+                tile[S.slot(ee[u] + 1)] = mk(re.y, im.y);
+                tile[S.slot(ee[u] + 2)] = mk(re.z, im.z);
+                tile[S.slot(ee[u] + 3)] = mk(re.w, im.w);
             }
         }
     } else {
@@ -269,7 +380,7 @@ __global__ void __launch_bounds__(Shape::kMaxThreads) tile_pass(PassArgs a) {
                 v.re = fl[q.a * N + r];
                 v.im = q.c >= 0 ? fl[q.c * N + r] : R(0);
             }
-            tile[e] = v;
+            tile[S.slot(e)] = v;
         }
     }
     if (bulk_in) {
@@ -292,19 +403,31 @@ __global__ void __launch_bounds__(Shape::kMaxThreads) tile_pass(PassArgs a) {
         if (MID == MID_COULOMB) {
             S.template fft_z<-1, R>(tile, twz, a);
             const R four_pi_s = R(4.0 * 3.14159265358979323846 * a.kscale);
-            const R b0 = R(a.b[0]), b1 = R(a.b[1]), b2 = R(a.b[2]), b3 = R(a.b[3]), b4 = R(a.b[4]), b5 = R(a.b[5]),
-                    b6 = R(a.b[6]), b7 = R(a.b[7]), b8 = R(a.b[8]);
-            for (int e = threadIdx.x; e < tile_elems; e += S.nt()) {
-                const int ex = e % S.tx, ey = (e / S.tx) % S.ty, ez = e / txy;
-                // positions hold digit-reversed frequencies after the forward stages
-                const R h = R(fold_index(fq[z0 + ez], S.n0)), k = R(fold_index(fq[S.n0 + y0 + ey], S.n1)),
-                        l = R(fold_index(fq[S.n0 + S.n1 + x0 + ex], S.n2));
-                const R gx = h * b0 + k * b3 + l * b6;
-                const R gy = h * b1 + k * b4 + l * b7;
-                const R gz = h * b2 + k * b5 + l * b8;
+            const R* g1 = gt + 3 * S.n0;
+            const R* g2t = gt + 3 * (S.n0 + S.n1);
+            auto coulomb = [&](int e, const R* gyx, int ez) {
+                const R gx = gyx[0] + gt[3 * (z0 + ez)];
+                const R gy = gyx[1] + gt[3 * (z0 + ez) + 1];
+                const R gz = gyx[2] + gt[3 * (z0 + ez) + 2];
                 const R g2 = gx * gx + gy * gy + gz * gz;
                 const R kv = g2 > R(0) ? four_pi_s / g2 : R(0);
                 tile[e] = scale(tile[e], kv);
+            };
+            if (S.nt() % txy == 0) {
+                // each thread keeps one (y, x) line of the tile: its G_y + G_x once
+                const int l = threadIdx.x % txy, ey = l / S.tx, ex = l - ey * S.tx;
+                const int xp = S.xpos(x0 + ex, y0 + ey);
+                const R gyx[3] = {g1[3 * (y0 + ey)] + g2t[3 * xp], g1[3 * (y0 + ey) + 1] + g2t[3 * xp + 1],
+                                  g1[3 * (y0 + ey) + 2] + g2t[3 * xp + 2]};
+                for (int ez = threadIdx.x / txy; ez < S.tz; ez += S.nt() / txy) coulomb(ez * txy + l, gyx, ez);
+            } else {
+                for (int e = threadIdx.x; e < tile_elems; e += S.nt()) {
+                    const int ex = e % S.tx, ey = (e / S.tx) % S.ty, ez = e / txy;
+                    const int xp = S.xpos(x0 + ex, y0 + ey);
+                    const R gyx[3] = {g1[3 * (y0 + ey)] + g2t[3 * xp], g1[3 * (y0 + ey) + 1] + g2t[3 * xp + 1],
+                                      g1[3 * (y0 + ey) + 2] + g2t[3 * xp + 2]};
+                    coulomb(e, gyx, ez);
+                }
             }
             __syncthreads();
             S.template fft_z<+1, R>(tile, twz, a);
@@ -348,7 +471,7 @@ __global__ void __launch_bounds__(Shape::kMaxThreads) tile_pass(PassArgs a) {
                 const int e = g << 2;
                 const int ex = e % S.tx, ey = (e / S.tx) % S.ty, ez = e / txy;
                 const long long r = ((long long)(z0 + ez) * S.n1 + (y0 + ey)) * S.n2 + (x0 + ex);
-                const cx<R>* v = tile + e;
+                const cx<R> v[4] = {tile[S.slot(e)], tile[S.slot(e + 1)], tile[S.slot(e + 2)], tile[S.slot(e + 3)]};
                 st4(accl + q.a * N + r, V4<R>{v[0].re * s, v[1].re * s, v[2].re * s, v[3].re * s});
                 if (q.c >= 0) st4(accl + q.c * N + r, V4<R>{v[0].im * s, v[1].im * s, v[2].im * s, v[3].im * s});
             }
@@ -356,8 +479,8 @@ __global__ void __launch_bounds__(Shape::kMaxThreads) tile_pass(PassArgs a) {
             for (int e = threadIdx.x; e < tile_elems; e += S.nt()) {
                 const int ex = e % S.tx, ey = (e / S.tx) % S.ty, ez = e / txy;
                 const long long r = ((long long)(z0 + ez) * S.n1 + (y0 + ey)) * S.n2 + (x0 + ex);
-                accl[q.a * N + r] = tile[e].re * s;
-                if (q.c >= 0) accl[q.c * N + r] = tile[e].im * s;
+                accl[q.a * N + r] = tile[S.slot(e)].re * s;
+                if (q.c >= 0) accl[q.c * N + r] = tile[S.slot(e)].im * s;
             }
         }
         return;
@@ -372,7 +495,7 @@ __global__ void __launch_bounds__(Shape::kMaxThreads) tile_pass(PassArgs a) {
             const int e = g << 2;
             const int ex = e % S.tx, ey = (e / S.tx) % S.ty, ez = e / txy;
             const long long r = ((long long)(z0 + ez) * S.n1 + (y0 + ey)) * S.n2 + (x0 + ex);
-            const cx<R>* v = tile + e;
+            const cx<R> v[4] = {tile[S.slot(e)], tile[S.slot(e + 1)], tile[S.slot(e + 2)], tile[S.slot(e + 3)]};
             const V4<R> v1 = {v[0].re, v[1].re, v[2].re, v[3].re};
             const V4<R> v2 = {v[0].im, v[1].im, v[2].im, v[3].im};
             const V4<R> la = ld4(fl + q.a * N + r), rb = ld4(fr + q.b * N + r);
@@ -394,7 +517,7 @@ __global__ void __launch_bounds__(Shape::kMaxThreads) tile_pass(PassArgs a) {
         for (int e = threadIdx.x; e < tile_elems; e += S.nt()) {
             const int ex = e % S.tx, ey = (e / S.tx) % S.ty, ez = e / txy;
             const long long r = ((long long)(z0 + ez) * S.n1 + (y0 + ey)) * S.n2 + (x0 + ex);
-            const cx<R> v = tile[e];
+            const cx<R> v = tile[S.slot(e)];
             const R la = fl[q.a * N + r], rb = fr[q.b * N + r];
             e1 += la * rb * v.re;
             R wa = v.re * rb;
