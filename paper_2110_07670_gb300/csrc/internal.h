@@ -73,7 +73,10 @@ struct PassShape {
 constexpr bool cube_supported(int n) {
     return n == 32 || n == 60 || n == 80 || n == 90 || n == 96 || n == 100 || n == 108 || n == 120 || n == 160;
 }
-constexpr int cube_xy_threads(int n) { return n * n >= 12000 ? 512 : 256; }
+// threads of a plane block: the butterfly counts of both stages divide evenly
+constexpr int cube_xy_threads(int n) {
+    return n == 32 ? 128 : n == 96 ? 384 : n == 120 ? 480 : n == 160 ? 320 : (n * n >= 12000 ? 512 : 256);
+}
 // Plane layout of N % 16 == 0 cubes: within each 16-element block of a row,
 // x position p sits in slot p ^ (((p >> 4) & 7) | ((y & 1) << 3)); the
 // permutation is its own inverse, keeps blocks in place, spreads the

@@ -111,6 +111,7 @@ __device__ __forceinline__ void chunk_at(const Shape& a, int k, int z0, int y0, 
 // Runtime tile geometry (any grid) ...
 struct DynShape {
     static constexpr int kMaxThreads = 512;
+    static constexpr int kMinBlocks = 1;
     int n0, n1, n2, tz, ty, tx, axes;
     __device__ explicit DynShape(const PassArgs& a)
         : n0(a.n0), n1(a.n1), n2(a.n2), tz(a.tz), ty(a.ty), tx(a.tx), axes(a.axes) {}
@@ -161,7 +162,6 @@ __device__ __forceinline__ void butterfly_at(cx<R>* row, const int (&idx)[RAD], 
 template <int RAD, int SGN, int N, int LB, int NT, typename R>
 __device__ __forceinline__ void static_stage_rows_swizzled(cx<R>* buf, const cx<R>* tw) {
     constexpr int M = LB / RAD, NB = N / RAD, TOTAL = NB * N, TS = N / LB;
-#pragma unroll 2
     for (int b = threadIdx.x; b < TOTAL; b += NT) {
         const int line = b / NB, i = b - line * NB;
         const int beta = i / M, j = i - beta * M;
@@ -179,7 +179,6 @@ __device__ __forceinline__ void static_stage_rows_swizzled(cx<R>* buf, const cx<
 template <int RAD, int SGN, int N, int LB, int NT, typename R>
 __device__ __forceinline__ void static_stage_cols_swizzled(cx<R>* buf, const cx<R>* tw) {
     constexpr int M = LB / RAD, NB = N / RAD, TOTAL = NB * N, TS = N / LB;
-#pragma unroll 2
     for (int b = threadIdx.x; b < TOTAL; b += NT) {
         const int i = b / N, p = b - i * N;
         const int beta = i / M, j = i - beta * M;
@@ -215,6 +214,7 @@ __device__ __forceinline__ void static_fft_rows_swizzled(cx<R>* buf, const cx<R>
 template <int N, int TZ, int TY, int TX, int NT>
 struct CubeShape {
     static constexpr int kMaxThreads = NT;
+    static constexpr int kMinBlocks = (TZ == 1 && TY == N && TX == N) ? 2 : 1;
     static constexpr int n0 = N, n1 = N, n2 = N, tz = TZ, ty = TY, tx = TX;
     static constexpr int axes = (TZ == 1 && TY == N && TX == N) ? 3 : (TZ == N ? 4 : (TZ == 1 && TX == N ? 1 : 2));
     // Plane tiles of N % 16 == 0 boxes are stored (in shared and global memory)
@@ -256,7 +256,7 @@ struct CubeShape {
 };
 
 template <typename Shape, typename R, int PRO, int EPI, int MID, int SGN>
-__global__ void __launch_bounds__(Shape::kMaxThreads) tile_pass(PassArgs a) {
+__global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pass(PassArgs a) {
     const Shape S(a);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
@@ -323,6 +323,20 @@ __global__ void __launch_bounds__(Shape::kMaxThreads) tile_pass(PassArgs a) {
     if (PRO != PRO_LOAD || EPI != EPI_STORE) q = a.quads[a.t0 + t];
     const R* fl = reinterpret_cast<const R*>(a.fl);
     const R* fr = reinterpret_cast<const R*>(a.fr);
+    if (EPI == EPI_ACCUM && S.tx == S.n2 && S.ty == S.n1 && threadIdx.x == 32) {
+        // the accumulation reads four function planes after the transforms:
+        // start pulling them into L2 now so the loads overlap the FFT stages
+        const long long off = (long long)z0 * S.n1 * S.n2;
+        const uint32_t bytes = (uint32_t)((long long)S.tz * S.n1 * S.n2 * sizeof(R));
+        if (bytes % 16 == 0) {
+            prefetch_l2(fl + q.a * N + off, bytes);
+            prefetch_l2(fr + q.b * N + off, bytes);
+            if (q.c >= 0) {
+                if (q.c != q.a) prefetch_l2(fl + q.c * N + off, bytes);
+                prefetch_l2(fr + q.d * N + off, bytes);
+            }
+        }
+    }
 
     // ---- prologue: global -> tile
     if (PRO == PRO_LOAD) {

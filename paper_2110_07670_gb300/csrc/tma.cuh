@@ -75,6 +75,11 @@ __device__ __forceinline__ void bulk_store(void* gdst, const void* smem_src, uin
 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
+// bring `bytes` at a 16-byte aligned global address into L2 (no shared memory, no completion)
+__device__ __forceinline__ void prefetch_l2(const void* gsrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gsrc), "r"(bytes) : "memory");
+}
+
 // wait until the committed bulk stores have finished reading shared memory
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
