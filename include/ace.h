@@ -142,6 +142,42 @@ int hfx_apply_exact(ace_plan* plan, const void* psi_occ, int n_occ, double alpha
                     void* Vx_psi, void* stream);
 
 /*
+ * Several independent systems (their own plans, sizes and pair lists) built
+ * in one call, the batching of independent ACE builds (each system is one
+ * ace_build, Section 2.2): the systems' work runs concurrently on streams
+ * forked from and joined back into `stream`.  Every plan must be on the same
+ * device and distinct.  On return each system carries its E_x and status
+ * (ACE_OK or the error ace_build would return); the call returns ACE_OK or the
+ * first error.
+ */
+typedef struct {
+    ace_plan* plan;               /* this system's plan */
+    const void* psi_G;            /* [n_occ][n_pw_half] device */
+    int n_occ;
+    double alpha;
+    const int32_t* pair_row_ptr;  /* host CSR of kept pairs, or NULL for all */
+    const int32_t* pair_col;
+    void* xi;                     /* [n_occ][n_pw_half] device output */
+    double E_x;                   /* output */
+    int status;                   /* output */
+} ace_system;
+
+int ace_build_batched(ace_system* systems, int n_sys, void* stream);
+
+/*
+ * Checkpoint of the ACE operator between MTS steps (the operator persists
+ * across the inner steps, Section 2.3): ace_save writes the vectors xi
+ * [n_occ][n_pw_half] (device) with the plan's grid, cell, cutoff, precision,
+ * alpha and E_x to a file; ace_load reads them back into xi (device, room for
+ * n_occ_max rows) for a plan of the same grid, cell, cutoff and precision,
+ * returning n_occ, alpha and E_x (alpha, E_x may be NULL).  Both synchronise
+ * the stream.  ACE_ERR_INVALID_ARG on I/O failure or a mismatched file.
+ */
+int ace_save(const char* path, const ace_plan* plan, const void* xi, int n_occ, double alpha, double E_x,
+             void* stream);
+int ace_load(const char* path, const ace_plan* plan, void* xi, int* n_occ, double* alpha, double* E_x, void* stream);
+
+/*
  * Intermediates of the last ace_build on this plan (for checking):
  *   W_G [n_occ][n_pw_half] device (alpha-scaled V_X Phi), may be NULL;
  *   M   [n_occ][n_occ] host doubles, may be NULL.  Synchronises the stream.

@@ -46,6 +46,7 @@ def _load():
             "orc_exchange": [P, i32, i32, P, P, P, f64, P, P, i32, P, P],
             "orc_exchange_timed": [P, i32, i32, P, P, P, f64, P, P, i32, P, P, P],
             "orc_vx_apply": [P, i32, P, i32, i32, P, P, P, f64, i32, P],
+            "orc_exchange_rows": [P, i32, i32, P, P, P, f64, P, P, i32, P, i32, P],
             "orc_pair_energy": [P, P, i32, P, P, P, P],
             "orc_to_real": [P, i32, i32, P, P, P, P],
             "orc_gamma_gram": [P, i32, P, i32, i32, P, P],
@@ -122,6 +123,20 @@ def exchange(psi, cell, grid, ecut, alpha, pairs=None, nthreads=0, times=False):
     _check(_load().orc_exchange_timed(_p(psi), n, npw, _p(m), _p(_grid(grid)), _p(_cell(cell)), float(alpha),
                                       _p(rp), _p(col), int(nthreads), _p(W), ctypes.byref(E), _p(t)))
     return (W, E.value, t) if times else (W, E.value)
+
+
+def exchange_rows(psi, cell, grid, ecut, alpha, rows, pairs=None, nthreads=0):
+    """Rows of W_G (alpha-scaled V_X phi_i restricted to the listed pairs) for
+    the requested orbitals only; equals exchange(...)[0][rows]."""
+    psi = _c128(psi)
+    m = half_sphere(cell, ecut)
+    n, npw = psi.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.zeros((len(rows), npw), dtype=np.complex128)
+    rp, col = _csr(pairs)
+    _check(_load().orc_exchange_rows(_p(psi), n, npw, _p(m), _p(_grid(grid)), _p(_cell(cell)), float(alpha),
+                                     _p(rp), _p(col), len(rows), _p(rows), int(nthreads), _p(out)))
+    return out
 
 
 def vx_apply(psi_occ, trials, cell, grid, ecut, alpha, nthreads=0):

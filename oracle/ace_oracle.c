@@ -426,6 +426,20 @@ static void to_recip_one(void *ctx, int i, cplx *box)
     to_recip(m->g, f, box, m->cout + (long)i * m->g->npw);
 }
 
+typedef struct {
+    const grid_t *g;
+    const cplx *c;
+    double *f;
+    const int32_t *list;
+} listmap_t;
+
+static void to_real_listed(void *ctx, int q, cplx *box)
+{
+    listmap_t *m = ctx;
+    int i = m->list[q];
+    to_real(m->g, m->c + (long)i * m->g->npw, box, m->f + (long)i * m->g->N);
+}
+
 static double wall(void)
 {
     struct timespec ts;
@@ -513,6 +527,76 @@ int orc_exchange_timed(const double *psi_G, int n_occ, int npw, const int32_t *m
         times[2] = wall() - t2;
     }
     free(phi);
+    free(acc);
+    free(box);
+    return ORC_OK;
+}
+
+/*
+ * Rows of the (possibly screened) exchange: for each requested orbital i,
+ * W_G[i] = -alpha sum_{j : (min(i,j), max(i,j)) listed} v_ij phi_j on the half
+ * sphere (Eq. 2 restricted to the kept pairs), the same quantity as row i of
+ * orc_exchange's W_G, computed from the orbitals those rows need only.
+ * row_ptr/col: CSR of kept pairs i <= j, or NULL for every pair.
+ */
+int orc_exchange_rows(const double *psi_G, int n_occ, int npw, const int32_t *miller, const int grid[3],
+                      const double cell[9], double alpha, const int32_t *row_ptr, const int32_t *col, int nrows,
+                      const int32_t *rows, int nthreads, double *W_rows)
+{
+    grid_t g;
+    int st = grid_init(&g, grid, cell, npw, miller);
+    if (st) return st;
+    if (n_occ < 1 || nrows < 1) return ORC_ERR_ARG;
+    for (int k = 0; k < nrows; ++k)
+        if (rows[k] < 0 || rows[k] >= n_occ) return ORC_ERR_ARG;
+    long N = g.N;
+    /* pairs (row k, orbital j) with (min, max) in the list */
+    int32_t *pa = malloc(sizeof(int32_t) * (long)nrows * n_occ), *pb = malloc(sizeof(int32_t) * (long)nrows * n_occ);
+    char *need = calloc(n_occ, 1);
+    long np = 0;
+    for (int k = 0; k < nrows; ++k) {
+        int i = rows[k];
+        need[i] = 1;
+        for (int j = 0; j < n_occ; ++j) {
+            int lo = i < j ? i : j, hi = i < j ? j : i, kept = 1;
+            if (row_ptr) {
+                kept = 0;
+                for (int32_t t = row_ptr[lo]; t < row_ptr[lo + 1]; ++t)
+                    if (col[t] == hi) kept = 1;
+            }
+            if (kept) {
+                pa[np] = k;
+                pb[np] = j;
+                need[j] = 1;
+                ++np;
+            }
+        }
+    }
+    /* real-space orbitals: only those the rows touch (others stay zero) */
+    double *phi = calloc((size_t)N * n_occ, sizeof(double)), *f = malloc(sizeof(double) * N * nrows);
+    double *acc = calloc((size_t)N * nrows, sizeof(double));
+    int nneed = 0;
+    for (int j = 0; j < n_occ; ++j) nneed += need[j];
+    int32_t *list = malloc(sizeof(int32_t) * (nneed > 0 ? nneed : 1));
+    for (int j = 0, q = 0; j < n_occ; ++j)
+        if (need[j]) list[q++] = j;
+    cplx *box = malloc(sizeof(cplx) * N);
+    listmap_t lm = {.g = &g, .c = (const cplx *)psi_G, .f = phi, .list = list};
+    parallel_for(nneed, nthreads, N, to_real_listed, &lm);
+    for (int k = 0; k < nrows; ++k) memcpy(f + (long)k * N, phi + (long)rows[k] * N, sizeof(double) * N);
+    pthread_mutex_t *locks = new_locks(nrows);
+    xwork_t w = {.g = &g, .left = f, .right = phi, .acc_left = acc, .acc_right = NULL, .symmetric = 0,
+                 .pa = pa, .pb = pb, .npairs = np, .lock_left = locks, .lock_right = NULL};
+    run_pairs(&w, nthreads);
+    free_locks(locks, nrows);
+    map_t m = {.g = &g, .f = acc, .cout = (cplx *)W_rows, .scale = -alpha};
+    parallel_for(nrows, nthreads, N, to_recip_one, &m);
+    free(pa);
+    free(pb);
+    free(need);
+    free(list);
+    free(phi);
+    free(f);
     free(acc);
     free(box);
     return ORC_OK;

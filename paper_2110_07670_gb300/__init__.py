@@ -22,7 +22,8 @@ ACE_MIXED = 1
 _ERRORS = {-1: "ACE_ERR_INVALID_ARG", -2: "ACE_ERR_GRID_TOO_SMALL", -3: "ACE_ERR_NOT_POSDEF", -4: "ACE_ERR_OOM",
            -5: "ACE_ERR_CUDA", -6: "ACE_ERR_TIMEOUT"}
 SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_apply", "hfx_apply_exact",
-           "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc")
+           "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc",
+           "ace_build_batched", "ace_save", "ace_load")
 
 _lib = None
 
@@ -31,6 +32,12 @@ class AceError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
         self.code = code
+
+
+class _System(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("psi_G", ctypes.c_void_p), ("n_occ", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("pair_row_ptr", ctypes.c_void_p), ("pair_col", ctypes.c_void_p),
+                ("xi", ctypes.c_void_p), ("E_x", ctypes.c_double), ("status", ctypes.c_int)]
 
 
 class _Opts(ctypes.Structure):
@@ -72,6 +79,9 @@ def load(build_if_missing=False):
     lib.hfx_apply_exact.argtypes = [P, P, i32, f64, P, i32, P, P]
     lib.ace_last_intermediates.argtypes = [P, P, P, P]
     lib.ace_set_timing.argtypes = [P, i32]
+    lib.ace_build_batched.argtypes = [ctypes.POINTER(_System), i32, P]
+    lib.ace_save.argtypes = [ctypes.c_char_p, P, P, i32, f64, f64, P]
+    lib.ace_load.argtypes = [ctypes.c_char_p, P, P, ctypes.POINTER(i32), ctypes.POINTER(f64), ctypes.POINTER(f64), P]
     lib.ace_get_stats.argtypes = [P, ctypes.POINTER(_Stats)]
     lib.ace_last_error.argtypes = [ctypes.c_char_p, i32]
     for name in SYMBOLS:
@@ -246,3 +256,46 @@ def ace_apply_noalloc(xi, psi, out, stream=None):
     _check(load().ace_apply_noalloc(_ptr(xi), xi.shape[0], _ptr(psi), psi.shape[0], xi.shape[1], prec, _ptr(out),
                                     _stream(stream)))
     return out
+
+
+def ace_build_batched(systems, stream=None):
+    """Build several independent systems in one call.  systems: list of dicts
+    with plan, psi_G, alpha and optionally pairs (row_ptr, col).  Returns a list
+    of (xi, E_x); raises on the first failing system."""
+    import torch
+    arr = (_System * len(systems))()
+    keep = []
+    outs = []
+    for k, s in enumerate(systems):
+        plan = s["plan"]
+        psi = plan._vec(s["psi_G"], "psi_G")
+        xi = torch.empty_like(psi)
+        rp = col = None
+        if s.get("pairs") is not None:
+            rp = np.ascontiguousarray(s["pairs"][0], dtype=np.int32)
+            col = np.ascontiguousarray(s["pairs"][1], dtype=np.int32)
+            keep += [rp, col]
+        arr[k] = _System(plan.handle.value, psi.data_ptr(), psi.shape[0], float(s["alpha"]),
+                         rp.ctypes.data if rp is not None else None, col.ctypes.data if col is not None else None,
+                         xi.data_ptr(), 0.0, 0)
+        outs.append(xi)
+    _check(load().ace_build_batched(arr, len(systems), _stream(stream)))
+    return [(outs[k], arr[k].E_x) for k in range(len(systems))]
+
+
+def ace_save(plan, path, xi, alpha, E_x, stream=None):
+    plan._vec(xi, "xi")
+    _check(load().ace_save(os.fsencode(path), plan.handle, _ptr(xi), xi.shape[0], float(alpha), float(E_x),
+                           _stream(stream)))
+
+
+def ace_load(plan, path, stream=None):
+    """(xi, alpha, E_x) saved by ace_save for a plan of the same geometry."""
+    import torch
+    buf = torch.empty((plan.n_occ_max, plan.n_pw_half), dtype=plan.cdtype, device="cuda")
+    n = ctypes.c_int(0)
+    a = ctypes.c_double(0)
+    e = ctypes.c_double(0)
+    _check(load().ace_load(os.fsencode(path), plan.handle, _ptr(buf), ctypes.byref(n), ctypes.byref(a),
+                           ctypes.byref(e), _stream(stream)))
+    return buf[:n.value].clone(), a.value, e.value

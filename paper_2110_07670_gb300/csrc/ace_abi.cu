@@ -114,6 +114,12 @@ struct ace_plan {
     double* d_C = nullptr;
     size_t C_cap = 0;
     int last_n_occ = 0;
+    int pending_n_occ = 0;
+    struct Result {
+        int status;
+        double E;
+    };
+    Result* h_res = nullptr;  // pinned host slots for the asynchronous build result
     // timing: events recorded at phase boundaries; each interval belongs to the
     // phase of the event that opens it (PH_IDLE closes a call)
     bool timing = false;
@@ -421,10 +427,11 @@ int upload_quads(ace_plan* P, const std::vector<Quad>& q, cudaStream_t st) {
     return ACE_OK;
 }
 
+// Enqueue one ACE build on stream st (inputs already validated for the Gamma
+// point); the status and E_x land in the plan's pinned host slots.
 template <typename R>
-int build_impl(ace_plan* P, const void* psi_G, int n_occ, double alpha, const int32_t* rp, const int32_t* col,
-               void* xi, double* E_x, cudaStream_t st) {
-    ACE_TRY(check_gamma<R>(P, psi_G, n_occ, st));
+int build_enqueue(ace_plan* P, const void* psi_G, int n_occ, double alpha, const int32_t* rp, const int32_t* col,
+                  void* xi, cudaStream_t st) {
     std::vector<int> pa, pb;
     if (rp) {
         if (rp[0] != 0) return fail(ACE_ERR_INVALID_ARG, "pair_row_ptr[0] must be 0");
@@ -469,16 +476,28 @@ int build_impl(ace_plan* P, const void* psi_G, int n_occ, double alpha, const in
     mark(P, PH_XI, st);
     ACE_CKL(launch_gemm_nn<R>(P->d_Linv, n_occ, n_occ, (const R*)WG, 2LL * P->npw, 1.0, (R*)xi, true, st));
     mark(P, PH_IDLE, st);
-    int status = 0;
-    double E = 0;
-    ACE_CK(cudaMemcpyAsync(&status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    ACE_CK(cudaMemcpyAsync(&E, P->d_E, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaMemcpyAsync(&P->h_res->status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaMemcpyAsync(&P->h_res->E, P->d_E, sizeof(double), cudaMemcpyDeviceToHost, st));
+    P->pending_n_occ = n_occ;
+    return ACE_OK;
+}
+
+// Wait for an enqueued build and report its result.
+int build_finish(ace_plan* P, double* E_x, cudaStream_t st) {
     ACE_CK(cudaStreamSynchronize(st));
     ACE_TRY(check_device_error(P, st));
-    P->last_n_occ = n_occ;
-    if (E_x) *E_x = E;
-    if (status) return fail(ACE_ERR_NOT_POSDEF, "-M is not positive definite (dependent or zero orbitals)");
+    P->last_n_occ = P->pending_n_occ;
+    if (E_x) *E_x = P->h_res->E;
+    if (P->h_res->status) return fail(ACE_ERR_NOT_POSDEF, "-M is not positive definite (dependent or zero orbitals)");
     return ACE_OK;
+}
+
+template <typename R>
+int build_impl(ace_plan* P, const void* psi_G, int n_occ, double alpha, const int32_t* rp, const int32_t* col,
+               void* xi, double* E_x, cudaStream_t st) {
+    ACE_TRY(check_gamma<R>(P, psi_G, n_occ, st));
+    ACE_TRY(build_enqueue<R>(P, psi_G, n_occ, alpha, rp, col, xi, st));
+    return build_finish(P, E_x, st);
 }
 
 template <typename R>
@@ -532,6 +551,7 @@ int apply_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, v
 }
 
 void free_plan(ace_plan* P) {
+    if (P->h_res) cudaFreeHost(P->h_res);
     for (auto& m : P->marks) cudaEventDestroy(m.second);
     for (auto e : P->ev_pool) cudaEventDestroy(e);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
@@ -609,6 +629,11 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     ACE_TRY(dalloc((void**)&P->d_E, sizeof(double)));
     ACE_TRY(dalloc((void**)&P->d_status, sizeof(int)));
     ACE_TRY(dalloc((void**)&P->d_err, sizeof(int)));
+    if (cudaMallocHost((void**)&P->h_res, sizeof(ace_plan::Result)) != cudaSuccess) {
+        cudaGetLastError();
+        P->h_res = nullptr;
+        return fail(ACE_ERR_OOM, "pinned host allocation failed");
+    }
     ACE_CK(cudaMemset(P->d_err, 0, sizeof(int)));
     return ACE_OK;
 }
@@ -698,6 +723,139 @@ int hfx_apply_exact(ace_plan* plan, const void* psi_occ, int n_occ, double alpha
     cudaStream_t st = (cudaStream_t)stream;
     return plan->prec == ACE_FP64 ? hfx_impl<double>(plan, psi_occ, n_occ, alpha, psi, T, Vx_psi, st)
                                   : hfx_impl<float>(plan, psi_occ, n_occ, alpha, psi, T, Vx_psi, st);
+}
+
+int ace_build_batched(ace_system* sys, int n_sys, void* stream) {
+    if (n_sys < 0 || (n_sys > 0 && !sys)) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (n_sys == 0) return ACE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < n_sys; ++i) {
+        ace_system& s = sys[i];
+        s.E_x = 0;
+        s.status = ACE_ERR_INVALID_ARG;
+        if (!s.plan || !s.psi_G || !s.xi || s.n_occ < 1 || s.n_occ > s.plan->n_occ_max ||
+            (s.pair_row_ptr == nullptr) != (s.pair_col == nullptr))
+            return fail(ACE_ERR_INVALID_ARG, "system " + std::to_string(i) + ": invalid arguments");
+        if (s.plan->dev != sys[0].plan->dev) return fail(ACE_ERR_INVALID_ARG, "systems on different devices");
+        for (int j = 0; j < i; ++j)
+            if (sys[j].plan == s.plan) return fail(ACE_ERR_INVALID_ARG, "each system needs its own plan");
+    }
+    DeviceGuard g(sys[0].plan->dev);
+    for (int i = 0; i < n_sys; ++i) {
+        ace_system& s = sys[i];
+        s.status = s.plan->prec == ACE_FP64 ? check_gamma<double>(s.plan, s.psi_G, s.n_occ, st)
+                                            : check_gamma<float>(s.plan, s.psi_G, s.n_occ, st);
+        if (s.status != ACE_OK) return s.status;
+    }
+    // one stream per system, forked from and joined back into the caller's stream
+    std::vector<cudaStream_t> ss(n_sys, nullptr);
+    std::vector<cudaEvent_t> done(n_sys, nullptr);
+    cudaEvent_t fork = nullptr;
+    int rc = ACE_OK;
+    auto cleanup = [&]() {
+        for (auto s : ss)
+            if (s) cudaStreamDestroy(s);
+        for (auto e : done)
+            if (e) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+    };
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(fork, st) != cudaSuccess) {
+        cleanup();
+        return fail(ACE_ERR_CUDA, "event setup failed");
+    }
+    for (int i = 0; i < n_sys && rc == ACE_OK; ++i) {
+        ace_system& s = sys[i];
+        if (cudaStreamCreateWithFlags(&ss[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamWaitEvent(ss[i], fork, 0) != cudaSuccess) {
+            rc = fail(ACE_ERR_CUDA, "stream setup failed");
+            break;
+        }
+        s.status = s.plan->prec == ACE_FP64
+                       ? build_enqueue<double>(s.plan, s.psi_G, s.n_occ, s.alpha, s.pair_row_ptr, s.pair_col, s.xi, ss[i])
+                       : build_enqueue<float>(s.plan, s.psi_G, s.n_occ, s.alpha, s.pair_row_ptr, s.pair_col, s.xi, ss[i]);
+        if (s.status != ACE_OK) rc = s.status;
+        cudaEventRecord(done[i], ss[i]);
+    }
+    for (int i = 0; i < n_sys; ++i) {
+        if (!ss[i]) continue;
+        ace_system& s = sys[i];
+        if (s.status == ACE_OK) {
+            s.status = build_finish(s.plan, &s.E_x, ss[i]);
+            if (s.status != ACE_OK && rc == ACE_OK) rc = s.status;
+        } else {
+            cudaStreamSynchronize(ss[i]);
+        }
+        cudaStreamWaitEvent(st, done[i], 0);
+    }
+    cleanup();
+    return rc;
+}
+
+namespace {
+const char kSaveMagic[8] = {'A', 'C', 'E', 'X', 'I', '0', '0', '1'};
+struct SaveHeader {
+    char magic[8];
+    int32_t precision, grid[3], n_occ, n_pw_half;
+    double cell[9], ecut, alpha, E_x;
+};
+}  // namespace
+
+int ace_save(const char* path, const ace_plan* plan, const void* xi, int n_occ, double alpha, double E_x,
+             void* stream) {
+    if (!path || !plan || !xi || n_occ < 1 || n_occ > plan->n_occ_max)
+        return fail(ACE_ERR_INVALID_ARG, "ace_save: invalid arguments");
+    DeviceGuard g(plan->dev);
+    const size_t bytes = (size_t)n_occ * plan->npw * 2 * plan->esz;
+    std::vector<char> buf(bytes);
+    ACE_CK(cudaMemcpyAsync(buf.data(), xi, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    ACE_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    SaveHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kSaveMagic, 8);
+    h.precision = plan->prec;
+    for (int d = 0; d < 3; ++d) h.grid[d] = plan->n[d];
+    h.n_occ = n_occ;
+    h.n_pw_half = plan->npw;
+    std::memcpy(h.cell, plan->cell, sizeof(h.cell));
+    h.ecut = plan->ecut;
+    h.alpha = alpha;
+    h.E_x = E_x;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(ACE_ERR_INVALID_ARG, std::string("ace_save: cannot open ") + path);
+    const bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(buf.data(), 1, bytes, f) == bytes;
+    if (std::fclose(f) != 0 || !ok) return fail(ACE_ERR_INVALID_ARG, std::string("ace_save: write failed: ") + path);
+    return ACE_OK;
+}
+
+int ace_load(const char* path, const ace_plan* plan, void* xi, int* n_occ, double* alpha, double* E_x, void* stream) {
+    if (!path || !plan || !xi || !n_occ) return fail(ACE_ERR_INVALID_ARG, "ace_load: invalid arguments");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(ACE_ERR_INVALID_ARG, std::string("ace_load: cannot open ") + path);
+    SaveHeader h;
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kSaveMagic, 8) != 0) {
+        std::fclose(f);
+        return fail(ACE_ERR_INVALID_ARG, "ace_load: not an ACE vector file");
+    }
+    bool same = h.precision == plan->prec && h.n_pw_half == plan->npw && h.ecut == plan->ecut;
+    for (int d = 0; d < 3; ++d) same = same && h.grid[d] == plan->n[d];
+    for (int d = 0; d < 9; ++d) same = same && h.cell[d] == plan->cell[d];
+    if (!same || h.n_occ < 1 || h.n_occ > plan->n_occ_max) {
+        std::fclose(f);
+        return fail(ACE_ERR_INVALID_ARG, "ace_load: file was saved for another grid, cell, cutoff, precision or size");
+    }
+    const size_t bytes = (size_t)h.n_occ * plan->npw * 2 * plan->esz;
+    std::vector<char> buf(bytes);
+    const bool ok = std::fread(buf.data(), 1, bytes, f) == bytes;
+    std::fclose(f);
+    if (!ok) return fail(ACE_ERR_INVALID_ARG, "ace_load: truncated file");
+    DeviceGuard g(plan->dev);
+    ACE_CK(cudaMemcpyAsync(xi, buf.data(), bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    ACE_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    *n_occ = h.n_occ;
+    if (alpha) *alpha = h.alpha;
+    if (E_x) *E_x = h.E_x;
+    return ACE_OK;
 }
 
 int ace_last_intermediates(ace_plan* plan, void* W_G, double* M, void* stream) {

@@ -1,0 +1,150 @@
+"""Parity at the workloads' full sizes, in the launch configuration bench.py
+times (mixed precision, default plan), on outputs the oracle can compute one
+by one, plus properties that hold at any size:
+
+* sampled rows of W = alpha V_X Phi (Eq. 2) against the FP64 oracle;
+* M = Phi^T W recomputed in FP64 on the host from the GPU's W;
+* E_x (Eq. 4) = tr(M), and the oracle's row energies <phi_i|W_i> = M_ii;
+* K psi (Eq. 5) against the independent FP64 route W M^-1 W^T psi built from
+  the GPU's W and M, and ACE exactness K phi_i = W_i (unscreened);
+* the batched multi-system build against single builds and the oracle;
+* checkpoint save / load of the ACE vectors.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+import paper_2110_07670_gb300 as ace
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a, plan):
+    dt = np.complex64 if plan.prec == ace.ACE_MIXED else np.complex128
+    return torch.from_numpy(np.ascontiguousarray(a.astype(dt))).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2110_07670_gb300 import build
+    build.build_library()
+    ace.load()
+
+
+def check_full(cfg, rows, pairs=None, n_trials=8):
+    n = len(cfg["psi"])
+    plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, "mixed")
+    xi, E = ace.ace_build(plan, dev(cfg["psi"], plan), cfg["alpha"], pairs=pairs)
+    W, M = ace.ace_last_intermediates(plan, n)
+    Wh = host(W)
+    m = oracle.half_sphere(cfg["cell"], cfg["ecut"])
+    # sampled rows of W against the oracle
+    Wref = oracle.exchange_rows(cfg["psi"], cfg["cell"], cfg["grid"], cfg["ecut"], cfg["alpha"], rows, pairs=pairs)
+    assert rel(Wh[rows], Wref) <= 2e-6
+    # their row energies
+    e_ref = np.array([oracle.gamma_gram(cfg["psi"][i], Wref[k], m)[0, 0] for k, i in enumerate(rows)])
+    assert np.abs(np.diag(M)[rows] - e_ref).max() / cfg["n_atom"] <= 1e-6
+    # M from the GPU's W, in FP64 on the host
+    Mh = oracle.gamma_gram(cfg["psi"], Wh, m)
+    assert np.abs(M - Mh).max() <= 1e-6 * np.abs(Mh).max()
+    # E_x = tr(M)
+    assert abs(E - np.trace(M)) / cfg["n_atom"] <= 1e-6
+    # K psi against W sym(M)^-1 W^T psi in FP64 (the symmetric part is what is factored)
+    tr = gen.random_trials(cfg["cell"], cfg["ecut"], n_trials, seed=909)
+    K = host(ace.ace_apply(plan, xi, dev(tr, plan)))
+    Kref = oracle.ace_apply_lu(Wh, 0.5 * (M + M.T), tr, m)
+    assert rel(K, Kref) <= 1e-6
+    if pairs is None:
+        Kphi = host(ace.ace_apply(plan, xi, dev(cfg["psi"][rows], plan)))
+        assert rel(Kphi, Wh[rows]) <= 2e-6
+    plan.close()
+    return E
+
+
+def test_water32_full_size():
+    """128 orbitals, 96^3, the bench workload."""
+    check_full(gen.config_water32(), rows=[0, 77, 127])
+
+
+def test_water64_full_size():
+    """256 orbitals, 120^3, with one of its trial sets."""
+    cfg = gen.config_water64(n_trial_sets=1, T=8)
+    check_full(cfg, rows=[131])
+
+
+def test_localized_screened_full_size():
+    """512 localised orbitals, 160^3, pairs with centre distance < 8 bohr."""
+    cfg = gen.config_localized()
+    check_full(cfg, rows=[0, 300], pairs=cfg["pairs"])
+
+
+def _small_systems():
+    out = []
+    for k, (L, n, g) in enumerate([(7.0, 5, 16), (8.0, 7, 18), (6.5, 3, 16)]):
+        cell = gen.cubic_cell(L)
+        out.append(dict(cell=cell, ecut=14.0, grid=(g, g, g), alpha=0.25,
+                        psi=gen.random_orbitals(cell, 14.0, n, seed=70 + k), n_atom=3 * n / 4))
+    return out
+
+
+def test_batched_small_against_oracle_and_single_builds():
+    systems = _small_systems()
+    plans = [ace.Plan(s["grid"], s["cell"], s["ecut"], len(s["psi"]), "mixed") for s in systems]
+    res = ace.ace_build_batched([dict(plan=p, psi_G=dev(s["psi"], p), alpha=s["alpha"])
+                                 for p, s in zip(plans, systems)])
+    for (xi, E), p, s in zip(res, plans, systems):
+        ref = oracle.ace_build(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+        assert abs(E - ref["E_x"]) / s["n_atom"] <= 1e-6
+        tr = gen.random_trials(s["cell"], s["ecut"], 4, seed=3)
+        K = host(ace.ace_apply(p, xi, dev(tr, p)))
+        assert rel(K, oracle.ace_apply(ref["xi"], tr, ref["miller"])) <= 1e-6
+        xi1, E1 = ace.ace_build(p, dev(s["psi"], p), s["alpha"])
+        assert abs(E1 - E) / s["n_atom"] <= 1e-7
+
+
+def test_batched_sixteen_uneven_systems():
+    """The 16 uneven cells of the batched workload in one call: each system's
+    E_x = tr(M) and K psi against the FP64 route from its own W and M."""
+    systems = gen.batched_systems()
+    plans = [ace.Plan(s["grid"], s["cell"], s["ecut"], len(s["psi"]), "mixed") for s in systems]
+    res = ace.ace_build_batched([dict(plan=p, psi_G=dev(s["psi"], p), alpha=s["alpha"])
+                                 for p, s in zip(plans, systems)])
+    for k in (0, 3, 15):
+        (xi, E), p, s = res[k], plans[k], systems[k]
+        n = len(s["psi"])
+        W, M = ace.ace_last_intermediates(p, n)
+        assert abs(E - np.trace(M)) / s["n_atom"] <= 1e-6
+        m = oracle.half_sphere(s["cell"], s["ecut"])
+        tr = gen.random_trials(s["cell"], s["ecut"], 4, seed=4)
+        K = host(ace.ace_apply(p, xi, dev(tr, p)))
+        assert rel(K, oracle.ace_apply_lu(host(W), 0.5 * (M + M.T), tr, m)) <= 1e-6
+    for p in plans:
+        p.close()
+
+
+def test_save_load_roundtrip():
+    cfg = gen.config_small()
+    plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], 8, "mixed")
+    xi, E = ace.ace_build(plan, dev(cfg["psi"], plan), cfg["alpha"])
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "xi.ace")
+        ace.ace_save(plan, path, xi, cfg["alpha"], E)
+        plan2 = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], 8, "mixed")
+        xi2, a2, E2 = ace.ace_load(plan2, path)
+        assert torch.equal(xi, xi2) and a2 == cfg["alpha"] and E2 == E
+        other = ace.Plan((36, 36, 36), cfg["cell"], cfg["ecut"], 8, "mixed")
+        with pytest.raises(ace.AceError):
+            ace.ace_load(other, path)

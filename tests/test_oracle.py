@@ -282,3 +282,20 @@ def test_grid_too_small_rejected():
     psi = gen.random_orbitals(cell, 30.0, 2, seed=1)
     with pytest.raises(RuntimeError):
         oracle.exchange(psi, cell, (12, 12, 12), 30.0, 0.25)
+
+
+def test_exchange_rows_match_full_exchange(small):
+    s = small
+    n = len(s["psi"])
+    W, _ = oracle.exchange(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    Wr = oracle.exchange_rows(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"], [3, 0])
+    assert np.abs(Wr - W[[3, 0]]).max() < 1e-16
+    rng = np.random.default_rng(8)
+    row_ptr, cols = [0], []
+    for i in range(n):
+        cols += [j for j in range(i, n) if j == i or rng.random() < 0.5]
+        row_ptr.append(len(cols))
+    pairs = (np.array(row_ptr, dtype=np.int32), np.array(cols, dtype=np.int32))
+    Ws, _ = oracle.exchange(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"], pairs=pairs)
+    Wr = oracle.exchange_rows(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"], [1, 4, 2], pairs=pairs)
+    assert np.abs(Wr - Ws[[1, 4, 2]]).max() < 1e-16
