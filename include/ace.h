@@ -70,7 +70,8 @@ typedef struct ace_plan ace_plan;
 
 typedef struct {
     int pair_batch;    /* packed pair transforms per pass launch; 0 = automatic */
-    int deterministic; /* reserved: 1 = atomic-free accumulation of W */
+    int kernels;       /* 0: fastest available; 1: CUDA-core Gram products instead of
+                          tcgen05 tensor cores; 2: also generic (runtime-size) FFT passes */
 } ace_opts;
 
 /*

@@ -88,6 +88,7 @@ struct ace_plan {
     int* d_freq[3] = {nullptr, nullptr, nullptr};
     bool fused_xy = false;
     bool cube_kernels = true;  // compile-time kernels for supported N^3 boxes
+    bool tensor_gram = false;  // Gram products on tcgen05 tensor cores (single precision)
     PassShape s_xy{}, s_x{}, s_y{}, s_z{};
     int ntiles_last = 1;  // tiles of the pass that accumulates W
     int batch = 1;
@@ -370,11 +371,20 @@ int run_pairs(ace_plan* P, const R* fl, const R* fr, R* accl, R* accr, int symme
 template <typename R>
 int gram(ace_plan* P, const cx<R>* A, int m, const cx<R>* B, int n, double* G, cudaStream_t st) {
     const long long K = 2LL * P->npw;
+    mark(P, PH_GRAM, st);
+    if constexpr (sizeof(R) == 4) {
+        if (P->tensor_gram) {
+            const int nchunk = gram_umma_chunks(K);
+            ACE_TRY(grow(&P->d_part, &P->part_cap, (size_t)nchunk * m * n));
+            ACE_CKL(launch_gram_partial_umma((const float*)A, (const float*)B, m, n, K, P->d_part, P->d_err, st));
+            ACE_CKL(launch_gram_finish<R>(P->d_part, nchunk, (const R*)A, (const R*)B, m, n, K, G, n, st));
+            return ACE_OK;
+        }
+    }
     const int tiles = ((m + 63) / 64) * ((n + 63) / 64);
     int nchunk = std::max(1, (2 * 152 + tiles - 1) / tiles);
     nchunk = (int)std::min<long long>(nchunk, std::max<long long>(1, K / 256));
     ACE_TRY(grow(&P->d_part, &P->part_cap, (size_t)nchunk * m * n));
-    mark(P, PH_GRAM, st);
     ACE_CKL(launch_gram_partial<R>((const R*)A, (const R*)B, m, n, K, nchunk, P->d_part, st));
     ACE_CKL(launch_gram_finish<R>(P->d_part, nchunk, (const R*)A, (const R*)B, m, n, K, G, n, st));
     return ACE_OK;
@@ -588,7 +598,8 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
         ACE_TRY(dalloc((void**)&P->d_freq[d], P->n[d] * sizeof(int)));
         ACE_CK(cudaMemcpy(P->d_freq[d], fr.data(), P->n[d] * sizeof(int), cudaMemcpyHostToDevice));
     }
-    if (opts && opts->deterministic == 2) P->cube_kernels = false;  // generic kernels only (testing)
+    if (opts && opts->kernels >= 2) P->cube_kernels = false;  // generic runtime-size FFT passes
+    P->tensor_gram = !(opts && opts->kernels >= 1) && sizeof(R) == 4;
     ACE_TRY(setup_shapes<R>(P));
     // the compile-time plane kernels of N % 16 == 0 boxes keep x swizzled per row
     const bool swz = P->s_xy.cube && cube_swizzle(P->n[2]);

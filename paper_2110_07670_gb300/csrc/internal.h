@@ -123,6 +123,11 @@ cudaError_t launch_gather(const cx<R>* box, const Quad* quads, int t0, int batch
 template <typename R>
 cudaError_t launch_gram_partial(const R* A, const R* B, int m, int n, long long K, int nchunk, double* P,
                                 cudaStream_t st);
+// The same partials on tcgen05 tensor cores (split TF32, FP32 accumulation in
+// TMEM), gram_umma_chunks(K) K-slices; err: device error flag for bounded waits.
+int gram_umma_chunks(long long K);
+cudaError_t launch_gram_partial_umma(const float* A, const float* B, int m, int n, long long K, double* P, int* err,
+                                     cudaStream_t st);
 // G[i][j] = 2 sum_c P[c][i][j] - (A_i0 B_j0 + A_i1 B_j1)   (G = 0 counted once)
 template <typename R>
 cudaError_t launch_gram_finish(const double* P, int nchunk, const R* A, const R* B, int m, int n, long long K,

@@ -1,0 +1,219 @@
+// umma_gram.cu -- Gamma-point Gram partials on the 5th-generation tensor cores.
+//
+// G = A B^T over the real views of two sets of plane-wave vectors (K = 2
+// n_pw_half reals per row): M = Phi^T W of the ACE construction and
+// C = psi^T xi of the ACE apply (arXiv:2110.07670 Section 2.2, Eq. 5).
+// Split precision: every FP32 operand x is split into x_hi = tf32(x) and
+// x_lo = tf32(x - x_hi), and the four products hi.hi + hi.lo + lo.hi + lo.lo
+// are accumulated in FP32 in tensor memory (TMEM) by tcgen05.mma kind::tf32,
+// which carries the product to about 2^-22 of |a||b|.  Each thread block owns
+// a 128 x 128 output tile and one 256-wide slice of K; its partial is written
+// in double precision and the slices are summed in double by
+// launch_gram_finish (la.cu), as for the SIMT path.
+//
+// Data movement: the block's threads load 128 x 32 FP32 slices of both
+// operands as 8-byte vectors (rows of n_pw_half complex numbers are only
+// 8-byte aligned, so tensor-map copies do not apply), split them and store
+// hi / lo in the K-major 128-byte swizzle layout of a two-stage ring; one
+// thread issues the MMAs and commits them to an mbarrier; tcgen05.ld drains
+// the accumulator.  Every wait is bounded in time and sets the plan's device
+// error flag when it gives up.
+#include <cstdio>
+
+#include "internal.h"
+#include "tma.cuh"
+
+namespace ace {
+
+namespace {
+
+constexpr int TM = 128, TN = 128, TK = 32;   // output tile, K per stage (one 128-byte swizzle row)
+constexpr int KCHUNK = 256;                   // K per block
+constexpr int STAGES = 2;
+constexpr int TILE_BYTES = TM * TK * 4;       // 16 KB, same for A and B (TN == TM)
+constexpr uint32_t TMEM_COLS = 128;
+
+struct __align__(1024) GramSmem {
+    float a_hi[STAGES][TM * TK];
+    float a_lo[STAGES][TM * TK];
+    float b_hi[STAGES][TN * TK];
+    float b_lo[STAGES][TN * TK];
+    uint64_t mma_done[STAGES];
+    uint32_t tmem_base;
+    int abort;
+};
+
+// K-major operand in the 128-byte swizzle layout: rows of 128 bytes, 8-row
+// groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
+    const uint32_t a = smem_addr(p);
+    return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// instruction descriptor: D f32, A/B tf32, both K-major, M = TM, N = TN
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+constexpr int NTHR = 256;
+
+// Byte offset of element (row, k) of a 128-row x 32-float K-major tile in the
+// 128-byte swizzle layout: 16-byte chunk c of row r sits at chunk c ^ (r % 8).
+__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
+    return (uint32_t)(row * 128 + ((k * 4) ^ ((row & 7) << 4)));
+}
+
+__global__ void __launch_bounds__(NTHR, 1)
+    gram_partial_umma(const float* __restrict__ A, const float* __restrict__ B, int m, int n, long long K,
+                      double* __restrict__ P, int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    GramSmem& sm = *reinterpret_cast<GramSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TN;
+    const long long k0 = (long long)blockIdx.z * KCHUNK;
+    const int nst = (int)(((K - k0 < KCHUNK ? K - k0 : KCHUNK) + TK - 1) / TK);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&sm.mma_done[s], 1);
+        sm.abort = 0;
+        fence_mbar_init();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sm.tmem_base;
+
+    int committed = 0;
+    for (int s = 0; s < nst; ++s) {
+        const int buf = s & 1;
+        // the buffer was last read by the MMAs of stage s - 2
+        if (s >= 2 && !mbar_wait_bounded(&sm.mma_done[buf], ((s - 2) >> 1) & 1, err, 2)) sm.abort = 1;
+        __syncthreads();
+        if (sm.abort) break;
+        // load 128 x 32 floats of A and of B as float2, split, store swizzled
+        unsigned char* ah = reinterpret_cast<unsigned char*>(sm.a_hi[buf]);
+        unsigned char* al = reinterpret_cast<unsigned char*>(sm.a_lo[buf]);
+        unsigned char* bh = reinterpret_cast<unsigned char*>(sm.b_hi[buf]);
+        unsigned char* bl = reinterpret_cast<unsigned char*>(sm.b_lo[buf]);
+        const long long kb = k0 + (long long)s * TK;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < 2 * TM * (TK / 2); e += NTHR) {
+            const bool isb = e >= TM * (TK / 2);
+            const int ee = isb ? e - TM * (TK / 2) : e;
+            const int row = ee / (TK / 2), k = 2 * (ee % (TK / 2));
+            const int grow = (isb ? j0 : i0) + row;
+            const long long gk = kb + k;
+            float2 x = make_float2(0.f, 0.f);
+            if (grow < (isb ? n : m) && gk < K) {
+                const float* src = (isb ? B : A) + (long long)grow * K + gk;
+                if (gk + 1 < K)
+                    x = __ldg(reinterpret_cast<const float2*>(src));
+                else
+                    x.x = __ldg(src);
+            }
+            const uint32_t hx = tf32_round(x.x), hy = tf32_round(x.y);
+            const uint32_t lx = tf32_round(x.x - __uint_as_float(hx)), ly = tf32_round(x.y - __uint_as_float(hy));
+            const uint32_t off = sw128_offset(row, k);
+            *reinterpret_cast<uint2*>((isb ? bh : ah) + off) = make_uint2(hx, hy);
+            *reinterpret_cast<uint2*>((isb ? bl : al) + off) = make_uint2(lx, ly);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int kk = 0; kk < TK / 8; ++kk) {
+                // advance 8 tf32 (32 bytes) along K inside the swizzle row
+                const uint64_t dah = smem_desc_sw128(ah + kk * 32), dal = smem_desc_sw128(al + kk * 32);
+                const uint64_t dbh = smem_desc_sw128(bh + kk * 32), dbl = smem_desc_sw128(bl + kk * 32);
+                const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
+                umma_tf32(tmem, dal, dbl, acc0);  // small terms first
+                umma_tf32(tmem, dal, dbh, 1u);
+                umma_tf32(tmem, dah, dbl, 1u);
+                umma_tf32(tmem, dah, dbh, 1u);
+            }
+            umma_commit(&sm.mma_done[buf]);
+        }
+        ++committed;
+    }
+    __syncthreads();
+    const bool ok = !sm.abort;
+    if (committed > 0) {
+        const int last = committed - 1;
+        if (!mbar_wait_bounded(&sm.mma_done[last & 1], (last >> 1) & 1, err, 2)) sm.abort = 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (ok && !sm.abort && committed == nst) {
+        // warp w reads TMEM lanes 32 (w % 4) .. +31 (output rows), columns
+        // 64 (w / 4) .. +63, 32 at a time
+        const int row = i0 + (warp & 3) * 32 + lane;
+        double* out = P + ((long long)blockIdx.z * m + row) * n;
+        for (int c0 = (warp >> 2) * 64; c0 < (warp >> 2) * 64 + 64; c0 += 32) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < m) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (j0 + c0 + c < n) out[j0 + c0 + c] = (double)__uint_as_float(v[c]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+}  // namespace
+
+int gram_umma_chunks(long long K) { return (int)((K + KCHUNK - 1) / KCHUNK); }
+
+cudaError_t launch_gram_partial_umma(const float* A, const float* B, int m, int n, long long K, double* P, int* err,
+                                     cudaStream_t st) {
+    if (K % 2 != 0 || ((uintptr_t)A % 8) || ((uintptr_t)B % 8)) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(GramSmem) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(gram_partial_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((m + TM - 1) / TM, (n + TN - 1) / TN, gram_umma_chunks(K));
+    gram_partial_umma<<<grid, NTHR, smem, st>>>(A, B, m, n, K, P, err);
+    return cudaGetLastError();
+}
+
+}  // namespace ace

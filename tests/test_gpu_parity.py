@@ -147,3 +147,42 @@ def test_error_paths():
     # the plan stays usable after errors
     xi, E = ace.ace_build(plan, dev(s["psi"], plan), s["alpha"])
     assert np.isfinite(E)
+
+
+def test_tensor_core_gram_matches_cuda_cores():
+    """The tcgen05 split-TF32 Gram (default for single precision) against the
+    CUDA-core Gram, through ace_apply with ragged sizes (partial 128-row tiles,
+    K = 2 n_pw_half not a multiple of the K tile), and through ace_build."""
+    cfg = gen.config_small()
+    rng = np.random.default_rng(17)
+    npw = len(gen.half_sphere(cfg["cell"], cfg["ecut"]))
+    xi = (rng.standard_normal((200, npw)) + 1j * rng.standard_normal((200, npw))) / np.sqrt(npw)
+    xi[:, 0] = xi[:, 0].real
+    psi = gen.random_trials(cfg["cell"], cfg["ecut"], 150, seed=18)
+    out = []
+    for kernels in (0, 1):
+        plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], 200, "mixed", kernels=kernels)
+        out.append(host(ace.ace_apply(plan, dev(xi, plan), dev(psi, plan))))
+    ref = -xi.T @ oracle.gamma_gram(xi, psi, gen.half_sphere(cfg["cell"], cfg["ecut"]))
+    assert rel(out[0], ref.T) <= 1e-6 and rel(out[1], ref.T) <= 1e-6
+    assert rel(out[0], out[1]) <= 1e-6
+    Es, Ms = [], []
+    for kernels in (0, 1):
+        plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], 8, "mixed", kernels=kernels)
+        _, E = ace.ace_build(plan, dev(cfg["psi"], plan), cfg["alpha"])
+        Es.append(E)
+        Ms.append(ace.ace_last_intermediates(plan, 8)[1])
+    assert np.abs(Ms[0] - Ms[1]).max() <= 1e-6 * np.abs(Ms[1]).max()
+
+
+@pytest.mark.parametrize("prec", ["mixed"])
+def test_generic_kernels_on_a_cube(prec):
+    """The runtime-size FFT passes on a 32^3 box (normally served by the
+    compile-time cube kernels) give the same build."""
+    cfg = gen.config_small()
+    ref = oracle.ace_build(cfg["psi"], cfg["cell"], cfg["grid"], cfg["ecut"], cfg["alpha"])
+    plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], 8, prec, kernels=2)
+    xi, E = ace.ace_build(plan, dev(cfg["psi"], plan), cfg["alpha"])
+    assert abs(E - ref["E_x"]) / cfg["n_atom"] <= 1e-6
+    tr = gen.random_trials(cfg["cell"], cfg["ecut"], 4, seed=5)
+    assert rel(host(ace.ace_apply(plan, xi, dev(tr, plan))), oracle.ace_apply(ref["xi"], tr, ref["miller"])) <= 1e-6
