@@ -375,9 +375,11 @@ int gram(ace_plan* P, const cx<R>* A, int m, const cx<R>* B, int n, double* G, c
     if constexpr (sizeof(R) == 4) {
         if (P->tensor_gram) {
             const int nchunk = gram_umma_chunks(K);
-            ACE_TRY(grow(&P->d_part, &P->part_cap, (size_t)nchunk * m * n));
-            ACE_CKL(launch_gram_partial_umma((const float*)A, (const float*)B, m, n, K, P->d_part, P->d_err, st));
-            ACE_CKL(launch_gram_finish<R>(P->d_part, nchunk, (const R*)A, (const R*)B, m, n, K, G, n, st));
+            // single-precision partials: half the doubles' room is enough
+            ACE_TRY(grow(&P->d_part, &P->part_cap, ((size_t)nchunk * m * n + 1) / 2));
+            float* part = reinterpret_cast<float*>(P->d_part);
+            ACE_CKL(launch_gram_partial_umma((const float*)A, (const float*)B, m, n, K, part, P->d_err, st));
+            ACE_CKL(launch_gram_finish_f32(part, nchunk, (const float*)A, (const float*)B, m, n, K, G, n, st));
             return ACE_OK;
         }
     }

@@ -126,8 +126,11 @@ cudaError_t launch_gram_partial(const R* A, const R* B, int m, int n, long long 
 // The same partials on tcgen05 tensor cores (split TF32, FP32 accumulation in
 // TMEM), gram_umma_chunks(K) K-slices; err: device error flag for bounded waits.
 int gram_umma_chunks(long long K);
-cudaError_t launch_gram_partial_umma(const float* A, const float* B, int m, int n, long long K, double* P, int* err,
+cudaError_t launch_gram_partial_umma(const float* A, const float* B, int m, int n, long long K, float* P, int* err,
                                      cudaStream_t st);
+// launch_gram_finish for single-precision partials
+cudaError_t launch_gram_finish_f32(const float* P, int nchunk, const float* A, const float* B, int m, int n,
+                                   long long K, double* G, int ldg, cudaStream_t st);
 // G[i][j] = 2 sum_c P[c][i][j] - (A_i0 B_j0 + A_i1 B_j1)   (G = 0 counted once)
 template <typename R>
 cudaError_t launch_gram_finish(const double* P, int nchunk, const R* A, const R* B, int m, int n, long long K,

@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const R* __restrict__
         }
 }
 
-template <typename R>
-__global__ void gram_finish_kernel(const double* __restrict__ P, int nchunk, const R* __restrict__ A,
+template <typename R, typename PT>
+__global__ void gram_finish_kernel(const PT* __restrict__ P, int nchunk, const R* __restrict__ A,
                                    const R* __restrict__ B, int m, int n, long long K, double* __restrict__ G,
                                    int ldg) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -282,7 +282,14 @@ template <typename R>
 cudaError_t launch_gram_finish(const double* P, int nchunk, const R* A, const R* B, int m, int n, long long K,
                                double* G, int ldg, cudaStream_t st) {
     const int tot = m * n;
-    gram_finish_kernel<R><<<(tot + 255) / 256, 256, 0, st>>>(P, nchunk, A, B, m, n, K, G, ldg);
+    gram_finish_kernel<R, double><<<(tot + 255) / 256, 256, 0, st>>>(P, nchunk, A, B, m, n, K, G, ldg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_finish_f32(const float* P, int nchunk, const float* A, const float* B, int m, int n,
+                                   long long K, double* G, int ldg, cudaStream_t st) {
+    const int tot = m * n;
+    gram_finish_kernel<float, float><<<(tot + 255) / 256, 256, 0, st>>>(P, nchunk, A, B, m, n, K, G, ldg);
     return cudaGetLastError();
 }
 

@@ -7,9 +7,10 @@
 // x_lo = tf32(x - x_hi), and the four products hi.hi + hi.lo + lo.hi + lo.lo
 // are accumulated in FP32 in tensor memory (TMEM) by tcgen05.mma kind::tf32,
 // which carries the product to about 2^-22 of |a||b|.  Each thread block owns
-// a 128 x 128 output tile and one 256-wide slice of K; its partial is written
-// in double precision and the slices are summed in double by
-// launch_gram_finish (la.cu), as for the SIMT path.
+// a 128 x 128 output tile and one 128-wide slice of K; the large products
+// (hi.hi) and the three small ones accumulate in separate TMEM accumulators,
+// the slice's partial is written in single precision and the slices are
+// summed in double by launch_gram_finish (la.cu).
 //
 // Data movement: the block's threads load 128 x 32 FP32 slices of both
 // operands as 8-byte vectors (rows of n_pw_half complex numbers are only
@@ -28,10 +29,9 @@ namespace ace {
 namespace {
 
 constexpr int TM = 128, TN = 128, TK = 32;   // output tile, K per stage (one 128-byte swizzle row)
-constexpr int KCHUNK = 256;                   // K per block
+constexpr int KCHUNK = 128;                   // K per block
 constexpr int STAGES = 2;
-constexpr int TILE_BYTES = TM * TK * 4;       // 16 KB, same for A and B (TN == TM)
-constexpr uint32_t TMEM_COLS = 128;
+constexpr uint32_t TMEM_COLS = 256;  // two 128-column FP32 accumulators
 
 struct __align__(1024) GramSmem {
     float a_hi[STAGES][TM * TK];
@@ -68,6 +68,18 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+
 __device__ __forceinline__ uint32_t tf32_round(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -84,7 +96,7 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
 
 __global__ void __launch_bounds__(NTHR, 1)
     gram_partial_umma(const float* __restrict__ A, const float* __restrict__ B, int m, int n, long long K,
-                      double* __restrict__ P, int* err) {
+                      float* __restrict__ P, int* err) {
     extern __shared__ unsigned char smem_raw[];
     GramSmem& sm = *reinterpret_cast<GramSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TN;
@@ -152,10 +164,12 @@ __global__ void __launch_bounds__(NTHR, 1)
                 const uint64_t dah = smem_desc_sw128(ah + kk * 32), dal = smem_desc_sw128(al + kk * 32);
                 const uint64_t dbh = smem_desc_sw128(bh + kk * 32), dbl = smem_desc_sw128(bl + kk * 32);
                 const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
-                umma_tf32(tmem, dal, dbl, acc0);  // small terms first
-                umma_tf32(tmem, dal, dbh, 1u);
-                umma_tf32(tmem, dah, dbl, 1u);
-                umma_tf32(tmem, dah, dbh, 1u);
+                // the three small products in their own accumulator, so the
+                // large one is rounded once per K step only
+                umma_tf32(tmem + TN, dal, dbl, acc0);
+                umma_tf32(tmem + TN, dal, dbh, 1u);
+                umma_tf32(tmem + TN, dah, dbl, 1u);
+                umma_tf32(tmem, dah, dbh, acc0);
             }
             umma_commit(&sm.mma_done[buf]);
         }
@@ -173,25 +187,17 @@ __global__ void __launch_bounds__(NTHR, 1)
         // warp w reads TMEM lanes 32 (w % 4) .. +31 (output rows), columns
         // 64 (w / 4) .. +63, 32 at a time
         const int row = i0 + (warp & 3) * 32 + lane;
-        double* out = P + ((long long)blockIdx.z * m + row) * n;
+        float* out = P + ((long long)blockIdx.z * m + row) * n;
         for (int c0 = (warp >> 2) * 64; c0 < (warp >> 2) * 64 + 64; c0 += 32) {
-            uint32_t v[32];
+            uint32_t v[32], w[32];
             const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
+            tmem_ld32(taddr + TN, w);
+            tmem_ld32(taddr, v);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (row < m) {
 #pragma unroll
                 for (int c = 0; c < 32; ++c)
-                    if (j0 + c0 + c < n) out[j0 + c0 + c] = (double)__uint_as_float(v[c]);
+                    if (j0 + c0 + c < n) out[j0 + c0 + c] = __uint_as_float(v[c]) + __uint_as_float(w[c]);
             }
         }
     }
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(NTHR, 1)
 
 int gram_umma_chunks(long long K) { return (int)((K + KCHUNK - 1) / KCHUNK); }
 
-cudaError_t launch_gram_partial_umma(const float* A, const float* B, int m, int n, long long K, double* P, int* err,
+cudaError_t launch_gram_partial_umma(const float* A, const float* B, int m, int n, long long K, float* P, int* err,
                                      cudaStream_t st) {
     if (K % 2 != 0 || ((uintptr_t)A % 8) || ((uintptr_t)B % 8)) return cudaErrorInvalidValue;
     const size_t smem = sizeof(GramSmem) + 1024;
