@@ -326,6 +326,39 @@ def profile_case(n_occ, batch=64):
     print(json.dumps({"profile_case": n_occ, "E_x": E}))
 
 
+def profile_apply(T, reps=3):
+    """ACE applies on T random trials with 256 random ACE vectors in the
+    120^3 / 23.5-bohr / 80 Ry basis (78398 plane waves): the tensor-core Gram
+    and the apply product the ncu captures under profiles/ run."""
+    import torch
+
+    import gen
+    import paper_2110_07670_gb300 as ace
+    cell = gen.cubic_cell(23.5)
+    plan = ace.Plan((120, 120, 120), cell, 80.0, 256, "mixed")
+    rng = np.random.default_rng(1)
+    npw = plan.n_pw_half
+    xi = (rng.standard_normal((256, npw)) + 1j * rng.standard_normal((256, npw))) / np.sqrt(npw)
+    xi[:, 0] = xi[:, 0].real
+    tr = gen.random_trials(cell, 80.0, T, 2)
+    d_xi = torch.from_numpy(xi.astype(np.complex64)).cuda()
+    d_tr = torch.from_numpy(tr.astype(np.complex64)).cuda()
+    out = torch.empty_like(d_tr)
+    for _ in range(reps):
+        ace.ace_apply(plan, d_xi, d_tr, out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ace.ace_get_stats(plan)
+    ace.ace_set_timing(plan, True)
+    a.record()
+    ace.ace_apply(plan, d_xi, d_tr, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    st = ace.ace_get_stats(plan)
+    print(json.dumps({"profile_apply": T, "apply_ms": a.elapsed_time(b), "gram_ms": st["gram_ms"],
+                      "product_ms": st["xi_ms"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,9 +368,13 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", type=int, default=0, help="run one small build with this many orbitals")
+    ap.add_argument("--profile-apply", type=int, default=0, help="run ACE applies on this many trial vectors")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args.profile_case)
+        return
+    if args.profile_apply:
+        profile_apply(args.profile_apply)
         return
     if args.impl == "reference":
         run_reference(args)
