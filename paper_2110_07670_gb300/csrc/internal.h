@@ -137,10 +137,11 @@ cudaError_t launch_gram_finish(const double* P, int nchunk, const R* A, const R*
                                double* G, int ldg, cudaStream_t st);
 
 // out[i][c] = alpha sum_k A[i][k] B[k][c]  (A double [m][k], B R [k][ncols], out R);
-// fp64_math: products and sums in double, else in R over 16-wide slices.
+// fp64_math: products and sums in double, else in R over 16-wide slices with
+// compensated slice accumulation; lower: A is lower triangular (k <= row).
 template <typename R>
 cudaError_t launch_gemm_nn(const double* A, int m, int k, const R* B, long long ncols, double alpha, R* out,
-                           bool fp64_math, cudaStream_t st);
+                           bool fp64_math, cudaStream_t st, bool lower = false);
 
 // Cholesky of -M and the inverse of its factor, in double, one thread block.
 // status: 0 ok, 1 not positive definite.

@@ -126,21 +126,38 @@ __global__ void gram_finish_kernel(const PT* __restrict__ P, int nchunk, const R
 //             slices, slices summed in double (the ACE apply).
 constexpr int NM = 32, NC = 128, NK = 16;
 
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+    // hi + lo += x without losing the low part (Knuth's TwoSum)
+    const float t = hi + x;
+    const float bb = t - hi;
+    lo += (hi - (t - bb)) + (x - bb);
+    hi = t;
+}
+
 template <typename R, typename C>
 __global__ void __launch_bounds__(256) gemm_nn_kernel(const double* __restrict__ A, int m, int kdim,
                                                       const R* __restrict__ B, long long ncols, double alpha,
-                                                      R* __restrict__ out) {
+                                                      R* __restrict__ out, int lower) {
     __shared__ C As[NK][NM];
     __shared__ C Bs[NK][NC];
-    const int i0 = blockIdx.y * NM;
-    const long long c0 = (long long)blockIdx.x * NC;
+    // row blocks vary fastest, so the blocks that share a column tile of B run together
+    const int i0 = blockIdx.x * NM;
+    const long long c0 = (long long)blockIdx.y * NC;
     const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // ty: 0..7
+    // double: plain double sums; float: each 16-wide slice summed in float and
+    // the slices accumulated in a compensated (hi, lo) float pair
     double acc[4][4];
+    float hi[4][4], lo[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-    for (int k0 = 0; k0 < kdim; k0 += NK) {
+        for (int b = 0; b < 4; ++b) {
+            acc[a][b] = 0.0;
+            hi[a][b] = lo[a][b] = 0.f;
+        }
+    // a lower-triangular A has no terms beyond the block's last row
+    const int kend = lower ? (kdim < i0 + NM ? kdim : i0 + NM) : kdim;
+    for (int k0 = 0; k0 < kend; k0 += NK) {
         for (int e = threadIdx.x; e < NK * NM; e += 256) {
             const int r = e / NK, c = e % NK;
             As[c][r] = (i0 + r < m && k0 + c < kdim) ? C(A[(long long)(i0 + r) * kdim + k0 + c]) : C(0);
@@ -157,17 +174,25 @@ __global__ void __launch_bounds__(256) gemm_nn_kernel(const double* __restrict__
             for (int b = 0; b < 4; ++b) s[a][b] = C(0);
 #pragma unroll
         for (int c = 0; c < NK; ++c) {
+            C av[4], bv[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const C av = As[c][ty + 8 * a];
+            for (int a = 0; a < 4; ++a) av[a] = As[c][ty + 8 * a];
 #pragma unroll
-                for (int b = 0; b < 4; ++b) s[a][b] += av * Bs[c][tx + 32 * b];
-            }
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[c][tx + 32 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) s[a][b] += av[a] * bv[b];
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += double(s[a][b]);
+            for (int b = 0; b < 4; ++b) {
+                if constexpr (sizeof(C) == 8)
+                    acc[a][b] += double(s[a][b]);
+                else
+                    two_sum_acc(hi[a][b], lo[a][b], float(s[a][b]));
+            }
         __syncthreads();
     }
 #pragma unroll
@@ -176,7 +201,8 @@ __global__ void __launch_bounds__(256) gemm_nn_kernel(const double* __restrict__
         for (int b = 0; b < 4; ++b) {
             const int i = i0 + ty + 8 * a;
             const long long c = c0 + tx + 32 * b;
-            if (i < m && c < ncols) out[(long long)i * ncols + c] = R(alpha * acc[a][b]);
+            const double v = sizeof(C) == 8 ? acc[a][b] : (double)hi[a][b] + (double)lo[a][b];
+            if (i < m && c < ncols) out[(long long)i * ncols + c] = R(alpha * v);
         }
 }
 
@@ -295,12 +321,12 @@ cudaError_t launch_gram_finish_f32(const float* P, int nchunk, const float* A, c
 
 template <typename R>
 cudaError_t launch_gemm_nn(const double* A, int m, int k, const R* B, long long ncols, double alpha, R* out,
-                           bool fp64_math, cudaStream_t st) {
-    dim3 grid((unsigned)((ncols + NC - 1) / NC), (m + NM - 1) / NM);
+                           bool fp64_math, cudaStream_t st, bool lower) {
+    dim3 grid((m + NM - 1) / NM, (unsigned)((ncols + NC - 1) / NC));
     if (fp64_math)
-        gemm_nn_kernel<R, double><<<grid, 256, 0, st>>>(A, m, k, B, ncols, alpha, out);
+        gemm_nn_kernel<R, double><<<grid, 256, 0, st>>>(A, m, k, B, ncols, alpha, out, lower ? 1 : 0);
     else
-        gemm_nn_kernel<R, R><<<grid, 256, 0, st>>>(A, m, k, B, ncols, alpha, out);
+        gemm_nn_kernel<R, R><<<grid, 256, 0, st>>>(A, m, k, B, ncols, alpha, out, lower ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -326,7 +352,7 @@ cudaError_t launch_energy_reduce(const double* e_part, const Quad* quads, int nt
     template cudaError_t launch_gram_finish<R>(const double*, int, const R*, const R*, int, int, long long,     \
                                                double*, int, cudaStream_t);                                     \
     template cudaError_t launch_gemm_nn<R>(const double*, int, int, const R*, long long, double, R*, bool,      \
-                                           cudaStream_t);
+                                           cudaStream_t, bool);
 ACE_INST(float)
 ACE_INST(double)
 #undef ACE_INST

@@ -15,9 +15,10 @@
 // Data movement: the block's threads load 128 x 32 FP32 slices of both
 // operands as 8-byte vectors (rows of n_pw_half complex numbers are only
 // 8-byte aligned, so tensor-map copies do not apply), split them and store
-// hi / lo in the K-major 128-byte swizzle layout of a two-stage ring; one
-// thread issues the MMAs and commits them to an mbarrier; tcgen05.ld drains
-// the accumulator.  Every wait is bounded in time and sets the plan's device
+// hi / lo in the K-major 128-byte swizzle layout (the next slice is already
+// loading into registers while the tensor core works); one thread issues the
+// MMAs and commits them to an mbarrier; tcgen05.ld drains the accumulators.
+// 64 KB of shared memory and 256 TMEM columns let two blocks share an SM.  Every wait is bounded in time and sets the plan's device
 // error flag when it gives up.
 #include <cstdio>
 
@@ -30,15 +31,14 @@ namespace {
 
 constexpr int TM = 128, TN = 128, TK = 32;   // output tile, K per stage (one 128-byte swizzle row)
 constexpr int KCHUNK = 128;                   // K per block
-constexpr int STAGES = 2;
 constexpr uint32_t TMEM_COLS = 256;  // two 128-column FP32 accumulators
 
 struct __align__(1024) GramSmem {
-    float a_hi[STAGES][TM * TK];
-    float a_lo[STAGES][TM * TK];
-    float b_hi[STAGES][TN * TK];
-    float b_lo[STAGES][TN * TK];
-    uint64_t mma_done[STAGES];
+    float a_hi[TM * TK];
+    float a_lo[TM * TK];
+    float b_hi[TN * TK];
+    float b_lo[TN * TK];
+    uint64_t mma_done;
     uint32_t tmem_base;
     int abort;
 };
@@ -94,7 +94,7 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
     return (uint32_t)(row * 128 + ((k * 4) ^ ((row & 7) << 4)));
 }
 
-__global__ void __launch_bounds__(NTHR, 1)
+__global__ void __launch_bounds__(NTHR, 2)
     gram_partial_umma(const float* __restrict__ A, const float* __restrict__ B, int m, int n, long long K,
                       float* __restrict__ P, int* err) {
     extern __shared__ unsigned char smem_raw[];
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(NTHR, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 32) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&sm.mma_done[s], 1);
+        mbar_init(&sm.mma_done, 1);
         sm.abort = 0;
         fence_mbar_init();
     }
@@ -120,40 +120,55 @@ __global__ void __launch_bounds__(NTHR, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = sm.tmem_base;
 
-    int committed = 0;
-    for (int s = 0; s < nst; ++s) {
-        const int buf = s & 1;
-        // the buffer was last read by the MMAs of stage s - 2
-        if (s >= 2 && !mbar_wait_bounded(&sm.mma_done[buf], ((s - 2) >> 1) & 1, err, 2)) sm.abort = 1;
-        __syncthreads();
-        if (sm.abort) break;
-        // load 128 x 32 floats of A and of B as float2, split, store swizzled
-        unsigned char* ah = reinterpret_cast<unsigned char*>(sm.a_hi[buf]);
-        unsigned char* al = reinterpret_cast<unsigned char*>(sm.a_lo[buf]);
-        unsigned char* bh = reinterpret_cast<unsigned char*>(sm.b_hi[buf]);
-        unsigned char* bl = reinterpret_cast<unsigned char*>(sm.b_lo[buf]);
+    // Each thread owns 16 float2 of a stage (8 of A, 8 of B); the next stage is
+    // loaded into registers while the tensor core works on the current one.
+    constexpr int PER = 2 * TM * (TK / 2) / NTHR;  // 16
+    float2 x[PER];
+    auto load_stage = [&](int s) {
         const long long kb = k0 + (long long)s * TK;
-#pragma unroll 4
-        for (int e = threadIdx.x; e < 2 * TM * (TK / 2); e += NTHR) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = threadIdx.x + u * NTHR;
             const bool isb = e >= TM * (TK / 2);
             const int ee = isb ? e - TM * (TK / 2) : e;
             const int row = ee / (TK / 2), k = 2 * (ee % (TK / 2));
             const int grow = (isb ? j0 : i0) + row;
             const long long gk = kb + k;
-            float2 x = make_float2(0.f, 0.f);
+            x[u] = make_float2(0.f, 0.f);
             if (grow < (isb ? n : m) && gk < K) {
                 const float* src = (isb ? B : A) + (long long)grow * K + gk;
                 if (gk + 1 < K)
-                    x = __ldg(reinterpret_cast<const float2*>(src));
+                    x[u] = __ldg(reinterpret_cast<const float2*>(src));
                 else
-                    x.x = __ldg(src);
+                    x[u].x = __ldg(src);
             }
-            const uint32_t hx = tf32_round(x.x), hy = tf32_round(x.y);
-            const uint32_t lx = tf32_round(x.x - __uint_as_float(hx)), ly = tf32_round(x.y - __uint_as_float(hy));
+        }
+    };
+    unsigned char* ah = reinterpret_cast<unsigned char*>(sm.a_hi);
+    unsigned char* al = reinterpret_cast<unsigned char*>(sm.a_lo);
+    unsigned char* bh = reinterpret_cast<unsigned char*>(sm.b_hi);
+    unsigned char* bl = reinterpret_cast<unsigned char*>(sm.b_lo);
+    load_stage(0);
+    int committed = 0;
+    for (int s = 0; s < nst; ++s) {
+        // the single operand buffer was last read by the MMAs of stage s - 1
+        if (s >= 1 && !mbar_wait_bounded(&sm.mma_done, (s - 1) & 1, err, 2)) sm.abort = 1;
+        __syncthreads();
+        if (sm.abort) break;
+        // split hi = tf32(x), lo = tf32(x - hi) and store in the swizzled layout
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = threadIdx.x + u * NTHR;
+            const bool isb = e >= TM * (TK / 2);
+            const int ee = isb ? e - TM * (TK / 2) : e;
+            const int row = ee / (TK / 2), k = 2 * (ee % (TK / 2));
+            const uint32_t hx = tf32_round(x[u].x), hy = tf32_round(x[u].y);
+            const uint32_t lx = tf32_round(x[u].x - __uint_as_float(hx)), ly = tf32_round(x[u].y - __uint_as_float(hy));
             const uint32_t off = sw128_offset(row, k);
             *reinterpret_cast<uint2*>((isb ? bh : ah) + off) = make_uint2(hx, hy);
             *reinterpret_cast<uint2*>((isb ? bl : al) + off) = make_uint2(lx, ly);
         }
+        if (s + 1 < nst) load_stage(s + 1);  // in flight during this stage's MMAs
         fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -171,15 +186,14 @@ __global__ void __launch_bounds__(NTHR, 1)
                 umma_tf32(tmem + TN, dah, dbl, 1u);
                 umma_tf32(tmem, dah, dbh, acc0);
             }
-            umma_commit(&sm.mma_done[buf]);
+            umma_commit(&sm.mma_done);
         }
         ++committed;
     }
     __syncthreads();
     const bool ok = !sm.abort;
     if (committed > 0) {
-        const int last = committed - 1;
-        if (!mbar_wait_bounded(&sm.mma_done[last & 1], (last >> 1) & 1, err, 2)) sm.abort = 1;
+        if (!mbar_wait_bounded(&sm.mma_done, (committed - 1) & 1, err, 2)) sm.abort = 1;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
