@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -89,6 +90,7 @@ struct ace_plan {
     bool fused_xy = false;
     bool cube_kernels = true;  // compile-time kernels for supported N^3 boxes
     bool tensor_gram = false;  // Gram products on tcgen05 tensor cores (single precision)
+    int lookahead = 2;         // L2 look-ahead of the pair passes, in transforms (env ACE_LOOKAHEAD)
     PassShape s_xy{}, s_x{}, s_y{}, s_z{};
     int ntiles_last = 1;  // tiles of the pass that accumulates W
     int batch = 1;
@@ -272,6 +274,7 @@ PassArgs base_args(const ace_plan* P) {
     for (int i = 0; i < 9; ++i) a.b[i] = P->b[i];
     a.kscale = 1.0 / (double)P->N;
     a.err = P->d_err;
+    a.lookahead = P->lookahead;
     for (int d = 0; d < 3; ++d) a.freq[d] = P->d_freq[d];
     return a;
 }
@@ -602,6 +605,7 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     }
     if (opts && opts->kernels >= 2) P->cube_kernels = false;  // generic runtime-size FFT passes
     P->tensor_gram = !(opts && opts->kernels >= 1) && sizeof(R) == 4;
+    if (const char* env = std::getenv("ACE_LOOKAHEAD")) P->lookahead = std::max(0, std::atoi(env));
     ACE_TRY(setup_shapes<R>(P));
     // the compile-time plane kernels of N % 16 == 0 boxes keep x swizzled per row
     const bool swz = P->s_xy.cube && cube_swizzle(P->n[2]);

@@ -39,6 +39,7 @@ struct PassArgs {
     int bulk;        // spectrum tiles by bulk async copies (16-byte aligned runs)
     int vec;         // real functions as 4-wide vectors (tx, n2 multiples of 4)
     int* err;        // device error flag (1: a bounded wait timed out)
+    int lookahead;   // transforms ahead whose inputs a block pulls into L2 (0: none)
     AxisPlan px, py, pz;
     const void *twx, *twy, *twz;  // exp(-2 pi i j / n) per axis, cx<R>
     // prologue

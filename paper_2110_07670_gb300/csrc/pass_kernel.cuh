@@ -323,17 +323,49 @@ __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pa
     if (PRO != PRO_LOAD || EPI != EPI_STORE) q = a.quads[a.t0 + t];
     const R* fl = reinterpret_cast<const R*>(a.fl);
     const R* fr = reinterpret_cast<const R*>(a.fr);
-    if (EPI == EPI_ACCUM && S.tx == S.n2 && S.ty == S.n1 && threadIdx.x == 32) {
-        // the accumulation reads four function planes after the transforms:
-        // start pulling them into L2 now so the loads overlap the FFT stages
-        const long long off = (long long)z0 * S.n1 * S.n2;
-        const uint32_t bytes = (uint32_t)((long long)S.tz * S.n1 * S.n2 * sizeof(R));
-        if (bytes % 16 == 0) {
-            prefetch_l2(fl + q.a * N + off, bytes);
-            prefetch_l2(fr + q.b * N + off, bytes);
-            if (q.c >= 0) {
-                if (q.c != q.a) prefetch_l2(fl + q.c * N + off, bytes);
-                prefetch_l2(fr + q.d * N + off, bytes);
+    // L2 look-ahead (one lane of warp 1, no shared memory): the accumulation
+    // reads four function planes and updates up to four W planes after the
+    // transforms, so start pulling this tile's into L2 now; and since the
+    // launch order puts tile (z, t + D) about D waves behind (z, t), pull
+    // what that later block will load as well.
+    if (threadIdx.x >= 32 && threadIdx.x < 64) {
+        const int lane = threadIdx.x - 32;
+        const int tn = t + a.lookahead;
+        const bool ahead = a.lookahead > 0 && tn < (int)gridDim.y;
+        if (S.tx == S.n2 && S.ty == S.n1 && lane == 0) {
+            const long long off = (long long)z0 * S.n1 * S.n2;
+            const uint32_t bytes = (uint32_t)((long long)S.tz * S.n1 * S.n2 * sizeof(R));
+            if (bytes % 16 == 0) {
+                auto planes = [&](const Quad& qq, bool with_w) {
+                    prefetch_l2(fl + qq.a * N + off, bytes);
+                    prefetch_l2(fr + qq.b * N + off, bytes);
+                    if (qq.c >= 0) {
+                        if (qq.c != qq.a) prefetch_l2(fl + qq.c * N + off, bytes);
+                        prefetch_l2(fr + qq.d * N + off, bytes);
+                    }
+                    if (with_w) {
+                        const R* wl = reinterpret_cast<const R*>(a.accl);
+                        prefetch_l2(wl + qq.a * N + off, bytes);
+                        if (qq.c >= 0 && qq.c != qq.a) prefetch_l2(wl + qq.c * N + off, bytes);
+                        if (a.symmetric) {
+                            const R* wr = reinterpret_cast<const R*>(a.accr);
+                            if (qq.b != qq.a) prefetch_l2(wr + qq.b * N + off, bytes);
+                            if (qq.c >= 0 && qq.d != qq.c) prefetch_l2(wr + qq.d * N + off, bytes);
+                        }
+                    }
+                };
+                if (EPI == EPI_ACCUM) planes(q, true);
+                if (ahead && (PRO == PRO_PAIR || EPI == EPI_ACCUM)) planes(a.quads[a.t0 + tn], false);
+            }
+        }
+        if (PRO == PRO_LOAD && a.bulk && ahead) {
+            const Chunks ch = tile_chunks(S);
+            const cx<R>* srcn = reinterpret_cast<const cx<R>*>(a.src) + (long long)tn * a.src_tstride;
+            for (int k = lane; k < ch.count; k += 32) {
+                long long g;
+                int sk;
+                chunk_at(S, k, z0, y0, x0, g, sk);
+                prefetch_l2(srcn + g, (uint32_t)(ch.len * sizeof(cx<R>)));
             }
         }
     }
