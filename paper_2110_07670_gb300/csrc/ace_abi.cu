@@ -90,7 +90,7 @@ struct ace_plan {
     bool fused_xy = false;
     bool cube_kernels = true;  // compile-time kernels for supported N^3 boxes
     bool tensor_gram = false;  // Gram products on tcgen05 tensor cores (single precision)
-    int lookahead = 2;         // L2 look-ahead of the pair passes, in transforms (env ACE_LOOKAHEAD)
+    int lookahead = 1;         // L2 look-ahead of the pair passes, in transforms (env ACE_LOOKAHEAD)
     PassShape s_xy{}, s_x{}, s_y{}, s_z{};
     int ntiles_last = 1;  // tiles of the pass that accumulates W
     int batch = 1;

@@ -325,9 +325,11 @@ __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pa
     const R* fr = reinterpret_cast<const R*>(a.fr);
     // L2 look-ahead (one lane of warp 1, no shared memory): the accumulation
     // reads four function planes and updates up to four W planes after the
-    // transforms, so start pulling this tile's into L2 now; and since the
-    // launch order puts tile (z, t + D) about D waves behind (z, t), pull
-    // what that later block will load as well.
+    // transforms, so start pulling this tile's into L2 now.  The pair-product
+    // and spectrum-load passes also pull what tile (z, t + D) will load, since
+    // the launch order puts that block about D waves behind this one (measured:
+    // one transform ahead helps the pair-product pass; pulling ahead in the
+    // accumulating pass only competes with its own read-modify-write traffic).
     if (threadIdx.x >= 32 && threadIdx.x < 64) {
         const int lane = threadIdx.x - 32;
         const int tn = t + a.lookahead;
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pa
                     }
                 };
                 if (EPI == EPI_ACCUM) planes(q, true);
-                if (ahead && (PRO == PRO_PAIR || EPI == EPI_ACCUM)) planes(a.quads[a.t0 + tn], false);
+                if (ahead && PRO == PRO_PAIR) planes(a.quads[a.t0 + tn], false);
             }
         }
         if (PRO == PRO_LOAD && a.bulk && ahead) {
