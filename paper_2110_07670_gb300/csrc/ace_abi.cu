@@ -91,6 +91,8 @@ struct ace_plan {
     bool cube_kernels = true;  // compile-time kernels for supported N^3 boxes
     bool tensor_gram = false;  // Gram products on tcgen05 tensor cores (single precision)
     int lookahead = 1;         // L2 look-ahead of the pair passes, in transforms (env ACE_LOOKAHEAD)
+    bool zline = false;        // per-pencil Coulomb pass (zline.cuh) with the kernel table d_kern
+    float* d_kern = nullptr;   // 4 pi / |G|^2 / N in spectrum layout (zline only)
     PassShape s_xy{}, s_x{}, s_y{}, s_z{};
     int ntiles_last = 1;  // tiles of the pass that accumulates W
     int batch = 1;
@@ -275,6 +277,7 @@ PassArgs base_args(const ace_plan* P) {
     a.kscale = 1.0 / (double)P->N;
     a.err = P->d_err;
     a.lookahead = P->lookahead;
+    a.kern = P->d_kern;
     for (int d = 0; d < 3; ++d) a.freq[d] = P->d_freq[d];
     return a;
 }
@@ -354,7 +357,10 @@ int run_pairs(ace_plan* P, const R* fl, const R* fr, R* accl, R* accr, int symme
         if (P->fused_xy) {
             ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_PAIR, EPI_STORE, MID_NONE, -1, nb, st));
             mark(P, PH_PCOUL, st);
-            ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_COULOMB, -1, nb, st));
+            if (P->zline)
+                ACE_CKL(zline_coulomb_launch(P->n[0], a, nb, st));
+            else
+                ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_COULOMB, -1, nb, st));
             mark(P, PH_PINV, st);
             ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_LOAD, EPI_ACCUM, MID_NONE, +1, nb, st));
         } else {
@@ -571,7 +577,7 @@ void free_plan(ace_plan* P) {
     for (auto e : P->ev_pool) cudaEventDestroy(e);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
                     P->d_WG, P->d_M, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
-                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C};
+                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -592,10 +598,11 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
         ACE_CK(cudaMemcpy(P->d_tw[d], tw.data(), tw.size() * sizeof(cx<R>), cudaMemcpyHostToDevice));
     }
     // digit-reversed positions of every frequency, per axis, and their inverse
-    std::vector<int> pos[3];
+    std::vector<int> pos[3], frq[3];
     for (int d = 0; d < 3; ++d) {
         pos[d].resize(P->n[d]);
-        std::vector<int> fr(P->n[d]);
+        std::vector<int>& fr = frq[d];
+        fr.resize(P->n[d]);
         for (int k = 0; k < P->n[d]; ++k) {
             pos[d][k] = digit_reversed_position(P->ax[d], k);
             fr[pos[d][k]] = k;
@@ -609,6 +616,29 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     ACE_TRY(setup_shapes<R>(P));
     // the compile-time plane kernels of N % 16 == 0 boxes keep x swizzled per row
     const bool swz = P->s_xy.cube && cube_swizzle(P->n[2]);
+    // per-pencil Coulomb pass: its kernel 4 pi / |G|^2 / N (Eq. 3, G = 0
+    // dropped) at every stored position of the spectrum, computed in double
+    P->zline = P->s_xy.cube && P->s_z.cube && zline_group(P->n[0]) > 0;
+    if (const char* env = std::getenv("ACE_ZLINE")) P->zline = P->zline && std::atoi(env) != 0;
+    if (P->zline) {
+        const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
+        std::vector<float> kern((size_t)P->N);
+        auto fold = [](int k, int n) { return k < n - n / 2 ? k : k - n; };
+        for (int z = 0; z < n0; ++z)
+            for (int y = 0; y < n1; ++y)
+                for (int xs = 0; xs < n2; ++xs) {
+                    const int xp = swz ? plane_swizzle(xs, y) : xs;
+                    const int m[3] = {fold(frq[0][z], n0), fold(frq[1][y], n1), fold(frq[2][xp], n2)};
+                    double g2 = 0;
+                    for (int c = 0; c < 3; ++c) {
+                        const double g = m[0] * P->b[c] + m[1] * P->b[3 + c] + m[2] * P->b[6 + c];
+                        g2 += g * g;
+                    }
+                    kern[((size_t)z * n1 + y) * n2 + xs] = g2 > 0 ? (float)(4 * M_PI / (g2 * (double)P->N)) : 0.0f;
+                }
+        ACE_TRY(dalloc((void**)&P->d_kern, kern.size() * sizeof(float)));
+        ACE_CK(cudaMemcpy(P->d_kern, kern.data(), kern.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     std::vector<int> ip(P->npw), in(P->npw);
     for (int p = 0; p < P->npw; ++p) {
         int m[3], mn[3];

@@ -1,5 +1,6 @@
 // cube_b.cu -- compile-time pass kernels for the N^3 boxes N = 90, 96, 100.
 #include "pass_kernel.cuh"
+#include "zline.cuh"
 
 namespace ace {
 
@@ -9,5 +10,9 @@ template cudaError_t pass_detail::dispatch_cube<96>(const PassArgs&, const PassS
                                                   cudaStream_t);
 template cudaError_t pass_detail::dispatch_cube<100>(const PassArgs&, const PassShape&, int, int, int, int, int,
                                                   cudaStream_t);
+
+template cudaError_t zline_launch<90>(const PassArgs&, int, cudaStream_t);
+template cudaError_t zline_launch<96>(const PassArgs&, int, cudaStream_t);
+template cudaError_t zline_launch<100>(const PassArgs&, int, cudaStream_t);
 
 }  // namespace ace

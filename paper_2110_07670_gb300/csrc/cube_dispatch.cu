@@ -1,5 +1,6 @@
 // cube_dispatch.cu -- route a pass to the compile-time kernel of its N^3 box.
 #include "pass_kernel.cuh"
+#include "zline.cuh"
 
 namespace ace {
 
@@ -18,6 +19,33 @@ ACE_CUBE_DECL(120)
 ACE_CUBE_DECL(160)
 #undef ACE_CUBE_DECL
 }  // namespace pass_detail
+
+#define ACE_ZLINE_DECL(N) extern template cudaError_t zline_launch<N>(const PassArgs&, int, cudaStream_t);
+ACE_ZLINE_DECL(32)
+ACE_ZLINE_DECL(60)
+ACE_ZLINE_DECL(80)
+ACE_ZLINE_DECL(90)
+ACE_ZLINE_DECL(96)
+ACE_ZLINE_DECL(100)
+ACE_ZLINE_DECL(108)
+ACE_ZLINE_DECL(120)
+ACE_ZLINE_DECL(160)
+#undef ACE_ZLINE_DECL
+
+cudaError_t zline_coulomb_launch(int n, const PassArgs& a, int batch, cudaStream_t st) {
+    switch (n) {
+        case 32: return zline_launch<32>(a, batch, st);
+        case 60: return zline_launch<60>(a, batch, st);
+        case 80: return zline_launch<80>(a, batch, st);
+        case 90: return zline_launch<90>(a, batch, st);
+        case 96: return zline_launch<96>(a, batch, st);
+        case 100: return zline_launch<100>(a, batch, st);
+        case 108: return zline_launch<108>(a, batch, st);
+        case 120: return zline_launch<120>(a, batch, st);
+        case 160: return zline_launch<160>(a, batch, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t cube_pass_launch(int n, const PassArgs& a, const PassShape& s, int pro, int epi, int mid, int sgn,
                              int batch, cudaStream_t st) {

@@ -61,6 +61,7 @@ struct PassArgs {
     double b[9];  // reciprocal vectors as rows
     double kscale;
     const int* freq[3];  // per axis: frequency held at each position after the forward stages
+    const void* kern;    // per-pencil Coulomb pass: 4 pi / |G|^2 / N in spectrum layout, [n0][n1][n2] float
 };
 
 struct PassShape {
@@ -96,6 +97,16 @@ constexpr int cube_z_ty(int n) {  // largest divisor keeping the tile within 819
         if (n % d == 0 && n * d * cube_z_tx(n) <= 8192) return d;
     return 1;
 }
+
+// Pencils per warp of the per-pencil Coulomb pass (zline.cuh): the largest
+// even divisor of n^2 up to 32 (even: a z row of the group is a whole number
+// of 16-byte units).
+constexpr int zline_group(int n) {
+    for (int g = 32; g >= 2; g -= 2)
+        if ((n * n) % g == 0) return g;
+    return 0;
+}
+cudaError_t zline_coulomb_launch(int n, const PassArgs& a, int batch, cudaStream_t st);
 
 // compile-time cube passes (cube_*.cu), single precision
 cudaError_t cube_pass_launch(int n, const PassArgs& a, const PassShape& s, int pro, int epi, int mid, int sgn,
