@@ -93,6 +93,8 @@ struct ace_plan {
     int lookahead = 1;         // L2 look-ahead of the pair passes, in transforms (env ACE_LOOKAHEAD)
     bool zline = false;        // per-pencil Coulomb pass (zline.cuh) with the kernel table d_kern
     float* d_kern = nullptr;   // 4 pi / |G|^2 / N in spectrum layout (zline only)
+    bool tplane = false;       // pair passes with transposed spectrum planes (plane.cuh; needs zline; opt-in)
+    int pair_tile = 0;         // pairs ordered in pair_tile x pair_tile orbital blocks (0: row by row; env ACE_PAIR_TILE)
     PassShape s_xy{}, s_x{}, s_y{}, s_z{};
     int ntiles_last = 1;  // tiles of the pass that accumulates W
     int batch = 1;
@@ -354,7 +356,13 @@ int run_pairs(ace_plan* P, const R* fl, const R* fr, R* accl, R* accr, int symme
         a.t0 = t0;
         P->pair_transforms += nb;
         mark(P, PH_PFWD, st);
-        if (P->fused_xy) {
+        if (P->tplane) {
+            ACE_CKL(tplane_pair_launch(P->n[0], 0, a, nb, st));
+            mark(P, PH_PCOUL, st);
+            ACE_CKL(zline_coulomb_launch(P->n[0], a, nb, st));
+            mark(P, PH_PINV, st);
+            ACE_CKL(tplane_pair_launch(P->n[0], 1, a, nb, st));
+        } else if (P->fused_xy) {
             ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_PAIR, EPI_STORE, MID_NONE, -1, nb, st));
             mark(P, PH_PCOUL, st);
             if (P->zline)
@@ -405,6 +413,26 @@ std::vector<Quad> orbital_quads(int n) {
     std::vector<Quad> q;
     for (int a = 0; a < n; a += 2) q.push_back(Quad{a, a, a + 1 < n ? a + 1 : -1, a + 1 < n ? a + 1 : -1});
     return q;
+}
+
+// Order the pairs (i, j) by blocks of tb x tb orbitals, each block row by row:
+// the transforms of one block touch only 2 tb functions and 2 tb accumulators,
+// which can stay in L2 between their uses instead of streaming once per pair.
+void tile_pairs(std::vector<int>& pa, std::vector<int>& pb, int tb) {
+    std::vector<size_t> idx(pa.size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+        const int bx = pa[x] / tb, by = pa[y] / tb, cx_ = pb[x] / tb, cy = pb[y] / tb;
+        if (bx != by) return bx < by;
+        return cx_ < cy;
+    });
+    std::vector<int> a2(pa.size()), b2(pb.size());
+    for (size_t k = 0; k < idx.size(); ++k) {
+        a2[k] = pa[idx[k]];
+        b2[k] = pb[idx[k]];
+    }
+    pa.swap(a2);
+    pb.swap(b2);
 }
 
 void pack_pairs(const std::vector<int>& pa, const std::vector<int>& pb, std::vector<Quad>& q) {
@@ -471,6 +499,7 @@ int build_enqueue(ace_plan* P, const void* psi_G, int n_occ, double alpha, const
                 pb.push_back(j);
             }
     }
+    if (P->pair_tile > 0) tile_pairs(pa, pb, P->pair_tile);
     std::vector<Quad> oq = orbital_quads(n_occ), q = oq;
     const int n_orb_t = (int)oq.size();
     pack_pairs(pa, pb, q);
@@ -613,6 +642,7 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     if (opts && opts->kernels >= 2) P->cube_kernels = false;  // generic runtime-size FFT passes
     P->tensor_gram = !(opts && opts->kernels >= 1) && sizeof(R) == 4;
     if (const char* env = std::getenv("ACE_LOOKAHEAD")) P->lookahead = std::max(0, std::atoi(env));
+    if (const char* env = std::getenv("ACE_PAIR_TILE")) P->pair_tile = std::max(0, std::atoi(env));
     ACE_TRY(setup_shapes<R>(P));
     // the compile-time plane kernels of N % 16 == 0 boxes keep x swizzled per row
     const bool swz = P->s_xy.cube && cube_swizzle(P->n[2]);
@@ -620,6 +650,11 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     // dropped) at every stored position of the spectrum, computed in double
     P->zline = P->s_xy.cube && P->s_z.cube && zline_group(P->n[0]) > 0;
     if (const char* env = std::getenv("ACE_ZLINE")) P->zline = P->zline && std::atoi(env) != 0;
+    // transposed-plane pair passes: opt-in (ACE_TPLANE=1); at 96^3 their
+    // forward pass is faster and their inverse pass slower than the tile passes
+    P->tplane = false;
+    if (const char* env = std::getenv("ACE_TPLANE"))
+        P->tplane = P->zline && tplane_supported(P->n[0]) && std::atoi(env) != 0;
     if (P->zline) {
         const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
         std::vector<float> kern((size_t)P->N);
@@ -627,14 +662,16 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
         for (int z = 0; z < n0; ++z)
             for (int y = 0; y < n1; ++y)
                 for (int xs = 0; xs < n2; ++xs) {
-                    const int xp = swz ? plane_swizzle(xs, y) : xs;
+                    const int xp = swz && !P->tplane ? plane_swizzle(xs, y) : xs;
                     const int m[3] = {fold(frq[0][z], n0), fold(frq[1][y], n1), fold(frq[2][xp], n2)};
                     double g2 = 0;
                     for (int c = 0; c < 3; ++c) {
                         const double g = m[0] * P->b[c] + m[1] * P->b[3 + c] + m[2] * P->b[6 + c];
                         g2 += g * g;
                     }
-                    kern[((size_t)z * n1 + y) * n2 + xs] = g2 > 0 ? (float)(4 * M_PI / (g2 * (double)P->N)) : 0.0f;
+                    // stored (y, x) slot, or (x, y) for transposed planes
+                    const size_t at = P->tplane ? ((size_t)z * n2 + xs) * n1 + y : ((size_t)z * n1 + y) * n2 + xs;
+                    kern[at] = g2 > 0 ? (float)(4 * M_PI / (g2 * (double)P->N)) : 0.0f;
                 }
         ACE_TRY(dalloc((void**)&P->d_kern, kern.size() * sizeof(float)));
         ACE_CK(cudaMemcpy(P->d_kern, kern.data(), kern.size() * sizeof(float), cudaMemcpyHostToDevice));

@@ -1,5 +1,6 @@
 // cube_b.cu -- compile-time pass kernels for the N^3 boxes N = 90, 96, 100.
 #include "pass_kernel.cuh"
+#include "plane.cuh"
 #include "zline.cuh"
 
 namespace ace {
@@ -14,5 +15,6 @@ template cudaError_t pass_detail::dispatch_cube<100>(const PassArgs&, const Pass
 template cudaError_t zline_launch<90>(const PassArgs&, int, cudaStream_t);
 template cudaError_t zline_launch<96>(const PassArgs&, int, cudaStream_t);
 template cudaError_t zline_launch<100>(const PassArgs&, int, cudaStream_t);
+template cudaError_t tplane_launch<96>(int, const PassArgs&, int, cudaStream_t);
 
 }  // namespace ace

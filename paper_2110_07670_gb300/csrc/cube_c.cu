@@ -1,5 +1,6 @@
 // cube_c.cu -- compile-time pass kernels for the N^3 boxes N = 108, 120, 160.
 #include "pass_kernel.cuh"
+#include "plane.cuh"
 #include "zline.cuh"
 
 namespace ace {
@@ -14,5 +15,6 @@ template cudaError_t pass_detail::dispatch_cube<160>(const PassArgs&, const Pass
 template cudaError_t zline_launch<108>(const PassArgs&, int, cudaStream_t);
 template cudaError_t zline_launch<120>(const PassArgs&, int, cudaStream_t);
 template cudaError_t zline_launch<160>(const PassArgs&, int, cudaStream_t);
+template cudaError_t tplane_launch<160>(int, const PassArgs&, int, cudaStream_t);
 
 }  // namespace ace

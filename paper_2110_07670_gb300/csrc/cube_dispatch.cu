@@ -1,5 +1,6 @@
 // cube_dispatch.cu -- route a pass to the compile-time kernel of its N^3 box.
 #include "pass_kernel.cuh"
+#include "plane.cuh"
 #include "zline.cuh"
 
 namespace ace {
@@ -43,6 +44,23 @@ cudaError_t zline_coulomb_launch(int n, const PassArgs& a, int batch, cudaStream
         case 108: return zline_launch<108>(a, batch, st);
         case 120: return zline_launch<120>(a, batch, st);
         case 160: return zline_launch<160>(a, batch, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+#define ACE_TPLANE_DECL(N) extern template cudaError_t tplane_launch<N>(int, const PassArgs&, int, cudaStream_t);
+ACE_TPLANE_DECL(32)
+ACE_TPLANE_DECL(80)
+ACE_TPLANE_DECL(96)
+ACE_TPLANE_DECL(160)
+#undef ACE_TPLANE_DECL
+
+cudaError_t tplane_pair_launch(int n, int which, const PassArgs& a, int batch, cudaStream_t st) {
+    switch (n) {
+        case 32: return tplane_launch<32>(which, a, batch, st);
+        case 80: return tplane_launch<80>(which, a, batch, st);
+        case 96: return tplane_launch<96>(which, a, batch, st);
+        case 160: return tplane_launch<160>(which, a, batch, st);
         default: return cudaErrorInvalidValue;
     }
 }

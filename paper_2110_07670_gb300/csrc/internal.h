@@ -99,14 +99,18 @@ constexpr int cube_z_ty(int n) {  // largest divisor keeping the tile within 819
 }
 
 // Pencils per warp of the per-pencil Coulomb pass (zline.cuh): the largest
-// even divisor of n^2 up to 32 (even: a z row of the group is a whole number
+// even divisor of n^2 up to 16 (even: a z row of the group is a whole number
 // of 16-byte units).
 constexpr int zline_group(int n) {
-    for (int g = 32; g >= 2; g -= 2)
+    for (int g = 16; g >= 2; g -= 2)
         if ((n * n) % g == 0) return g;
     return 0;
 }
 cudaError_t zline_coulomb_launch(int n, const PassArgs& a, int batch, cudaStream_t st);
+// plane passes with transposed spectrum planes (plane.cuh), N^3 boxes with
+// N % 16 == 0: which = 0 pair product + forward, 1 inverse + exchange accumulation
+constexpr bool tplane_supported(int n) { return n % 16 == 0; }
+cudaError_t tplane_pair_launch(int n, int which, const PassArgs& a, int batch, cudaStream_t st);
 
 // compile-time cube passes (cube_*.cu), single precision
 cudaError_t cube_pass_launch(int n, const PassArgs& a, const PassShape& s, int pro, int epi, int mid, int sgn,

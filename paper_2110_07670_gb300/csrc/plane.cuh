@@ -1,0 +1,386 @@
+// plane.cuh -- the two plane passes of the pair Poisson solves (Eq. 2-4) on
+// the compile-time N^3 boxes, with thread-owned lines:
+//
+//   forward  (pair_fwd):   rho = phi_a phi_b + i phi_c phi_d on plane z, 2-D
+//                          forward FFT, spectrum plane stored TRANSPOSED;
+//   inverse  (inv_accum):  2-D inverse FFT of a transposed spectrum plane,
+//                          then W_a += v phi_b, W_b += v phi_a, ... and the
+//                          pair energies sum rho v (Eq. 4).
+//
+// Between the passes (and through the per-pencil Coulomb pass) a spectrum
+// plane is stored as [x][y] (x position major, both positions digit-reversed
+// after the forward stages).  That lets the pass that works on x lines read
+// or write global memory straight from its butterflies with the lanes along
+// y (coalesced), while the pass that works on y lines meets the real-space
+// functions with the lanes along x (coalesced).
+//
+// Every line (a y column or an x row of the plane) belongs to two threads, the
+// two halves of a warp (lanes l and l + 16), which split its butterflies; a
+// stage needs only __syncwarp, and the plane needs one block barrier between
+// its y and x lines.  The shared tile has an odd row pitch (N + 1), so 16
+// lanes on 16 consecutive rows, or on 16 consecutive columns, hit 16 distinct
+// bank pairs.  The accumulation after the inverse runs on 4-wide vectors from
+// the shared tile (a final block barrier).  Both axes have two stages (radix R0 with N / R0 butterflies of
+// stride N / R0, then radix R1 on adjacent positions).
+#pragma once
+
+#include "fft_core.cuh"
+#include "internal.h"
+#include "tma.cuh"
+
+namespace ace {
+namespace plane_detail {
+
+template <int N>
+struct Geo {
+    using PL = CPlan<N>;
+    static_assert(PL::stages == 2, "plane passes assume two stages per axis");
+    static_assert(N % 16 == 0, "the vector epilogue tiles planes by 4 rows x 16 columns");
+    static constexpr int R0 = PL::radix(0), R1 = PL::radix(1);
+    static constexpr int M0 = N / R0;  // stage-0 butterflies per line (stride M0)
+    static constexpr int B1 = N / R1;  // stage-1 butterflies per line (adjacent)
+    static constexpr int P = N + 1;    // shared row pitch, odd
+    static constexpr int NT = (2 * N + 31) / 32 * 32;
+    static constexpr size_t smem = (size_t)(N * P + N) * sizeof(cx<float>);
+    // resident blocks per SM: 228 KB of shared memory, 1 KB reserved per block
+    // (and a little static shared memory)
+    static constexpr int kMinBlocks = 3 * (smem + 1280) <= 228 * 1024 ? 3 : (2 * (smem + 1280) <= 228 * 1024 ? 2 : 1);
+};
+
+// forward stage-0 twiddles on the outputs (DIF), inverse on the inputs (conjugate)
+template <int R>
+__device__ __forceinline__ void tw_out(cx<float> (&u)[R], const cx<float>* tw, int j) {
+    if (j > 0) {
+#pragma unroll
+        for (int s = 1; s < R; ++s) u[s] = cmul(u[s], tw[s * j]);
+    }
+}
+template <int R>
+__device__ __forceinline__ void tw_in_conj(cx<float> (&u)[R], const cx<float>* tw, int j) {
+    if (j > 0) {
+#pragma unroll
+        for (int q = 1; q < R; ++q) {
+            cx<float> w = tw[q * j];
+            w.im = -w.im;
+            u[q] = cmul(u[q], w);
+        }
+    }
+}
+
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 mul4(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
+__device__ __forceinline__ float4 fma4(float4 a, float4 b, float4 c) {
+    return make_float4(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y), fmaf(a.z, b.z, c.z), fmaf(a.w, b.w, c.w));
+}
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+__device__ __forceinline__ void red_add4(float* p, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// 8-byte global -> shared asynchronous copy (completes at cp_async_wait_all)
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Pull the plane-z slices of transform tt's functions (and accumulators) into L2.
+__device__ __forceinline__ void prefetch_planes(const PassArgs& a, const Quad& q, long long off, uint32_t bytes,
+                                                long long N3, bool with_w) {
+    const float* fl = reinterpret_cast<const float*>(a.fl);
+    const float* fr = reinterpret_cast<const float*>(a.fr);
+    prefetch_l2(fl + q.a * N3 + off, bytes);
+    prefetch_l2(fr + q.b * N3 + off, bytes);
+    if (q.c >= 0) {
+        if (q.c != q.a) prefetch_l2(fl + q.c * N3 + off, bytes);
+        prefetch_l2(fr + q.d * N3 + off, bytes);
+    }
+    if (with_w) {
+        const float* wl = reinterpret_cast<const float*>(a.accl);
+        prefetch_l2(wl + q.a * N3 + off, bytes);
+        if (q.c >= 0 && q.c != q.a) prefetch_l2(wl + q.c * N3 + off, bytes);
+        if (a.symmetric) {
+            const float* wr = reinterpret_cast<const float*>(a.accr);
+            if (q.b != q.a) prefetch_l2(wr + q.b * N3 + off, bytes);
+            if (q.c >= 0 && q.d != q.c) prefetch_l2(wr + q.d * N3 + off, bytes);
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) pair_fwd(PassArgs a) {
+    using G = Geo<N>;
+    constexpr long long NN = (long long)N * N, N3 = NN * N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<float>* tile = reinterpret_cast<cx<float>*>(smem_raw);  // (y, x) at y * P + x
+    cx<float>* tw = tile + N * G::P;
+    const int z = blockIdx.x, t = blockIdx.y;
+    const Quad q = a.quads[a.t0 + t];
+    const long long plane0 = (long long)z * NN;
+    for (int j = threadIdx.x; j < N; j += G::NT) tw[j] = reinterpret_cast<const cx<float>*>(a.twx)[j];
+    if (threadIdx.x == 32 && a.lookahead > 0 && t + a.lookahead < (int)gridDim.y && (NN * 4) % 16 == 0)
+        prefetch_planes(a, a.quads[a.t0 + t + a.lookahead], plane0, (uint32_t)(NN * 4), N3, false);
+    __syncthreads();
+
+    const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
+    const bool active = line < N;
+    const bool has2 = q.c >= 0;
+
+    // y lines (thread owns column x): stage 0 straight from the functions
+    if (active) {
+        const int x = line;
+        const float* pa = reinterpret_cast<const float*>(a.fl) + q.a * N3 + plane0 + x;
+        const float* pb = reinterpret_cast<const float*>(a.fr) + q.b * N3 + plane0 + x;
+        const float* pc = reinterpret_cast<const float*>(a.fl) + (has2 ? q.c : q.a) * N3 + plane0 + x;
+        const float* pd = reinterpret_cast<const float*>(a.fr) + (has2 ? q.d : q.b) * N3 + plane0 + x;
+        for (int j = h; j < G::M0; j += 2) {
+            cx<float> u[G::R0];
+#pragma unroll
+            for (int k = 0; k < G::R0; ++k) {
+                const long long r = (long long)(j + k * G::M0) * N;
+                u[k].re = __ldg(pa + r) * __ldg(pb + r);
+                u[k].im = has2 ? __ldg(pc + r) * __ldg(pd + r) : 0.0f;
+            }
+            Dft<G::R0, -1, float>::run(u);
+            tw_out<G::R0>(u, tw, j);
+#pragma unroll
+            for (int s = 0; s < G::R0; ++s) tile[(j + s * G::M0) * G::P + x] = u[s];
+        }
+    }
+    __syncwarp();
+    if (active) {
+        const int x = line;
+        for (int b = h; b < G::B1; b += 2) {
+            cx<float> u[G::R1];
+#pragma unroll
+            for (int k = 0; k < G::R1; ++k) u[k] = tile[(b * G::R1 + k) * G::P + x];
+            Dft<G::R1, -1, float>::run(u);
+#pragma unroll
+            for (int s = 0; s < G::R1; ++s) tile[(b * G::R1 + s) * G::P + x] = u[s];
+        }
+    }
+    __syncthreads();
+
+    // x lines (thread owns row y): stage 0 in shared memory, stage 1 to the
+    // transposed spectrum plane
+    if (active) {
+        cx<float>* row = tile + line * G::P;
+        for (int j = h; j < G::M0; j += 2) {
+            cx<float> u[G::R0];
+#pragma unroll
+            for (int k = 0; k < G::R0; ++k) u[k] = row[j + k * G::M0];
+            Dft<G::R0, -1, float>::run(u);
+            tw_out<G::R0>(u, tw, j);
+#pragma unroll
+            for (int s = 0; s < G::R0; ++s) row[j + s * G::M0] = u[s];
+        }
+    }
+    __syncwarp();
+    if (active) {
+        const cx<float>* row = tile + line * G::P;
+        cx<float>* out = reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride + plane0 + line;
+        for (int b = h; b < G::B1; b += 2) {
+            cx<float> u[G::R1];
+#pragma unroll
+            for (int k = 0; k < G::R1; ++k) u[k] = row[b * G::R1 + k];
+            Dft<G::R1, -1, float>::run(u);
+#pragma unroll
+            for (int s = 0; s < G::R1; ++s) out[(long long)(b * G::R1 + s) * N] = u[s];
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) inv_accum(PassArgs a) {
+    using G = Geo<N>;
+    constexpr long long NN = (long long)N * N, N3 = NN * N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[2 * (G::NT / 32)];
+    cx<float>* tile = reinterpret_cast<cx<float>*>(smem_raw);
+    cx<float>* tw = tile + N * G::P;
+    const int z = blockIdx.x, t = blockIdx.y;
+    const long long plane0 = (long long)z * NN;
+    const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
+    const bool active = line < N;
+    // The thread's share of the transposed spectrum plane (the inputs of its
+    // first x-line butterflies) goes to its row of the tile by 8-byte
+    // asynchronous copies, all in flight at once.
+    if (active) {
+        const cx<float>* in = reinterpret_cast<const cx<float>*>(a.src) + t * a.src_tstride + plane0 + line;
+        cx<float>* row = tile + line * G::P;
+        for (int b = h; b < G::B1; b += 2)
+#pragma unroll
+            for (int k = 0; k < G::R1; ++k) cp_async8(row + b * G::R1 + k, in + (long long)(b * G::R1 + k) * N);
+    }
+    cp_async_commit();
+    const Quad q = a.quads[a.t0 + t];
+    for (int j = threadIdx.x; j < N; j += G::NT) tw[j] = reinterpret_cast<const cx<float>*>(a.twx)[j];
+    // the accumulation reads up to four function planes and updates up to four
+    // accumulator planes at the end: start pulling them into L2 now
+    if (threadIdx.x == 32 && (NN * 4) % 16 == 0) prefetch_planes(a, q, plane0, (uint32_t)(NN * 4), N3, true);
+    cp_async_wait_all();
+    __syncthreads();
+
+    // x lines (thread owns row y): both inverse stages in shared memory
+    if (active) {
+        cx<float>* row = tile + line * G::P;
+        for (int b = h; b < G::B1; b += 2) {
+            cx<float> u[G::R1];
+#pragma unroll
+            for (int k = 0; k < G::R1; ++k) u[k] = row[b * G::R1 + k];
+            Dft<G::R1, +1, float>::run(u);
+#pragma unroll
+            for (int s = 0; s < G::R1; ++s) row[b * G::R1 + s] = u[s];
+        }
+    }
+    __syncwarp();
+    if (active) {
+        cx<float>* row = tile + line * G::P;
+        for (int j = h; j < G::M0; j += 2) {
+            cx<float> u[G::R0];
+#pragma unroll
+            for (int k = 0; k < G::R0; ++k) u[k] = row[j + k * G::M0];
+            tw_in_conj<G::R0>(u, tw, j);
+            Dft<G::R0, +1, float>::run(u);
+#pragma unroll
+            for (int s = 0; s < G::R0; ++s) row[j + s * G::M0] = u[s];
+        }
+    }
+    __syncthreads();
+
+    // y lines (thread owns column x): both inverse stages in shared memory
+    if (active) {
+        const int x = line;
+        for (int b = h; b < G::B1; b += 2) {
+            cx<float> u[G::R1];
+#pragma unroll
+            for (int k = 0; k < G::R1; ++k) u[k] = tile[(b * G::R1 + k) * G::P + x];
+            Dft<G::R1, +1, float>::run(u);
+#pragma unroll
+            for (int s = 0; s < G::R1; ++s) tile[(b * G::R1 + s) * G::P + x] = u[s];
+        }
+    }
+    __syncwarp();
+    if (active) {
+        const int x = line;
+        for (int j = h; j < G::M0; j += 2) {
+            cx<float> u[G::R0];
+#pragma unroll
+            for (int k = 0; k < G::R0; ++k) u[k] = tile[(j + k * G::M0) * G::P + x];
+            tw_in_conj<G::R0>(u, tw, j);
+            Dft<G::R0, +1, float>::run(u);
+#pragma unroll
+            for (int s = 0; s < G::R0; ++s) tile[(j + s * G::M0) * G::P + x] = u[s];
+        }
+    }
+    __syncthreads();
+
+    // Exchange accumulation (Eq. 2) and pair energies (Eq. 4) in 4-wide
+    // vectors: a half-warp takes 4 rows x 16 columns, lane (r, c) the four
+    // columns 4c .. 4c + 3 of row r; with the pitch P = 1 (mod 16) its 16
+    // lanes read 16 distinct bank pairs.
+    float e1 = 0.0f, e2 = 0.0f;
+    {
+        const bool has2 = q.c >= 0, share = has2 && q.c == q.a, sym = a.symmetric != 0;
+        const bool upd_b = sym && q.a != q.b, upd_d = sym && has2 && q.c != q.d;
+        const float* la_p = reinterpret_cast<const float*>(a.fl) + q.a * N3 + plane0;
+        const float* rb_p = reinterpret_cast<const float*>(a.fr) + q.b * N3 + plane0;
+        const float* lc_p = reinterpret_cast<const float*>(a.fl) + (has2 ? q.c : q.a) * N3 + plane0;
+        const float* rd_p = reinterpret_cast<const float*>(a.fr) + (has2 ? q.d : q.b) * N3 + plane0;
+        float* wa_p = reinterpret_cast<float*>(a.accl) + q.a * N3 + plane0;
+        float* wc_p = reinterpret_cast<float*>(a.accl) + (has2 ? q.c : q.a) * N3 + plane0;
+        float* wb_p = sym ? reinterpret_cast<float*>(a.accr) + q.b * N3 + plane0 : nullptr;
+        float* wd_p = sym ? reinterpret_cast<float*>(a.accr) + (has2 ? q.d : q.b) * N3 + plane0 : nullptr;
+        const int hw = threadIdx.x >> 4, l16 = threadIdx.x & 15;
+        const int rr = l16 & 3, cc = l16 >> 2;
+        // N^2 / 64 tasks over N / 8 half-warps: N / 8 tasks each, taken U at a
+        // time with every load of the U tasks issued before the first update
+        constexpr int HW = G::NT / 16, PER = (N / 4) * (N / 16) / HW, U = PER % 2 == 0 ? 2 : 1;
+        static_assert(PER * HW == (N / 4) * (N / 16), "tasks divide evenly");
+        for (int k0 = 0; k0 < PER; k0 += U) {
+            float4 la[U], rb[U], lc[U], rd[U];
+            long long rof[U];
+            int sof[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int task = hw + (k0 + u) * HW;
+                const int y = (task / (N / 16)) * 4 + rr, x = (task % (N / 16)) * 16 + 4 * cc;
+                rof[u] = (long long)y * N + x;
+                sof[u] = y * G::P + x;
+                la[u] = ldg4(la_p + rof[u]);
+                rb[u] = ldg4(rb_p + rof[u]);
+                if (has2) {
+                    lc[u] = ldg4(lc_p + rof[u]);
+                    rd[u] = ldg4(rd_p + rof[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const cx<float>* src = tile + sof[u];
+                const cx<float> v[4] = {src[0], src[1], src[2], src[3]};
+                const float4 v1 = make_float4(v[0].re, v[1].re, v[2].re, v[3].re);
+                const float4 v2 = make_float4(v[0].im, v[1].im, v[2].im, v[3].im);
+                const long long r = rof[u];
+                float4 wa = mul4(v1, rb[u]);
+                e1 += dot4(mul4(la[u], rb[u]), v1);
+                if (has2) {
+                    e2 += dot4(mul4(lc[u], rd[u]), v2);
+                    if (share)
+                        wa = fma4(v2, rd[u], wa);
+                    else
+                        red_add4(wc_p + r, mul4(v2, rd[u]));
+                    if (upd_d) red_add4(wd_p + r, mul4(v2, lc[u]));
+                }
+                red_add4(wa_p + r, wa);
+                if (upd_b) red_add4(wb_p + r, mul4(v1, la[u]));
+            }
+        }
+    }
+    if (a.e_part != nullptr) {
+        double d1 = double(e1), d2 = double(e2);
+        for (int o = 16; o > 0; o >>= 1) {
+            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+            d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        }
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) {
+            red[2 * warp] = d1;
+            red[2 * warp + 1] = d2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s1 = 0, s2 = 0;
+            for (int w = 0; w < G::NT / 32; ++w) {
+                s1 += red[2 * w];
+                s2 += red[2 * w + 1];
+            }
+            double* dst = a.e_part + ((long long)(a.t0 + t) * gridDim.x + z) * 2;
+            dst[0] = s1;
+            dst[1] = s2;
+        }
+    }
+}
+
+template <typename K>
+cudaError_t launch_plane(K k, size_t smem, int n, int nt, const PassArgs& a, int batch, cudaStream_t st) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)n, (unsigned)batch);
+    k<<<grid, nt, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace plane_detail
+
+// which: 0 = pair product + forward plane FFT, 1 = inverse plane FFT + accumulation
+template <int N>
+cudaError_t tplane_launch(int which, const PassArgs& a, int batch, cudaStream_t st) {
+    using G = plane_detail::Geo<N>;
+    if (which == 0) return plane_detail::launch_plane(plane_detail::pair_fwd<N>, G::smem, N, G::NT, a, batch, st);
+    return plane_detail::launch_plane(plane_detail::inv_accum<N>, G::smem, N, G::NT, a, batch, st);
+}
+
+}  // namespace ace

@@ -2,19 +2,21 @@
 // compile-time N^3 boxes: forward FFT along z, times the Coulomb kernel
 // 4 pi / |G|^2 / N (G = 0 dropped), inverse FFT along z.
 //
-// Geometry: every thread owns one z line (pencil) and runs all of its
-// butterflies itself, so no two threads ever exchange data and no block-wide
-// barrier is needed.  A warp owns G consecutive pencils of the (y, x) plane
-// (G consecutive complex values per z row, 8 G bytes, one bulk copy each), so
-// at every step its lanes touch G adjacent shared-memory words (no bank
-// conflicts) and G adjacent global words (full sectors).  Blocks are one warp.
+// Geometry: every z line (pencil) belongs to two lanes of one warp (lanes l
+// and l + 16), which split its butterflies, so stages need only __syncwarp and
+// no block-wide barrier exists.  A warp owns G <= 16 consecutive pencils of
+// the plane (G consecutive complex values per z row, 8 G bytes, one bulk copy
+// each), so at every step each half-warp touches G adjacent shared-memory
+// words (no bank conflicts) and G adjacent global words (full sectors).
+// Blocks are one warp.
 //
 // Per pencil the stages are: forward stages 0 .. S-2 in shared memory; the
 // last forward stage, the Coulomb factors and the first inverse stage fused
 // in registers (they act on the same butterflies); inverse stages S-2 .. 1 in
 // shared memory; inverse stage 0 from shared memory straight to global memory.
 // The Coulomb factors come from a table in the spectrum's own layout
-// (digit-reversed z position, stored (y, x) slot), read once per element.
+// (digit-reversed z position, then the plane's stored slot), read once per
+// element; the pass itself never needs to know the plane layout.
 #pragma once
 
 #include "fft_core.cuh"
@@ -27,10 +29,10 @@ namespace zline_detail {
 // Stage of the forward (SGN < 0) or inverse (SGN > 0) transform on one pencil
 // held in shared memory with element stride G.
 template <int RAD, int SGN, int N, int LB, int G>
-__device__ __forceinline__ void pencil_stage(cx<float>* col, const cx<float>* tw) {
+__device__ __forceinline__ void pencil_stage(cx<float>* col, const cx<float>* tw, int h) {
     constexpr int M = LB / RAD, NB = N / RAD, TS = N / LB;
 #pragma unroll 2
-    for (int i = 0; i < NB; ++i) {
+    for (int i = h; i < NB; i += 2) {
         const int beta = i / M, j = i - beta * M;
         butterfly_core<RAD, SGN, float>(col + (beta * LB + j) * G, M * G, tw, TS * j, M > 1 && j > 0);
     }
@@ -39,11 +41,11 @@ __device__ __forceinline__ void pencil_stage(cx<float>* col, const cx<float>* tw
 // Last forward stage (blocks of RAD adjacent positions, no twiddles), the
 // Coulomb factors, and the first inverse stage on the same RAD positions.
 template <int RAD, int N, int G>
-__device__ __forceinline__ void pencil_middle(cx<float>* col, const float* krow) {
+__device__ __forceinline__ void pencil_middle(cx<float>* col, const float* krow, int h) {
     constexpr int NB = N / RAD;
     constexpr long long NN = (long long)N * N;
 #pragma unroll 2
-    for (int beta = 0; beta < NB; ++beta) {
+    for (int beta = h; beta < NB; beta += 2) {
         float k[RAD];
         cx<float> u[RAD];
 #pragma unroll
@@ -62,11 +64,11 @@ __device__ __forceinline__ void pencil_middle(cx<float>* col, const float* krow)
 // Inverse stage 0 (blocks of the whole line): conjugate twiddles, butterfly,
 // and the results in natural order straight to global memory (stride N^2).
 template <int RAD, int N, int G>
-__device__ __forceinline__ void pencil_last(const cx<float>* col, const cx<float>* tw, cx<float>* out) {
+__device__ __forceinline__ void pencil_last(const cx<float>* col, const cx<float>* tw, cx<float>* out, int h) {
     constexpr int M = N / RAD;
     constexpr long long NN = (long long)N * N;
 #pragma unroll 2
-    for (int j = 0; j < M; ++j) {
+    for (int j = h; j < M; j += 2) {
         cx<float> u[RAD];
 #pragma unroll
         for (int q = 0; q < RAD; ++q) u[q] = col[(j + q * M) * G];
@@ -88,7 +90,7 @@ template <int N, int G>
 __global__ void __launch_bounds__(32) zline_coulomb(PassArgs a) {
     using PL = CPlan<N>;
     static_assert(PL::stages >= 2, "the fused middle needs two stages or more");
-    static_assert(G % 2 == 0 && G <= 32 && (N * N) % G == 0, "pencil group");
+    static_assert(G % 2 == 0 && G <= 16 && (N * N) % G == 0, "pencil group");
     constexpr long long NN = (long long)N * N;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
@@ -114,20 +116,24 @@ __global__ void __launch_bounds__(32) zline_coulomb(PassArgs a) {
         mbar_wait_bounded(&bar, 0, nullptr, 0);
         return;
     }
-    if (lane >= G) return;
-
-    cx<float>* col = buf + lane;
+    // lanes past the group's pencils (G < 16) skip every step but the syncs
+    const int pl = lane & 15, h = lane >> 4;
+    const bool on = pl < G;
+    cx<float>* col = buf + pl;
     CLoop<0, PL::stages - 1>::run([&](auto sc) {
         constexpr int s = decltype(sc)::value;
-        pencil_stage<PL::radix(s), -1, N, PL::block_len(s), G>(col, tw);
+        if (on) pencil_stage<PL::radix(s), -1, N, PL::block_len(s), G>(col, tw, h);
+        __syncwarp();
     });
-    pencil_middle<PL::radix(PL::stages - 1), N, G>(col, reinterpret_cast<const float*>(a.kern) + p0 + lane);
+    if (on) pencil_middle<PL::radix(PL::stages - 1), N, G>(col, reinterpret_cast<const float*>(a.kern) + p0 + pl, h);
+    __syncwarp();
     CLoop<0, PL::stages - 2>::run([&](auto sc) {
         constexpr int s = PL::stages - 2 - decltype(sc)::value;
-        pencil_stage<PL::radix(s), +1, N, PL::block_len(s), G>(col, tw);
+        if (on) pencil_stage<PL::radix(s), +1, N, PL::block_len(s), G>(col, tw, h);
+        __syncwarp();
     });
-    cx<float>* out = reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride + p0 + lane;
-    pencil_last<PL::radix(0), N, G>(col, tw, out);
+    cx<float>* out = reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride + p0 + pl;
+    if (on) pencil_last<PL::radix(0), N, G>(col, tw, out, h);
 }
 
 }  // namespace zline_detail
