@@ -106,6 +106,29 @@ int ace_build(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const 
               const int32_t* pair_col, void* xi, double* E_x, void* stream);
 
 /*
+ * The two halves of ace_build, for a build whose pairs are split over several
+ * GPUs (the pair terms of Eq. 2-4 are independent; W and E_x are sums over
+ * pairs, so the only exchange is one sum over the shards):
+ *   ace_build_pairs: phi(r), the Poisson solve of every listed pair and the
+ *     exchange accumulation, restricted to this shard's pairs:
+ *       W_G    [n_occ][n_pw_half] device output, alpha-scaled V_X Phi over the
+ *              listed pairs only (zero where no listed pair touches a row)
+ *       E_part host output (may be NULL), -alpha sum (2 - d_ij) e_ij over the
+ *              listed pairs
+ *     pair_row_ptr/pair_col as in ace_build (all n_occ rows; a shard's rows
+ *     may be empty; both NULL = every pair).  Synchronises the stream.
+ *   ace_build_finish: with W_G summed over the shards (by the caller, e.g. an
+ *     allreduce), M = Phi^T W, -M = L L^T, xi = W L^-T into xi
+ *     [n_occ][n_pw_half] device.  ACE_ERR_NOT_POSDEF as ace_build.
+ *     Synchronises the stream.
+ * When the shards' pair lists partition the full list, summing the shards'
+ * W_G and E_part and finishing gives ace_build's xi and E_x up to rounding.
+ */
+int ace_build_pairs(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const int32_t* pair_row_ptr,
+                    const int32_t* pair_col, void* W_G, double* E_part, void* stream);
+int ace_build_finish(ace_plan* plan, const void* psi_G, int n_occ, const void* W_G, void* xi, void* stream);
+
+/*
  * Apply the compressed operator (Eq. 5, an inner MTS step):
  *   Kpsi = -xi (xi^T psi), with the Gamma-point inner product
  *   <a|b> = 2 Re sum_{half} a^* b - a(0) b(0).

@@ -23,7 +23,7 @@ _ERRORS = {-1: "ACE_ERR_INVALID_ARG", -2: "ACE_ERR_GRID_TOO_SMALL", -3: "ACE_ERR
            -5: "ACE_ERR_CUDA", -6: "ACE_ERR_TIMEOUT"}
 SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_apply", "hfx_apply_exact",
            "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc",
-           "ace_build_batched", "ace_save", "ace_load")
+           "ace_build_batched", "ace_save", "ace_load", "ace_build_pairs", "ace_build_finish")
 
 _lib = None
 
@@ -75,6 +75,8 @@ def load(build_if_missing=False):
     lib.ace_gvec.argtypes = [P, ctypes.POINTER(i32), P]
     lib.ace_build.argtypes = [P, P, i32, f64, P, P, P, ctypes.POINTER(f64), P]
     lib.ace_apply.argtypes = [P, P, i32, P, i32, P, P]
+    lib.ace_build_pairs.argtypes = [P, P, i32, f64, P, P, P, ctypes.POINTER(f64), P]
+    lib.ace_build_finish.argtypes = [P, P, i32, P, P, P]
     lib.ace_apply_noalloc.argtypes = [P, i32, P, i32, i32, i32, P, P]
     lib.hfx_apply_exact.argtypes = [P, P, i32, f64, P, i32, P, P]
     lib.ace_last_intermediates.argtypes = [P, P, P, P]
@@ -189,6 +191,42 @@ def ace_build(plan, psi_G, alpha, pairs=None, xi=None, stream=None):
                             col.ctypes.data_as(ctypes.c_void_p) if col is not None else None,
                             _ptr(xi), ctypes.byref(E), _stream(stream)))
     return xi, E.value
+
+
+def ace_build_pairs(plan, psi_G, alpha, pairs=None, W_G=None, stream=None):
+    """Pair half of a build split over shards: returns (W_G, E_part) over the
+    listed pairs only.  pairs = (row_ptr, col) CSR over all n_occ rows (rows may
+    be empty), or None for every pair."""
+    import torch
+    psi_G = plan._vec(psi_G, "psi_G")
+    n_occ = psi_G.shape[0]
+    if W_G is None:
+        W_G = torch.empty_like(psi_G)
+    plan._vec(W_G, "W_G")
+    rp = col = None
+    if pairs is not None:
+        rp = np.ascontiguousarray(pairs[0], dtype=np.int32)
+        col = np.ascontiguousarray(pairs[1], dtype=np.int32)
+    E = ctypes.c_double(0.0)
+    _check(load().ace_build_pairs(plan.handle, _ptr(psi_G), n_occ, float(alpha),
+                                  rp.ctypes.data_as(ctypes.c_void_p) if rp is not None else None,
+                                  col.ctypes.data_as(ctypes.c_void_p) if col is not None else None,
+                                  _ptr(W_G), ctypes.byref(E), _stream(stream)))
+    return W_G, E.value
+
+
+def ace_build_finish(plan, psi_G, W_G, xi=None, stream=None):
+    """Dense half of a split build: M = Phi^T W, Cholesky, xi = W L^-T, from
+    W_G summed over the shards."""
+    import torch
+    psi_G = plan._vec(psi_G, "psi_G")
+    plan._vec(W_G, "W_G")
+    if xi is None:
+        xi = torch.empty_like(psi_G)
+    plan._vec(xi, "xi")
+    _check(load().ace_build_finish(plan.handle, _ptr(psi_G), psi_G.shape[0], _ptr(W_G), _ptr(xi),
+                                   _stream(stream)))
+    return xi
 
 
 def ace_apply(plan, xi, psi, out=None, stream=None):

@@ -476,11 +476,13 @@ int upload_quads(ace_plan* P, const std::vector<Quad>& q, cudaStream_t st) {
     return ACE_OK;
 }
 
-// Enqueue one ACE build on stream st (inputs already validated for the Gamma
-// point); the status and E_x land in the plan's pinned host slots.
+// Enqueue the pair part of an ACE build on stream st (inputs already
+// validated for the Gamma point): phi(r), every listed pair's Poisson solve
+// with the exchange accumulation (Eq. 2-4), W -> W_G (into WG) and E_x over
+// the listed pairs (into the plan's pinned host slot).
 template <typename R>
-int build_enqueue(ace_plan* P, const void* psi_G, int n_occ, double alpha, const int32_t* rp, const int32_t* col,
-                  void* xi, cudaStream_t st) {
+int pairs_enqueue(ace_plan* P, const void* psi_G, int n_occ, double alpha, const int32_t* rp, const int32_t* col,
+                  void* WG_out, cudaStream_t st) {
     std::vector<int> pa, pb;
     if (rp) {
         if (rp[0] != 0) return fail(ACE_ERR_INVALID_ARG, "pair_row_ptr[0] must be 0");
@@ -518,8 +520,19 @@ int build_enqueue(ace_plan* P, const void* psi_G, int n_occ, double alpha, const
     mark(P, PH_ENERGY, st);
     ACE_CKL(launch_energy_reduce(P->d_epart, d_pq, n_pair_t, P->ntiles_last, -alpha * P->omega / (double)P->N,
                                  P->d_E, st));
-    cx<R>* WG = (cx<R>*)P->d_WG;
+    cx<R>* WG = (cx<R>*)WG_out;
     ACE_TRY(run_to_recip<R>(P, acc, d_oq, n_orb_t, -alpha * std::sqrt(P->omega) / (double)P->N, WG, st));
+    ACE_CK(cudaMemcpyAsync(&P->h_res->E, P->d_E, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return ACE_OK;
+}
+
+// Enqueue the dense part of an ACE build: M = Phi^T W, -M = L L^T, and
+// xi = W L^-T (Section 2.2); the Cholesky status lands in the plan's pinned
+// host slot.
+template <typename R>
+int finish_enqueue(ace_plan* P, const void* psi_G, int n_occ, const void* WG_in, void* xi, cudaStream_t st) {
+    const cx<R>* psi = (const cx<R>*)psi_G;
+    const cx<R>* WG = (const cx<R>*)WG_in;
     ACE_TRY(gram<R>(P, psi, n_occ, WG, n_occ, P->d_M, st));
     mark(P, PH_FACTOR, st);
     ACE_CKL(launch_neg_cholesky_inverse(P->d_M, n_occ, P->d_L, P->d_Linv, P->d_status, st));
@@ -527,9 +540,17 @@ int build_enqueue(ace_plan* P, const void* psi_G, int n_occ, double alpha, const
     ACE_CKL(launch_gemm_nn<R>(P->d_Linv, n_occ, n_occ, (const R*)WG, 2LL * P->npw, 1.0, (R*)xi, true, st, true));
     mark(P, PH_IDLE, st);
     ACE_CK(cudaMemcpyAsync(&P->h_res->status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    ACE_CK(cudaMemcpyAsync(&P->h_res->E, P->d_E, sizeof(double), cudaMemcpyDeviceToHost, st));
     P->pending_n_occ = n_occ;
     return ACE_OK;
+}
+
+// Enqueue one ACE build on stream st; the status and E_x land in the plan's
+// pinned host slots.
+template <typename R>
+int build_enqueue(ace_plan* P, const void* psi_G, int n_occ, double alpha, const int32_t* rp, const int32_t* col,
+                  void* xi, cudaStream_t st) {
+    ACE_TRY(pairs_enqueue<R>(P, psi_G, n_occ, alpha, rp, col, P->d_WG, st));
+    return finish_enqueue<R>(P, psi_G, n_occ, P->d_WG, xi, st);
 }
 
 // Wait for an enqueued build and report its result.
@@ -540,6 +561,24 @@ int build_finish(ace_plan* P, double* E_x, cudaStream_t st) {
     if (E_x) *E_x = P->h_res->E;
     if (P->h_res->status) return fail(ACE_ERR_NOT_POSDEF, "-M is not positive definite (dependent or zero orbitals)");
     return ACE_OK;
+}
+
+template <typename R>
+int pairs_impl(ace_plan* P, const void* psi_G, int n_occ, double alpha, const int32_t* rp, const int32_t* col,
+               void* WG, double* E_part, cudaStream_t st) {
+    ACE_TRY(check_gamma<R>(P, psi_G, n_occ, st));
+    ACE_TRY(pairs_enqueue<R>(P, psi_G, n_occ, alpha, rp, col, WG, st));
+    ACE_CK(cudaStreamSynchronize(st));
+    ACE_TRY(check_device_error(P, st));
+    if (E_part) *E_part = P->h_res->E;
+    return ACE_OK;
+}
+
+template <typename R>
+int finish_impl(ace_plan* P, const void* psi_G, int n_occ, const void* WG, void* xi, cudaStream_t st) {
+    ACE_TRY(check_gamma<R>(P, psi_G, n_occ, st));
+    ACE_TRY(finish_enqueue<R>(P, psi_G, n_occ, WG, xi, st));
+    return build_finish(P, nullptr, st);
 }
 
 template <typename R>
@@ -786,6 +825,28 @@ int ace_build(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const 
     cudaStream_t st = (cudaStream_t)stream;
     return plan->prec == ACE_FP64 ? build_impl<double>(plan, psi_G, n_occ, alpha, pair_row_ptr, pair_col, xi, E_x, st)
                                   : build_impl<float>(plan, psi_G, n_occ, alpha, pair_row_ptr, pair_col, xi, E_x, st);
+}
+
+int ace_build_pairs(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const int32_t* pair_row_ptr,
+                    const int32_t* pair_col, void* W_G, double* E_part, void* stream) {
+    if (!plan || !psi_G || !W_G) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (n_occ < 1 || n_occ > plan->n_occ_max) return fail(ACE_ERR_INVALID_ARG, "n_occ out of range");
+    if ((pair_row_ptr == nullptr) != (pair_col == nullptr))
+        return fail(ACE_ERR_INVALID_ARG, "pair_row_ptr and pair_col must both be set or both be NULL");
+    DeviceGuard g(plan->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->prec == ACE_FP64
+               ? pairs_impl<double>(plan, psi_G, n_occ, alpha, pair_row_ptr, pair_col, W_G, E_part, st)
+               : pairs_impl<float>(plan, psi_G, n_occ, alpha, pair_row_ptr, pair_col, W_G, E_part, st);
+}
+
+int ace_build_finish(ace_plan* plan, const void* psi_G, int n_occ, const void* W_G, void* xi, void* stream) {
+    if (!plan || !psi_G || !W_G || !xi) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (n_occ < 1 || n_occ > plan->n_occ_max) return fail(ACE_ERR_INVALID_ARG, "n_occ out of range");
+    DeviceGuard g(plan->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->prec == ACE_FP64 ? finish_impl<double>(plan, psi_G, n_occ, W_G, xi, st)
+                                  : finish_impl<float>(plan, psi_G, n_occ, W_G, xi, st);
 }
 
 int ace_apply(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T, void* Kpsi, void* stream) {
