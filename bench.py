@@ -109,21 +109,36 @@ def pair_quads(n):
     return [(pairs[k], pairs[k + 1] if k + 1 < len(pairs) else None) for k in range(0, len(pairs), 2)]
 
 
-def pass_bytes(n, N, esz=4):
-    """Algorithmic HBM bytes of each pair pass summed over one build (FP32):
-    P1 writes the half-transformed spectrum (8N per transform) and reads each
-    distinct orbital of its two pairs once (4N each); P2 reads and writes the
-    spectrum (16N); P3 reads the spectrum (8N), each distinct orbital once
-    (4N) and read-modify-writes each distinct W it updates (8N)."""
+def pass_bytes(n, N, esz=4, batch=64):
+    """Algorithmic HBM bytes of each pair pass over one build (FP32), counted
+    per launch of `batch` packed transforms (the library's launch size on this
+    workload): P1 writes the half-transformed spectrum (8N per transform) and
+    reads each distinct orbital of the launch once (4N); P2 reads and writes
+    the spectrum (16N per transform); P3 reads the spectrum (8N per transform),
+    each distinct orbital of the launch once (4N) and read-modify-writes each
+    distinct W of the launch once (8N).  Returns (bytes per pass, launches)."""
     c = 2 * esz
     tot = {"pair_fwd": 0, "pair_coulomb": 0, "pair_inv": 0}
-    for p, q in pair_quads(n):
-        fs = {p[0], p[1]} | ({q[0], q[1]} if q else set())
-        ws = {p[0], p[1]} | ({q[0], q[1]} if q else set())
-        tot["pair_fwd"] += N * (c + esz * len(fs))
-        tot["pair_coulomb"] += N * 2 * c
-        tot["pair_inv"] += N * (c + esz * len(fs) + 2 * esz * len(ws))
-    return tot
+    quads = pair_quads(n)
+    launches = 0
+    for s0 in range(0, len(quads), batch):
+        chunk = quads[s0:s0 + batch]
+        t = len(chunk)
+        fs = set()
+        for p, q in chunk:
+            fs |= {p[0], p[1]} | ({q[0], q[1]} if q else set())
+        tot["pair_fwd"] += N * (c * t + esz * len(fs))
+        tot["pair_coulomb"] += N * 2 * c * t
+        tot["pair_inv"] += N * (c * t + esz * len(fs) + 2 * esz * len(fs))
+        launches += 1
+    return tot, launches
+
+
+# DRAM bytes per launch (64 transforms) of the pair passes on this workload,
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; see
+# profiles/dram_pair_passes_water32_96cubed.md), for the kernels that run by
+# default; None where the kernel changed since the capture.
+MEASURED_TRAFFIC_PER_LAUNCH = {"pair_fwd": 0.8625e9, "pair_coulomb": 0.8464e9, "pair_inv": 1.7938e9}
 
 
 def cpu_baseline(cfg, seconds_target=15.0):
@@ -260,17 +275,22 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (pass with the largest share of the step)
     hbm, peak_kind = peaks()
-    pb = pass_bytes(n, N)  # bytes of one build
+    pb, n_launch = pass_bytes(n, N)  # bytes of one build, launches of each pass per build
     ntrans = stats["pair_transforms"]
     phase_ms = {"pair_fwd": stats["pair_fwd_ms"], "pair_coulomb": stats["pair_coulomb_ms"],
                 "pair_inv": stats["pair_inv_ms"]}
     dom = max(phase_ms, key=phase_ms.get)
-    per_launch = pb[dom] / max(1, ntrans // args.steps) * 64  # a launch processes 64 transforms
+    per_launch = pb[dom] / n_launch
     achieved = pb[dom] * args.steps / (phase_ms[dom] / 1e3) / 1e9 if phase_ms[dom] > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
-                "algorithmic_bytes_per_launch": per_launch, "transforms_per_step": ntrans // args.steps,
-                "share_of_step": phase_ms[dom] / max(stats["total_ms"], 1e-9)}
+                "frac": achieved / hbm, "peak_kind": peak_kind,
+                "traffic": MEASURED_TRAFFIC_PER_LAUNCH.get(dom) if world == 1 else None,
+                "algorithmic_bytes_per_launch": per_launch, "launches_per_step": n_launch,
+                "transforms_per_step": ntrans // args.steps,
+                "share_of_step": phase_ms[dom] / max(stats["total_ms"], 1e-9),
+                "all_passes": {k: {"ms_per_step": phase_ms[k] / args.steps,
+                                   "achieved_gbs": pb[k] * args.steps / (phase_ms[k] / 1e3) / 1e9
+                                   if phase_ms[k] > 0 else 0.0} for k in phase_ms}}
     gpu_launches = int(stats["launches"]) + 0
 
     # ---- end to end through the public API with host buffers
