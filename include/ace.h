@@ -72,6 +72,8 @@ typedef struct {
     int pair_batch;    /* packed pair transforms per pass launch; 0 = automatic */
     int kernels;       /* 0: fastest available; 1: CUDA-core Gram products instead of
                           tcgen05 tensor cores; 2: also generic (runtime-size) FFT passes */
+    int pair_streams;  /* streams the pair sub-batches overlap on; 0 = automatic (2),
+                          1 = every pass in order on the call's stream */
 } ace_opts;
 
 /*
@@ -209,11 +211,14 @@ int ace_load(const char* path, const ace_plan* plan, void* xi, int* n_occ, doubl
 int ace_last_intermediates(ace_plan* plan, void* W_G, double* M, void* stream);
 
 /*
- * Per-phase device time, from CUDA events recorded on the call's stream while
- * timing is enabled (ace_set_timing), summed over the calls since the last
- * ace_get_stats.  ace_get_stats synchronises with the recorded events and
- * resets the sums.  Counters (transforms, launches) are kept whether timing
- * is on or not.
+ * Per-phase device time, from CUDA events recorded while timing is enabled
+ * (ace_set_timing), summed over the calls since the last ace_get_stats.  The
+ * pair passes run in sub-batches on two streams forked from the call's stream
+ * (they overlap); each pass is timed on the stream that runs it, so the three
+ * pair phases can add up to more than their wall time.  total_ms is the wall
+ * time of the calls on their own stream.  ace_get_stats synchronises with the
+ * recorded events and resets the sums.  Counters (transforms, launches) are
+ * kept whether timing is on or not.
  */
 typedef struct {
     double orbitals_ms;       /* psi_G -> phi(r): scatter and inverse FFT passes */
@@ -225,9 +230,10 @@ typedef struct {
     double factor_ms;         /* Cholesky of -M and the inverse factor */
     double xi_ms;             /* xi = L^-1 W, and -xi C in the apply */
     double energy_ms;         /* E_x reduction */
-    double total_ms;          /* all of the above */
+    double total_ms;          /* wall time of the calls */
     long long pair_transforms;  /* packed pair transforms (two pairs each) */
     long long launches;         /* kernels launched by the library */
+    double pair_wall_ms;        /* wall time of the pair passes (all streams) */
 } ace_stats;
 
 int ace_set_timing(ace_plan* plan, int enable);

@@ -41,7 +41,7 @@ class _System(ctypes.Structure):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("pair_batch", ctypes.c_int), ("kernels", ctypes.c_int)]
+    _fields_ = [("pair_batch", ctypes.c_int), ("kernels", ctypes.c_int), ("pair_streams", ctypes.c_int)]
 
 
 STAT_FIELDS = ("orbitals_ms", "pair_fwd_ms", "pair_coulomb_ms", "pair_inv_ms", "w_to_g_ms", "gram_ms", "factor_ms",
@@ -50,7 +50,8 @@ STAT_FIELDS = ("orbitals_ms", "pair_fwd_ms", "pair_coulomb_ms", "pair_inv_ms", "
 
 class _Stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_double) for f in STAT_FIELDS] + [("pair_transforms", ctypes.c_longlong),
-                                                               ("launches", ctypes.c_longlong)]
+                                                               ("launches", ctypes.c_longlong),
+                                                               ("pair_wall_ms", ctypes.c_double)]
 
 
 def library_path():
@@ -114,14 +115,14 @@ class Plan:
     """One system: grid, cell (rows = lattice vectors, bohr), cutoff (Ry),
     the largest occupied set, and the precision ("mixed" or "fp64")."""
 
-    def __init__(self, grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0, kernels=0):
+    def __init__(self, grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0, kernels=0, pair_streams=0):
         lib = load()
         self.precision = precision
         self.prec = ACE_MIXED if precision == "mixed" else ACE_FP64
         g = np.ascontiguousarray(np.asarray(grid, dtype=np.int32).reshape(3))
         c = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(9))
         h = ctypes.c_void_p()
-        opts = _Opts(int(pair_batch), int(kernels))
+        opts = _Opts(int(pair_batch), int(kernels), int(pair_streams))
         _check(lib.ace_plan_create(ctypes.byref(h), g.ctypes.data_as(ctypes.c_void_p),
                                    c.ctypes.data_as(ctypes.c_void_p), float(ecut), int(n_occ_max), self.prec,
                                    ctypes.byref(opts)))
@@ -155,9 +156,10 @@ class Plan:
         return t
 
 
-def ace_plan_create(grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0, kernels=0):
-    """kernels: 0 fastest available, 1 CUDA-core Gram products, 2 also generic FFT passes."""
-    return Plan(grid, cell, ecut, n_occ_max, precision, pair_batch, kernels)
+def ace_plan_create(grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0, kernels=0, pair_streams=0):
+    """kernels: 0 fastest available, 1 CUDA-core Gram products, 2 also generic FFT passes;
+    pair_streams: 0 automatic (2), 1 every pair pass in order on the call's stream."""
+    return Plan(grid, cell, ecut, n_occ_max, precision, pair_batch, kernels, pair_streams)
 
 
 def ace_plan_destroy(plan):
@@ -277,6 +279,7 @@ def ace_get_stats(plan):
     d = {f: getattr(st, f) for f in STAT_FIELDS}
     d["pair_transforms"] = st.pair_transforms
     d["launches"] = st.launches
+    d["pair_wall_ms"] = st.pair_wall_ms
     return d
 
 

@@ -95,6 +95,11 @@ struct ace_plan {
     float* d_kern = nullptr;   // 4 pi / |G|^2 / N in spectrum layout (zline only)
     bool tplane = false;       // pair passes with transposed spectrum planes (plane.cuh; needs zline; opt-in)
     int pair_tile = 0;         // pairs ordered in pair_tile x pair_tile orbital blocks (0: row by row; env ACE_PAIR_TILE)
+    int pair_streams = 2;      // concurrent streams of pair sub-batches (env ACE_PAIR_STREAMS)
+    int pair_sub = 0;          // transforms per sub-batch (0: batch / pair_streams; env ACE_PAIR_SUB)
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> aux_ev;
+    cudaEvent_t fork_ev = nullptr;
     PassShape s_xy{}, s_x{}, s_y{}, s_z{};
     int ntiles_last = 1;  // tiles of the pass that accumulates W
     int batch = 1;
@@ -131,16 +136,24 @@ struct ace_plan {
     // phase of the event that opens it (PH_IDLE closes a call)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, cudaEvent_t>> marks;
+    struct Mark {
+        int phase;
+        cudaEvent_t ev;
+        int lane;  // 0: the call's stream; k + 1: pair stream k
+    };
+    std::vector<Mark> marks;
     long long pair_transforms = 0;
     long long launches = 0;
 };
 
 namespace {
 
-enum Phase { PH_IDLE = -1, PH_ORB = 0, PH_PFWD, PH_PCOUL, PH_PINV, PH_W2G, PH_GRAM, PH_FACTOR, PH_XI, PH_ENERGY, PH_N };
+// PH_PAIRWALL: the wall time of pair passes spread over the pair streams
+// (counted in the total only; the passes themselves are timed per stream)
+enum Phase { PH_IDLE = -1, PH_ORB = 0, PH_PFWD, PH_PCOUL, PH_PINV, PH_W2G, PH_GRAM, PH_FACTOR, PH_XI, PH_ENERGY,
+             PH_PAIRWALL, PH_N };
 
-void mark(ace_plan* P, int phase, cudaStream_t st) {
+void mark(ace_plan* P, int phase, cudaStream_t st, int lane = 0) {
     if (!P->timing) return;
     cudaEvent_t e;
     if (!P->ev_pool.empty()) {
@@ -151,7 +164,7 @@ void mark(ace_plan* P, int phase, cudaStream_t st) {
         return;
     }
     cudaEventRecord(e, st);
-    P->marks.push_back({phase, e});
+    P->marks.push_back({phase, e, lane});
 }
 
 template <typename T>
@@ -339,7 +352,45 @@ int run_to_recip(ace_plan* P, const R* acc, const Quad* dq, int ntrans, double s
     return ACE_OK;
 }
 
-// Pair Poisson solves with fused exchange accumulation (Eq. 2-4).
+// The passes of one batch of nb packed transforms on stream st, with phase
+// marks in timing lane `lane`.
+template <typename R>
+int pair_batch(ace_plan* P, PassArgs& a, int nb, cudaStream_t st, int lane) {
+    P->pair_transforms += nb;
+    mark(P, PH_PFWD, st, lane);
+    if (P->tplane) {
+        ACE_CKL(tplane_pair_launch(P->n[0], 0, a, nb, st));
+        mark(P, PH_PCOUL, st, lane);
+        ACE_CKL(zline_coulomb_launch(P->n[0], a, nb, st));
+        mark(P, PH_PINV, st, lane);
+        ACE_CKL(tplane_pair_launch(P->n[0], 1, a, nb, st));
+    } else if (P->fused_xy) {
+        ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_PAIR, EPI_STORE, MID_NONE, -1, nb, st));
+        mark(P, PH_PCOUL, st, lane);
+        if (P->zline)
+            ACE_CKL(zline_coulomb_launch(P->n[0], a, nb, st));
+        else
+            ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_COULOMB, -1, nb, st));
+        mark(P, PH_PINV, st, lane);
+        ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_LOAD, EPI_ACCUM, MID_NONE, +1, nb, st));
+    } else {
+        ACE_CKL(launch_pass<R>(a, P->s_x, PRO_PAIR, EPI_STORE, MID_NONE, -1, nb, st));
+        ACE_CKL(launch_pass<R>(a, P->s_y, PRO_LOAD, EPI_STORE, MID_NONE, -1, nb, st));
+        mark(P, PH_PCOUL, st, lane);
+        ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_COULOMB, -1, nb, st));
+        mark(P, PH_PINV, st, lane);
+        ACE_CKL(launch_pass<R>(a, P->s_y, PRO_LOAD, EPI_STORE, MID_NONE, +1, nb, st));
+        ACE_CKL(launch_pass<R>(a, P->s_x, PRO_LOAD, EPI_ACCUM, MID_NONE, +1, nb, st));
+    }
+    return ACE_OK;
+}
+
+// Pair Poisson solves with fused exchange accumulation (Eq. 2-4).  With
+// pair_streams > 1 the transforms go in sub-batches round-robin over that many
+// streams forked from st (each with its own spectrum slots), so one
+// sub-batch's accumulation pass overlaps the next one's transforms; the
+// accumulators take atomic updates, so the streams need no ordering among
+// themselves.
 template <typename R>
 int run_pairs(ace_plan* P, const R* fl, const R* fr, R* accl, R* accr, int symmetric, const Quad* dq, int ntrans,
               double* e_part, cudaStream_t st) {
@@ -351,35 +402,39 @@ int run_pairs(ace_plan* P, const R* fl, const R* fr, R* accl, R* accr, int symme
     a.symmetric = symmetric;
     a.quads = dq;
     a.e_part = e_part;
-    for (int t0 = 0; t0 < ntrans; t0 += P->batch) {
-        const int nb = std::min(P->batch, ntrans - t0);
-        a.t0 = t0;
-        P->pair_transforms += nb;
-        mark(P, PH_PFWD, st);
-        if (P->tplane) {
-            ACE_CKL(tplane_pair_launch(P->n[0], 0, a, nb, st));
-            mark(P, PH_PCOUL, st);
-            ACE_CKL(zline_coulomb_launch(P->n[0], a, nb, st));
-            mark(P, PH_PINV, st);
-            ACE_CKL(tplane_pair_launch(P->n[0], 1, a, nb, st));
-        } else if (P->fused_xy) {
-            ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_PAIR, EPI_STORE, MID_NONE, -1, nb, st));
-            mark(P, PH_PCOUL, st);
-            if (P->zline)
-                ACE_CKL(zline_coulomb_launch(P->n[0], a, nb, st));
-            else
-                ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_COULOMB, -1, nb, st));
-            mark(P, PH_PINV, st);
-            ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_LOAD, EPI_ACCUM, MID_NONE, +1, nb, st));
-        } else {
-            ACE_CKL(launch_pass<R>(a, P->s_x, PRO_PAIR, EPI_STORE, MID_NONE, -1, nb, st));
-            ACE_CKL(launch_pass<R>(a, P->s_y, PRO_LOAD, EPI_STORE, MID_NONE, -1, nb, st));
-            mark(P, PH_PCOUL, st);
-            ACE_CKL(launch_pass<R>(a, P->s_z, PRO_LOAD, EPI_STORE, MID_COULOMB, -1, nb, st));
-            mark(P, PH_PINV, st);
-            ACE_CKL(launch_pass<R>(a, P->s_y, PRO_LOAD, EPI_STORE, MID_NONE, +1, nb, st));
-            ACE_CKL(launch_pass<R>(a, P->s_x, PRO_LOAD, EPI_ACCUM, MID_NONE, +1, nb, st));
+    const int S = std::min(P->pair_streams, P->batch);
+    if (S <= 1 || ntrans <= 0) {
+        for (int t0 = 0; t0 < ntrans; t0 += P->batch) {
+            a.t0 = t0;
+            ACE_TRY(pair_batch<R>(P, a, std::min(P->batch, ntrans - t0), st, 0));
         }
+        return ACE_OK;
+    }
+    const int b = std::max(1, std::min(P->pair_sub > 0 ? P->pair_sub : P->batch / S, P->batch / S));
+    while ((int)P->aux.size() < S) {
+        cudaStream_t s2;
+        cudaEvent_t e2;
+        ACE_CK(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+        P->aux.push_back(s2);
+        ACE_CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+        P->aux_ev.push_back(e2);
+    }
+    if (!P->fork_ev) ACE_CK(cudaEventCreateWithFlags(&P->fork_ev, cudaEventDisableTiming));
+    mark(P, PH_PAIRWALL, st);
+    ACE_CK(cudaEventRecord(P->fork_ev, st));
+    for (int k = 0; k < S; ++k) ACE_CK(cudaStreamWaitEvent(P->aux[k], P->fork_ev, 0));
+    int k = 0;
+    for (int t0 = 0; t0 < ntrans; t0 += b, ++k) {
+        const int slot = k % S;
+        PassArgs a2 = a;
+        a2.t0 = t0;
+        a2.src = a2.dst = (cx<R>*)P->d_spec + (size_t)slot * b * P->N;
+        ACE_TRY(pair_batch<R>(P, a2, std::min(b, ntrans - t0), P->aux[slot], slot + 1));
+    }
+    for (int j = 0; j < S; ++j) {
+        mark(P, PH_IDLE, P->aux[j], j + 1);
+        ACE_CK(cudaEventRecord(P->aux_ev[j], P->aux[j]));
+        ACE_CK(cudaStreamWaitEvent(st, P->aux_ev[j], 0));
     }
     return ACE_OK;
 }
@@ -641,8 +696,11 @@ int apply_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, v
 
 void free_plan(ace_plan* P) {
     if (P->h_res) cudaFreeHost(P->h_res);
-    for (auto& m : P->marks) cudaEventDestroy(m.second);
+    for (auto& m : P->marks) cudaEventDestroy(m.ev);
     for (auto e : P->ev_pool) cudaEventDestroy(e);
+    for (auto s2 : P->aux) cudaStreamDestroy(s2);
+    for (auto e : P->aux_ev) cudaEventDestroy(e);
+    if (P->fork_ev) cudaEventDestroy(P->fork_ev);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
                     P->d_WG, P->d_M, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
                     P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern};
@@ -682,6 +740,9 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     P->tensor_gram = !(opts && opts->kernels >= 1) && sizeof(R) == 4;
     if (const char* env = std::getenv("ACE_LOOKAHEAD")) P->lookahead = std::max(0, std::atoi(env));
     if (const char* env = std::getenv("ACE_PAIR_TILE")) P->pair_tile = std::max(0, std::atoi(env));
+    if (opts && opts->pair_streams > 0) P->pair_streams = opts->pair_streams;
+    if (const char* env = std::getenv("ACE_PAIR_STREAMS")) P->pair_streams = std::max(1, std::atoi(env));
+    if (const char* env = std::getenv("ACE_PAIR_SUB")) P->pair_sub = std::max(0, std::atoi(env));
     ACE_TRY(setup_shapes<R>(P));
     // the compile-time plane kernels of N % 16 == 0 boxes keep x swizzled per row
     const bool swz = P->s_xy.cube && cube_swizzle(P->n[2]);
@@ -1025,17 +1086,31 @@ int ace_set_timing(ace_plan* plan, int enable) {
 int ace_get_stats(ace_plan* plan, ace_stats* out) {
     if (!plan || !out) return fail(ACE_ERR_INVALID_ARG, "null argument");
     DeviceGuard g(plan->dev);
-    double ph[PH_N] = {0};
+    // every timing lane on its own: an interval runs from a mark to the
+    // lane's next mark and belongs to the phase of the first
+    double ph[PH_N] = {0}, wall = 0, pair_wall = 0;
     auto& mk = plan->marks;
-    for (size_t i = 0; i + 1 < mk.size(); ++i) {
-        if (mk[i].first < 0) continue;
-        ACE_CK(cudaEventSynchronize(mk[i + 1].second));
-        float ms = 0;
-        ACE_CK(cudaEventElapsedTime(&ms, mk[i].second, mk[i + 1].second));
-        ph[mk[i].first] += ms;
+    int lanes = 0;
+    for (auto& m : mk) lanes = std::max(lanes, m.lane + 1);
+    for (int l = 0; l < lanes; ++l) {
+        int prev = -1;
+        for (size_t i = 0; i < mk.size(); ++i) {
+            if (mk[i].lane != l) continue;
+            if (prev >= 0 && mk[prev].phase >= 0) {
+                ACE_CK(cudaEventSynchronize(mk[i].ev));
+                float ms = 0;
+                ACE_CK(cudaEventElapsedTime(&ms, mk[prev].ev, mk[i].ev));
+                ph[mk[prev].phase] += ms;
+                if (l == 0) wall += ms;
+                if (l == 0 && (mk[prev].phase == PH_PAIRWALL || mk[prev].phase == PH_PFWD ||
+                               mk[prev].phase == PH_PCOUL || mk[prev].phase == PH_PINV))
+                    pair_wall += ms;
+            }
+            prev = (int)i;
+        }
     }
-    if (!mk.empty()) ACE_CK(cudaEventSynchronize(mk.back().second));
-    for (auto& m : mk) plan->ev_pool.push_back(m.second);
+    for (auto& m : mk) ACE_CK(cudaEventSynchronize(m.ev));
+    for (auto& m : mk) plan->ev_pool.push_back(m.ev);
     mk.clear();
     std::memset(out, 0, sizeof(*out));
     out->orbitals_ms = ph[PH_ORB];
@@ -1047,7 +1122,10 @@ int ace_get_stats(ace_plan* plan, ace_stats* out) {
     out->factor_ms = ph[PH_FACTOR];
     out->xi_ms = ph[PH_XI];
     out->energy_ms = ph[PH_ENERGY];
-    for (int i = 0; i < PH_N; ++i) out->total_ms += ph[i];
+    // wall time of the calls: the intervals of the call's own stream (pair
+    // passes spread over pair streams count there as one interval)
+    out->total_ms = wall;
+    out->pair_wall_ms = pair_wall;
     out->pair_transforms = plan->pair_transforms;
     out->launches = plan->launches;
     plan->pair_transforms = 0;
