@@ -214,7 +214,9 @@ __device__ __forceinline__ void static_fft_rows_swizzled(cx<R>* buf, const cx<R>
 template <int N, int TZ, int TY, int TX, int NT>
 struct CubeShape {
     static constexpr int kMaxThreads = NT;
-    static constexpr int kMinBlocks = (TZ == 1 && TY == N && TX == N) ? 2 : 1;
+    // two resident plane blocks where two N x N complex tiles fit in shared
+    // memory (N <= 108); otherwise one, with the whole register file for it
+    static constexpr int kMinBlocks = (TZ == 1 && TY == N && TX == N && 2 * (N * N * 8 + 4096) <= 227 * 1024) ? 2 : 1;
     static constexpr int n0 = N, n1 = N, n2 = N, tz = TZ, ty = TY, tx = TX;
     static constexpr int axes = (TZ == 1 && TY == N && TX == N) ? 3 : (TZ == N ? 4 : (TZ == 1 && TX == N ? 1 : 2));
     // Plane tiles of N % 16 == 0 boxes are stored (in shared and global memory)
@@ -539,27 +541,54 @@ __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pa
     R e1 = R(0), e2 = R(0);
     const bool share = q.c >= 0 && q.c == q.a;
     if (a.vec) {
-        for (int g = threadIdx.x; g < (tile_elems >> 2); g += S.nt()) {
-            const int e = g << 2;
-            const int ex = e % S.tx, ey = (e / S.tx) % S.ty, ez = e / txy;
-            const long long r = ((long long)(z0 + ez) * S.n1 + (y0 + ey)) * S.n2 + (x0 + ex);
-            const cx<R> v[4] = {tile[S.slot(e)], tile[S.slot(e + 1)], tile[S.slot(e + 2)], tile[S.slot(e + 3)]};
-            const V4<R> v1 = {v[0].re, v[1].re, v[2].re, v[3].re};
-            const V4<R> v2 = {v[0].im, v[1].im, v[2].im, v[3].im};
-            const V4<R> la = ld4(fl + q.a * N + r), rb = ld4(fr + q.b * N + r);
-            V4<R> wa = mul4(v1, rb);
-            e1 += dot4(mul4(la, rb), v1);
-            if (q.c >= 0) {
-                const V4<R> lc = ld4(fl + q.c * N + r), rd = ld4(fr + q.d * N + r);
-                e2 += dot4(mul4(lc, rd), v2);
-                if (share)
-                    wa = fma4(v2, rd, wa);
-                else
-                    red4(accl + q.c * N + r, mul4(v2, rd));
-                if (a.symmetric && q.c != q.d) red4(accr + q.d * N + r, mul4(v2, lc));
+        // two 4-wide float groups per round where the register budget allows
+        // (<= 768 resident threads per SM: 85 registers), else one; every
+        // function load of the round is issued before its first update (the
+        // updates are ordered memory operations)
+        constexpr int U = (sizeof(R) == 4 && Shape::kMaxThreads * Shape::kMinBlocks <= 768) ? 2 : 1;
+        const int groups = tile_elems >> 2;
+        for (int g0 = threadIdx.x; g0 < groups; g0 += U * S.nt()) {
+            V4<R> la[U], rb[U], lc[U], rd[U];
+            long long rr[U];
+            int ee[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int g = g0 + u * S.nt();
+                ee[u] = -1;
+                if (g < groups) {
+                    const int e = g << 2;
+                    const int ex = e % S.tx, ey = (e / S.tx) % S.ty, ez = e / txy;
+                    rr[u] = ((long long)(z0 + ez) * S.n1 + (y0 + ey)) * S.n2 + (x0 + ex);
+                    ee[u] = e;
+                    la[u] = ld4(fl + q.a * N + rr[u]);
+                    rb[u] = ld4(fr + q.b * N + rr[u]);
+                    if (q.c >= 0) {
+                        lc[u] = ld4(fl + q.c * N + rr[u]);
+                        rd[u] = ld4(fr + q.d * N + rr[u]);
+                    }
+                }
             }
-            red4(accl + q.a * N + r, wa);
-            if (a.symmetric && q.a != q.b) red4(accr + q.b * N + r, mul4(v1, la));
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (ee[u] < 0) continue;
+                const int e = ee[u];
+                const long long r = rr[u];
+                const cx<R> v[4] = {tile[S.slot(e)], tile[S.slot(e + 1)], tile[S.slot(e + 2)], tile[S.slot(e + 3)]};
+                const V4<R> v1 = {v[0].re, v[1].re, v[2].re, v[3].re};
+                const V4<R> v2 = {v[0].im, v[1].im, v[2].im, v[3].im};
+                V4<R> wa = mul4(v1, rb[u]);
+                e1 += dot4(mul4(la[u], rb[u]), v1);
+                if (q.c >= 0) {
+                    e2 += dot4(mul4(lc[u], rd[u]), v2);
+                    if (share)
+                        wa = fma4(v2, rd[u], wa);
+                    else
+                        red4(accl + q.c * N + r, mul4(v2, rd[u]));
+                    if (a.symmetric && q.c != q.d) red4(accr + q.d * N + r, mul4(v2, lc[u]));
+                }
+                red4(accl + q.a * N + r, wa);
+                if (a.symmetric && q.a != q.b) red4(accr + q.b * N + r, mul4(v1, la[u]));
+            }
         }
     } else {
         for (int e = threadIdx.x; e < tile_elems; e += S.nt()) {
