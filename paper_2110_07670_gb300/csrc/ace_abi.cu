@@ -97,6 +97,12 @@ struct ace_plan {
     int pair_tile = 0;         // pairs ordered in pair_tile x pair_tile orbital blocks (0: row by row; env ACE_PAIR_TILE)
     int pair_streams = 2;      // concurrent streams of pair sub-batches (env ACE_PAIR_STREAMS)
     int pair_sub = 0;          // transforms per sub-batch (0: batch / pair_streams; env ACE_PAIR_SUB)
+    bool fused = false;        // the pair passes as one persistent kernel (pipeline.cuh; env ACE_FUSED)
+    int fused_lag = 2;         // its steps between a transform's passes (env ACE_FUSED_LAG)
+    int fused_slots = 8;       // its spectrum ring, transforms (env ACE_FUSED_SLOTS)
+    int fused_flags = 1;       // bit 0: L2 discard of dead planes, bit 1: ticket prefetch (env ACE_FUSED_FLAGS)
+    int* d_pipe = nullptr;     // its counters: [3][ntrans] done, ticket, abort
+    size_t pipe_cap = 0;
     std::vector<cudaStream_t> aux;
     std::vector<cudaEvent_t> aux_ev;
     cudaEvent_t fork_ev = nullptr;
@@ -402,6 +408,25 @@ int run_pairs(ace_plan* P, const R* fl, const R* fr, R* accl, R* accr, int symme
     a.symmetric = symmetric;
     a.quads = dq;
     a.e_part = e_part;
+    if (P->fused && ntrans > 0) {
+        // one persistent kernel over every transform (pipeline.cuh)
+        ACE_TRY(grow(&P->d_pipe, &P->pipe_cap, (size_t)3 * ntrans + 2));
+        ACE_CK(cudaMemsetAsync(P->d_pipe, 0, ((size_t)3 * ntrans + 2) * sizeof(int), st));
+        PipeArgs pa;
+        pa.ntrans = ntrans;
+        pa.lag = P->fused_lag;
+        pa.slots = std::min(P->batch, P->fused_slots);
+        pa.done = P->d_pipe;
+        pa.ticket = P->d_pipe + 3 * (size_t)ntrans;
+        pa.abort_flag = pa.ticket + 1;
+        pa.discard = P->fused_flags & 1;
+        pa.prefetch = (P->fused_flags >> 1) & 1;
+        a.t0 = 0;
+        P->pair_transforms += ntrans;
+        mark(P, PH_PAIRWALL, st);
+        ACE_CKL(pipeline_pair_launch(P->n[0], a, pa, st));
+        return ACE_OK;
+    }
     const int S = std::min(P->pair_streams, P->batch);
     if (S <= 1 || ntrans <= 0) {
         for (int t0 = 0; t0 < ntrans; t0 += P->batch) {
@@ -703,7 +728,7 @@ void free_plan(ace_plan* P) {
     if (P->fork_ev) cudaEventDestroy(P->fork_ev);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
                     P->d_WG, P->d_M, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
-                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern};
+                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_pipe};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -755,6 +780,12 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     P->tplane = false;
     if (const char* env = std::getenv("ACE_TPLANE"))
         P->tplane = P->zline && tplane_supported(P->n[0]) && std::atoi(env) != 0;
+    if (const char* env = std::getenv("ACE_FUSED"))
+        P->fused = P->zline && tplane_supported(P->n[0]) && std::atoi(env) != 0;
+    if (P->fused) P->tplane = true;  // the pipeline stores transposed planes
+    if (const char* env = std::getenv("ACE_FUSED_LAG")) P->fused_lag = std::max(1, std::atoi(env));
+    if (const char* env = std::getenv("ACE_FUSED_FLAGS")) P->fused_flags = std::atoi(env);
+    if (const char* env = std::getenv("ACE_FUSED_SLOTS")) P->fused_slots = std::max(2 * P->fused_lag + 1, std::atoi(env));
     if (P->zline) {
         const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
         std::vector<float> kern((size_t)P->N);

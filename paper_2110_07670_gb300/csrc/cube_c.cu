@@ -1,5 +1,6 @@
 // cube_c.cu -- compile-time pass kernels for the N^3 boxes N = 108, 120, 160.
 #include "pass_kernel.cuh"
+#include "pipeline.cuh"
 #include "plane.cuh"
 #include "zline.cuh"
 
@@ -16,5 +17,6 @@ template cudaError_t zline_launch<108>(const PassArgs&, int, cudaStream_t);
 template cudaError_t zline_launch<120>(const PassArgs&, int, cudaStream_t);
 template cudaError_t zline_launch<160>(const PassArgs&, int, cudaStream_t);
 template cudaError_t tplane_launch<160>(int, const PassArgs&, int, cudaStream_t);
+template cudaError_t pipeline_launch<160>(const PassArgs&, const PipeArgs&, cudaStream_t);
 
 }  // namespace ace

@@ -1,5 +1,6 @@
 // cube_dispatch.cu -- route a pass to the compile-time kernel of its N^3 box.
 #include "pass_kernel.cuh"
+#include "pipeline.cuh"
 #include "plane.cuh"
 #include "zline.cuh"
 
@@ -61,6 +62,23 @@ cudaError_t tplane_pair_launch(int n, int which, const PassArgs& a, int batch, c
         case 80: return tplane_launch<80>(which, a, batch, st);
         case 96: return tplane_launch<96>(which, a, batch, st);
         case 160: return tplane_launch<160>(which, a, batch, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+#define ACE_PIPE_DECL(N) extern template cudaError_t pipeline_launch<N>(const PassArgs&, const PipeArgs&, cudaStream_t);
+ACE_PIPE_DECL(32)
+ACE_PIPE_DECL(80)
+ACE_PIPE_DECL(96)
+ACE_PIPE_DECL(160)
+#undef ACE_PIPE_DECL
+
+cudaError_t pipeline_pair_launch(int n, const PassArgs& a, const PipeArgs& p, cudaStream_t st) {
+    switch (n) {
+        case 32: return pipeline_launch<32>(a, p, st);
+        case 80: return pipeline_launch<80>(a, p, st);
+        case 96: return pipeline_launch<96>(a, p, st);
+        case 160: return pipeline_launch<160>(a, p, st);
         default: return cudaErrorInvalidValue;
     }
 }

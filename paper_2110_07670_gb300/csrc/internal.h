@@ -111,6 +111,18 @@ cudaError_t zline_coulomb_launch(int n, const PassArgs& a, int batch, cudaStream
 // N % 16 == 0: which = 0 pair product + forward, 1 inverse + exchange accumulation
 constexpr bool tplane_supported(int n) { return n % 16 == 0; }
 cudaError_t tplane_pair_launch(int n, int which, const PassArgs& a, int batch, cudaStream_t st);
+// the three pair passes as one persistent kernel (pipeline.cuh), same boxes
+struct PipeArgs {
+    int ntrans;       // packed transforms: quads a.t0 .. a.t0 + ntrans - 1
+    int lag;          // steps between a transform's passes
+    int slots;        // spectrum ring (transforms), PassArgs::dst
+    int* done;        // [3][ntrans] finished items per pass and transform
+    int* ticket;      // next item
+    int* abort_flag;  // set by a timed-out wait
+    int discard;      // drop dead spectrum planes from L2 unwritten
+    int prefetch;     // fetch tickets two items ahead
+};
+cudaError_t pipeline_pair_launch(int n, const PassArgs& a, const PipeArgs& p, cudaStream_t st);
 
 // compile-time cube passes (cube_*.cu), single precision
 cudaError_t cube_pass_launch(int n, const PassArgs& a, const PassShape& s, int pro, int epi, int mid, int sgn,

@@ -108,21 +108,16 @@ __device__ __forceinline__ void prefetch_planes(const PassArgs& a, const Quad& q
     }
 }
 
+// Plane z of one transform (quad q): pair product, 2-D forward FFT, and the
+// plane stored transposed into spec_t (the transform's spectrum).  tw holds
+// the N twiddles in shared memory (visible to the block); the block's threads
+// all call this.
 template <int N>
-__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) pair_fwd(PassArgs a) {
+__device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q, int z, cx<float>* tile,
+                                               const cx<float>* tw, cx<float>* spec_t) {
     using G = Geo<N>;
     constexpr long long NN = (long long)N * N, N3 = NN * N;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cx<float>* tile = reinterpret_cast<cx<float>*>(smem_raw);  // (y, x) at y * P + x
-    cx<float>* tw = tile + N * G::P;
-    const int z = blockIdx.x, t = blockIdx.y;
-    const Quad q = a.quads[a.t0 + t];
     const long long plane0 = (long long)z * NN;
-    for (int j = threadIdx.x; j < N; j += G::NT) tw[j] = reinterpret_cast<const cx<float>*>(a.twx)[j];
-    if (threadIdx.x == 32 && a.lookahead > 0 && t + a.lookahead < (int)gridDim.y && (NN * 4) % 16 == 0)
-        prefetch_planes(a, a.quads[a.t0 + t + a.lookahead], plane0, (uint32_t)(NN * 4), N3, false);
-    __syncthreads();
-
     const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
     const bool active = line < N;
     const bool has2 = q.c >= 0;
@@ -179,7 +174,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) pair_fwd(PassA
     __syncwarp();
     if (active) {
         const cx<float>* row = tile + line * G::P;
-        cx<float>* out = reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride + plane0 + line;
+        cx<float>* out = spec_t + plane0 + line;
         for (int b = h; b < G::B1; b += 2) {
             cx<float> u[G::R1];
 #pragma unroll
@@ -192,36 +187,76 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) pair_fwd(PassA
 }
 
 template <int N>
-__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) inv_accum(PassArgs a) {
+__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) pair_fwd(PassArgs a) {
     using G = Geo<N>;
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2 * (G::NT / 32)];
-    cx<float>* tile = reinterpret_cast<cx<float>*>(smem_raw);
+    cx<float>* tile = reinterpret_cast<cx<float>*>(smem_raw);  // (y, x) at y * P + x
     cx<float>* tw = tile + N * G::P;
     const int z = blockIdx.x, t = blockIdx.y;
+    const Quad q = a.quads[a.t0 + t];
     const long long plane0 = (long long)z * NN;
+    for (int j = threadIdx.x; j < N; j += G::NT) tw[j] = reinterpret_cast<const cx<float>*>(a.twx)[j];
+    if (threadIdx.x == 32 && a.lookahead > 0 && t + a.lookahead < (int)gridDim.y && (NN * 4) % 16 == 0)
+        prefetch_planes(a, a.quads[a.t0 + t + a.lookahead], plane0, (uint32_t)(NN * 4), N3, false);
+    __syncthreads();
+    pair_fwd_plane<N>(a, q, z, tile, tw, reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride);
+}
+
+// Inputs of the inverse pass: thread (row y, half h) needs the transposed
+// plane's x positions of its first butterflies in its row of the tile.
+// Asynchronous 8-byte copies (the standalone kernel: all in flight at once,
+// completed by cp_async_wait_all) ...
+template <int N>
+__device__ __forceinline__ void inv_issue_copies(const cx<float>* plane_in, cx<float>* tile) {
+    using G = Geo<N>;
     const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
-    const bool active = line < N;
-    // The thread's share of the transposed spectrum plane (the inputs of its
-    // first x-line butterflies) goes to its row of the tile by 8-byte
-    // asynchronous copies, all in flight at once.
-    if (active) {
-        const cx<float>* in = reinterpret_cast<const cx<float>*>(a.src) + t * a.src_tstride + plane0 + line;
+    if (line < N) {
+        const cx<float>* in = plane_in + line;
         cx<float>* row = tile + line * G::P;
         for (int b = h; b < G::B1; b += 2)
 #pragma unroll
             for (int k = 0; k < G::R1; ++k) cp_async8(row + b * G::R1 + k, in + (long long)(b * G::R1 + k) * N);
     }
     cp_async_commit();
-    const Quad q = a.quads[a.t0 + t];
-    for (int j = threadIdx.x; j < N; j += G::NT) tw[j] = reinterpret_cast<const cx<float>*>(a.twx)[j];
-    // the accumulation reads up to four function planes and updates up to four
-    // accumulator planes at the end: start pulling them into L2 now
-    if (threadIdx.x == 32 && (NN * 4) % 16 == 0) prefetch_planes(a, q, plane0, (uint32_t)(NN * 4), N3, true);
-    cp_async_wait_all();
-    __syncthreads();
+}
 
+// ... or loads that bypass L1 (ld.global.cg), for spectra written by other
+// blocks of the same kernel.
+__device__ __forceinline__ cx<float> ld_cg2(const cx<float>* p) {
+    float2 v;
+    asm volatile("ld.global.cg.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return mk(v.x, v.y);
+}
+template <int N>
+__device__ __forceinline__ void inv_load_cg(const cx<float>* plane_in, cx<float>* tile) {
+    using G = Geo<N>;
+    const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
+    if (line < N) {
+        const cx<float>* in = plane_in + line;
+        cx<float>* row = tile + line * G::P;
+        for (int b = h; b < G::B1; b += 2) {
+            cx<float> u[G::R1];
+#pragma unroll
+            for (int k = 0; k < G::R1; ++k) u[k] = ld_cg2(in + (long long)(b * G::R1 + k) * N);
+#pragma unroll
+            for (int k = 0; k < G::R1; ++k) row[b * G::R1 + k] = u[k];
+        }
+    }
+}
+
+// Plane z of one transform (quad q), its inputs already in the tile (each
+// thread's own): 2-D inverse FFT, then W_a += v phi_b, W_b += v phi_a, ...
+// (Eq. 2) and the pair-energy partials (Eq. 4) into e_dst[2] (may be null).
+// red: 2 * NT / 32 doubles of shared memory.  Every thread of the block calls it.
+template <int N>
+__device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q, int z, cx<float>* tile,
+                                                const cx<float>* tw, double* red, double* e_dst) {
+    using G = Geo<N>;
+    constexpr long long NN = (long long)N * N, N3 = NN * N;
+    const long long plane0 = (long long)z * NN;
+    const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
+    const bool active = line < N;
     // x lines (thread owns row y): both inverse stages in shared memory
     if (active) {
         cx<float>* row = tile + line * G::P;
@@ -337,7 +372,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) inv_accum(Pass
             }
         }
     }
-    if (a.e_part != nullptr) {
+    if (e_dst != nullptr) {
         double d1 = double(e1), d2 = double(e2);
         for (int o = 16; o > 0; o >>= 1) {
             d1 += __shfl_xor_sync(0xffffffffu, d1, o);
@@ -355,11 +390,32 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) inv_accum(Pass
                 s1 += red[2 * w];
                 s2 += red[2 * w + 1];
             }
-            double* dst = a.e_part + ((long long)(a.t0 + t) * gridDim.x + z) * 2;
-            dst[0] = s1;
-            dst[1] = s2;
+            e_dst[0] = s1;
+            e_dst[1] = s2;
         }
     }
+}
+
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) inv_accum(PassArgs a) {
+    using G = Geo<N>;
+    constexpr long long NN = (long long)N * N, N3 = NN * N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[2 * (G::NT / 32)];
+    cx<float>* tile = reinterpret_cast<cx<float>*>(smem_raw);
+    cx<float>* tw = tile + N * G::P;
+    const int z = blockIdx.x, t = blockIdx.y;
+    const long long plane0 = (long long)z * NN;
+    inv_issue_copies<N>(reinterpret_cast<const cx<float>*>(a.src) + t * a.src_tstride + plane0, tile);
+    const Quad q = a.quads[a.t0 + t];
+    for (int j = threadIdx.x; j < N; j += G::NT) tw[j] = reinterpret_cast<const cx<float>*>(a.twx)[j];
+    // the accumulation reads up to four function planes and updates up to four
+    // accumulator planes at the end: start pulling them into L2 now
+    if (threadIdx.x == 32 && (NN * 4) % 16 == 0) prefetch_planes(a, q, plane0, (uint32_t)(NN * 4), N3, true);
+    cp_async_wait_all();
+    __syncthreads();
+    inv_accum_plane<N>(a, q, z, tile, tw, red,
+                       a.e_part != nullptr ? a.e_part + ((long long)(a.t0 + t) * gridDim.x + z) * 2 : nullptr);
 }
 
 template <typename K>

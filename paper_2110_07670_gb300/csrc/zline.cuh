@@ -86,6 +86,34 @@ __device__ __forceinline__ void pencil_last(const cx<float>* col, const cx<float
     }
 }
 
+// The transforms of one group of G pencils held in buf ([N][G], element
+// stride G), by one warp: forward stages, the fused middle with the Coulomb
+// factors kern_p0[z N^2 + p], the inverse stages, and the results to
+// dst_p0[z N^2 + p] (p = 0 .. G-1, in natural z order).
+template <int N, int G>
+__device__ __forceinline__ void pencils_compute(cx<float>* buf, const cx<float>* tw, const float* kern_p0,
+                                                cx<float>* dst_p0, int lane) {
+    using PL = CPlan<N>;
+    // lanes past the group's pencils (G < 16) skip every step but the syncs
+    const int pl = lane & 15, h = lane >> 4;
+    const bool on = pl < G;
+    cx<float>* col = buf + pl;
+    CLoop<0, PL::stages - 1>::run([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        if (on) pencil_stage<PL::radix(s), -1, N, PL::block_len(s), G>(col, tw, h);
+        __syncwarp();
+    });
+    if (on) pencil_middle<PL::radix(PL::stages - 1), N, G>(col, kern_p0 + pl, h);
+    __syncwarp();
+    CLoop<0, PL::stages - 2>::run([&](auto sc) {
+        constexpr int s = PL::stages - 2 - decltype(sc)::value;
+        if (on) pencil_stage<PL::radix(s), +1, N, PL::block_len(s), G>(col, tw, h);
+        __syncwarp();
+    });
+    cx<float>* out = dst_p0 + pl;
+    if (on) pencil_last<PL::radix(0), N, G>(col, tw, out, h);
+}
+
 template <int N, int G>
 __global__ void __launch_bounds__(32) zline_coulomb(PassArgs a) {
     using PL = CPlan<N>;
@@ -116,24 +144,8 @@ __global__ void __launch_bounds__(32) zline_coulomb(PassArgs a) {
         mbar_wait_bounded(&bar, 0, nullptr, 0);
         return;
     }
-    // lanes past the group's pencils (G < 16) skip every step but the syncs
-    const int pl = lane & 15, h = lane >> 4;
-    const bool on = pl < G;
-    cx<float>* col = buf + pl;
-    CLoop<0, PL::stages - 1>::run([&](auto sc) {
-        constexpr int s = decltype(sc)::value;
-        if (on) pencil_stage<PL::radix(s), -1, N, PL::block_len(s), G>(col, tw, h);
-        __syncwarp();
-    });
-    if (on) pencil_middle<PL::radix(PL::stages - 1), N, G>(col, reinterpret_cast<const float*>(a.kern) + p0 + pl, h);
-    __syncwarp();
-    CLoop<0, PL::stages - 2>::run([&](auto sc) {
-        constexpr int s = PL::stages - 2 - decltype(sc)::value;
-        if (on) pencil_stage<PL::radix(s), +1, N, PL::block_len(s), G>(col, tw, h);
-        __syncwarp();
-    });
-    cx<float>* out = reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride + p0 + pl;
-    if (on) pencil_last<PL::radix(0), N, G>(col, tw, out, h);
+    pencils_compute<N, G>(buf, tw, reinterpret_cast<const float*>(a.kern) + p0,
+                          reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride + p0, lane);
 }
 
 }  // namespace zline_detail
