@@ -286,32 +286,43 @@ def run_ours(args):
     # two streams, so the passes overlap and the unit measured is the pipeline:
     # its algorithmic bytes (counted per 32-transform launch) over its wall time.
     hbm, peak_kind = peaks()
-    pb32, nl32 = pass_bytes(n, N, batch=32)
-    pipe_bytes = sum(pb32.values())  # per build
+    kcfg = plan.config()
+    variant, streams = kcfg["pair_variant"], kcfg["pair_streams"]
+    vname = {1: "tile passes", 2: "transposed-plane passes", 3: "persistent pipeline kernel"}[variant]
+    group = 32 if (variant != 3 and streams == 2) else 64  # transforms per launch (algorithmic count)
+    pbg, _ = pass_bytes(n, N, batch=group)
+    pipe_bytes = sum(pbg.values())  # per build
     pair_wall = stats["pair_wall_ms"] / args.steps
     achieved = pipe_bytes / (pair_wall / 1e3) / 1e9 if pair_wall > 0 else 0.0
     traffic_step = sum(MEASURED_TRAFFIC_PER_LAUNCH.values()) * (stats["pair_transforms"] / args.steps) / 64
-    # each pass alone (pair_streams = 1, 64-transform launches), timed the same way
+    # each pass alone (one stream, 64-transform launches), timed the same way:
+    # the chosen variant's passes, or the tile passes when the choice is the
+    # persistent kernel (which has no separate passes)
     per_pass = None
     if world == 1:
-        ps = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, "mixed", pair_streams=1)
+        ps = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, "mixed", pair_streams=1,
+                      pair_variant=variant if variant != 3 else 1)
         xs = torch.empty_like(psi)
         _, _, st1 = timed_steps(ps, psi, tr, xs, K, 2, 1, with_timing=True)
         ps.close()
         pb64, nl64 = pass_bytes(n, N, batch=64)
         per_pass = {}
+        per_pass["variant"] = "tile passes" if variant != 2 else "transposed-plane passes"
         for k in ("pair_fwd", "pair_coulomb", "pair_inv"):
             ms = st1[k + "_ms"] / 2
             per_pass[k] = {"ms_per_build": ms, "launches_per_build": nl64,
                            "algorithmic_bytes_per_launch": pb64[k] / nl64,
                            "achieved_gbs": pb64[k] / (ms / 1e3) / 1e9 if ms > 0 else 0.0,
                            "frac": (pb64[k] / (ms / 1e3) / 1e9) / hbm if ms > 0 else 0.0,
-                           "traffic_per_launch": MEASURED_TRAFFIC_PER_LAUNCH[k]}
+                           "traffic_per_launch": MEASURED_TRAFFIC_PER_LAUNCH[k] if variant != 2 else None}
+    layout = ("one launch for all transforms" if variant == 3 else
+              "32-transform sub-batches on 2 streams" if streams == 2 else "64-transform launches on one stream")
     roofline = {"bound": "hbm",
-                "kernel": "pair pipeline: P1 + P2 + P3 in 32-transform sub-batches on 2 streams",
+                "kernel": f"pair pipeline: P1 + P2 + P3 ({vname}), {layout}",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-                "traffic": traffic_step if world == 1 else None, "traffic_unit": "bytes per build (sum of the "
-                "three passes' DRAM bytes from the ncu capture, scaled from 64-transform launches)",
+                "traffic": traffic_step if world == 1 and variant == 1 else None,
+                "traffic_unit": "bytes per build (sum of the three tile passes' DRAM bytes from the ncu "
+                "capture, scaled from 64-transform launches)",
                 "algorithmic_bytes_per_build": pipe_bytes, "pair_wall_ms_per_build": pair_wall,
                 "share_of_step": pair_wall / max(stats["total_ms"] / args.steps, 1e-9),
                 "per_pass_alone": per_pass}
@@ -379,7 +390,8 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "precision": "mixed (FP32 FFT/pairs/W, FP64 M/Cholesky/xi/E_x)",
                        "apply_trials": int(trials.shape[0]), "l2": "flushed between timed steps",
                        "parallelism": f"pair shards over {world} GPUs, W_G/E_x allreduce (NCCL)" if world > 1
-                       else "single GPU"},
+                       else "single GPU",
+                       "pair_kernels": kcfg},
             "ace_builds_per_s": builds, "E_x": E_mixed, "fp64_gpu": fp64,
             "phases_ms_per_step": {k: v / args.steps for k, v in stats.items() if k.endswith("_ms")},
             "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,

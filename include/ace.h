@@ -72,8 +72,14 @@ typedef struct {
     int pair_batch;    /* packed pair transforms per pass launch; 0 = automatic */
     int kernels;       /* 0: fastest available; 1: CUDA-core Gram products instead of
                           tcgen05 tensor cores; 2: also generic (runtime-size) FFT passes */
-    int pair_streams;  /* streams the pair sub-batches overlap on; 0 = automatic (2),
+    int pair_streams;  /* streams the pair sub-batches overlap on; 0 = automatic,
                           1 = every pass in order on the call's stream */
+    int pair_variant;  /* kernels of the pair passes (Eq. 2-4): 1 tile passes, 2 transposed-
+                          plane passes, 3 one persistent kernel for all three passes (2 and 3:
+                          single precision, n^3 boxes with n in {32, 80, 96, 160});
+                          0 = automatic: where several apply (and pair_streams is 0, both 1
+                          and 2 streams) they are timed at plan creation on the plan's own
+                          buffers and the fastest is kept (see ace_plan_config) */
 } ace_opts;
 
 /*
@@ -87,6 +93,12 @@ int ace_plan_create(ace_plan** plan, const int grid[3], const double cell[9], do
                     int precision, const ace_opts* opts);
 
 void ace_plan_destroy(ace_plan* plan);
+
+/* The plan's pair-pass kernels: pair_variant (1, 2 or 3 as in ace_opts),
+ * pair_streams, and, where plan creation timed them, tune_ms[4] = ms per
+ * timing run of {tile passes on 1 stream, on 2 streams, transposed-plane
+ * passes, persistent kernel} (0 = not timed).  Any output may be NULL. */
+int ace_plan_config(const ace_plan* plan, int* pair_variant, int* pair_streams, float* tune_ms);
 
 /* Number of half-sphere plane waves and, when miller != NULL, their Miller
  * indices [n_pw_half][3] (host memory, canonical order). */

@@ -23,7 +23,8 @@ _ERRORS = {-1: "ACE_ERR_INVALID_ARG", -2: "ACE_ERR_GRID_TOO_SMALL", -3: "ACE_ERR
            -5: "ACE_ERR_CUDA", -6: "ACE_ERR_TIMEOUT"}
 SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_apply", "hfx_apply_exact",
            "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc",
-           "ace_build_batched", "ace_save", "ace_load", "ace_build_pairs", "ace_build_finish")
+           "ace_build_batched", "ace_save", "ace_load", "ace_build_pairs", "ace_build_finish",
+           "ace_plan_config")
 
 _lib = None
 
@@ -41,7 +42,8 @@ class _System(ctypes.Structure):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("pair_batch", ctypes.c_int), ("kernels", ctypes.c_int), ("pair_streams", ctypes.c_int)]
+    _fields_ = [("pair_batch", ctypes.c_int), ("kernels", ctypes.c_int), ("pair_streams", ctypes.c_int),
+                ("pair_variant", ctypes.c_int)]
 
 
 STAT_FIELDS = ("orbitals_ms", "pair_fwd_ms", "pair_coulomb_ms", "pair_inv_ms", "w_to_g_ms", "gram_ms", "factor_ms",
@@ -78,6 +80,7 @@ def load(build_if_missing=False):
     lib.ace_apply.argtypes = [P, P, i32, P, i32, P, P]
     lib.ace_build_pairs.argtypes = [P, P, i32, f64, P, P, P, ctypes.POINTER(f64), P]
     lib.ace_build_finish.argtypes = [P, P, i32, P, P, P]
+    lib.ace_plan_config.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
     lib.ace_apply_noalloc.argtypes = [P, i32, P, i32, i32, i32, P, P]
     lib.hfx_apply_exact.argtypes = [P, P, i32, f64, P, i32, P, P]
     lib.ace_last_intermediates.argtypes = [P, P, P, P]
@@ -115,14 +118,15 @@ class Plan:
     """One system: grid, cell (rows = lattice vectors, bohr), cutoff (Ry),
     the largest occupied set, and the precision ("mixed" or "fp64")."""
 
-    def __init__(self, grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0, kernels=0, pair_streams=0):
+    def __init__(self, grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0, kernels=0, pair_streams=0,
+                 pair_variant=0):
         lib = load()
         self.precision = precision
         self.prec = ACE_MIXED if precision == "mixed" else ACE_FP64
         g = np.ascontiguousarray(np.asarray(grid, dtype=np.int32).reshape(3))
         c = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(9))
         h = ctypes.c_void_p()
-        opts = _Opts(int(pair_batch), int(kernels), int(pair_streams))
+        opts = _Opts(int(pair_batch), int(kernels), int(pair_streams), int(pair_variant))
         _check(lib.ace_plan_create(ctypes.byref(h), g.ctypes.data_as(ctypes.c_void_p),
                                    c.ctypes.data_as(ctypes.c_void_p), float(ecut), int(n_occ_max), self.prec,
                                    ctypes.byref(opts)))
@@ -149,6 +153,16 @@ class Plan:
         except Exception:
             pass
 
+    def config(self):
+        """dict(pair_variant, pair_streams, tune_ms) of the pair-pass kernels
+        (1 tile, 2 transposed planes, 3 persistent pipeline)."""
+        v, st = ctypes.c_int(0), ctypes.c_int(0)
+        tm = (ctypes.c_float * 4)()
+        _check(load().ace_plan_config(self.handle, ctypes.byref(v), ctypes.byref(st), tm))
+        return {"pair_variant": v.value, "pair_streams": st.value,
+                "tune_ms": {k: round(float(x), 3) for k, x in
+                            zip(("tile_1_stream", "tile_2_streams", "planes", "pipeline"), tm) if x > 0}}
+
     def _vec(self, t, name):
         if t.dtype != self.cdtype or not t.is_cuda or not t.is_contiguous() or t.dim() != 2 \
                 or t.shape[1] != self.n_pw_half:
@@ -156,10 +170,13 @@ class Plan:
         return t
 
 
-def ace_plan_create(grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0, kernels=0, pair_streams=0):
+def ace_plan_create(grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0, kernels=0, pair_streams=0,
+                    pair_variant=0):
     """kernels: 0 fastest available, 1 CUDA-core Gram products, 2 also generic FFT passes;
-    pair_streams: 0 automatic (2), 1 every pair pass in order on the call's stream."""
-    return Plan(grid, cell, ecut, n_occ_max, precision, pair_batch, kernels, pair_streams)
+    pair_streams: 0 automatic, 1 every pair pass in order on the call's stream;
+    pair_variant: 0 automatic (timed at creation), 1 tile passes, 2 transposed planes,
+    3 persistent pipeline."""
+    return Plan(grid, cell, ecut, n_occ_max, precision, pair_batch, kernels, pair_streams, pair_variant)
 
 
 def ace_plan_destroy(plan):

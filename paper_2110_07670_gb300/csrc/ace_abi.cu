@@ -92,15 +92,18 @@ struct ace_plan {
     bool tensor_gram = false;  // Gram products on tcgen05 tensor cores (single precision)
     int lookahead = 1;         // L2 look-ahead of the pair passes, in transforms (env ACE_LOOKAHEAD)
     bool zline = false;        // per-pencil Coulomb pass (zline.cuh) with the kernel table d_kern
-    float* d_kern = nullptr;   // 4 pi / |G|^2 / N in spectrum layout (zline only)
-    bool tplane = false;       // pair passes with transposed spectrum planes (plane.cuh; needs zline; opt-in)
+    float* d_kern = nullptr;   // 4 pi / |G|^2 / N in the tile passes' spectrum layout (zline only)
+    float* d_kern_t = nullptr; // the same for transposed planes (n % 16 == 0 cubes)
+    int variant = 1;           // pair passes: 1 tile, 2 transposed planes, 3 persistent pipeline
+    float tune_ms[4] = {0, 0, 0, 0};  // autotune timings: tile x1 stream, tile x2, planes x2, pipeline
+    bool tplane = false;       // pair passes with transposed spectrum planes (plane.cuh; needs zline)
     int pair_tile = 0;         // pairs ordered in pair_tile x pair_tile orbital blocks (0: row by row; env ACE_PAIR_TILE)
-    int pair_streams = 2;      // concurrent streams of pair sub-batches (env ACE_PAIR_STREAMS)
+    int pair_streams = 2;      // concurrent streams of pair sub-batches
     int pair_sub = 0;          // transforms per sub-batch (0: batch / pair_streams; env ACE_PAIR_SUB)
-    bool fused = false;        // the pair passes as one persistent kernel (pipeline.cuh; env ACE_FUSED)
-    int fused_lag = 2;         // its steps between a transform's passes (env ACE_FUSED_LAG)
-    int fused_slots = 8;       // its spectrum ring, transforms (env ACE_FUSED_SLOTS)
-    int fused_flags = 1;       // bit 0: L2 discard of dead planes, bit 1: ticket prefetch (env ACE_FUSED_FLAGS)
+    bool fused = false;        // the pair passes as one persistent kernel (pipeline.cuh)
+    int fused_lag = 2;         // its steps between a transform's passes
+    int fused_slots = 8;       // its spectrum ring, transforms
+    int fused_flags = 1;       // bit 0: L2 discard of dead planes, bit 1: ticket prefetch (measured slower)
     int* d_pipe = nullptr;     // its counters: [3][ntrans] done, ticket, abort
     size_t pipe_cap = 0;
     std::vector<cudaStream_t> aux;
@@ -298,7 +301,7 @@ PassArgs base_args(const ace_plan* P) {
     a.kscale = 1.0 / (double)P->N;
     a.err = P->d_err;
     a.lookahead = P->lookahead;
-    a.kern = P->d_kern;
+    a.kern = P->tplane ? P->d_kern_t : P->d_kern;
     for (int d = 0; d < 3; ++d) a.freq[d] = P->d_freq[d];
     return a;
 }
@@ -728,10 +731,115 @@ void free_plan(ace_plan* P) {
     if (P->fork_ev) cudaEventDestroy(P->fork_ev);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
                     P->d_WG, P->d_M, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
-                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_pipe};
+                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_kern_t, P->d_pipe};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete P;
+}
+
+void set_variant(ace_plan* P, int v, int streams) {
+    P->variant = v;
+    P->tplane = v == 2 || v == 3;
+    P->fused = v == 3;
+    P->pair_streams = streams;
+}
+
+// The pair-pass variant (ace_opts.pair_variant): forced, or, when 0 and more
+// than one applies, timed on this plan's own buffers (zeroed functions, the
+// first transforms of the full pair list of n_occ_max orbitals, one warm-up
+// and two timed runs each) and the fastest kept.
+template <typename R>
+int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
+    const int req = opts ? opts->pair_variant : 0;
+    const int fixed_streams = opts && opts->pair_streams > 0 ? opts->pair_streams : 0;
+    const bool t_ok = sizeof(R) == 4 && P->zline && P->d_kern_t != nullptr;
+    if (req < 0 || req > 3) return fail(ACE_ERR_INVALID_ARG, "pair_variant must be 0 (automatic), 1, 2 or 3");
+    if ((req == 2 || req == 3) && !t_ok)
+        return fail(ACE_ERR_INVALID_ARG,
+                    "pair_variant 2 and 3 need a single-precision n^3 plan with n in {32, 80, 96, 160}");
+    if (req > 0) {
+        set_variant(P, req, fixed_streams ? fixed_streams : 2);
+        return ACE_OK;
+    }
+    struct Cand {
+        int v, streams, slot;
+    };
+    std::vector<Cand> cand;
+    if (!fixed_streams || fixed_streams == 1) cand.push_back({1, 1, 0});
+    if (!fixed_streams || fixed_streams >= 2) cand.push_back({1, fixed_streams ? fixed_streams : 2, 1});
+    if (t_ok) {
+        cand.push_back({2, fixed_streams ? fixed_streams : 2, 2});
+        cand.push_back({3, 1, 3});
+    }
+    if (sizeof(R) != 4 || cand.size() == 1) {  // double plans: no timing, the two-stream tile passes
+        set_variant(P, 1, fixed_streams ? fixed_streams : 2);
+        return ACE_OK;
+    }
+    // timing pairs: the first transforms of every pair i <= j of n_occ_max rows
+    const int n = P->n_occ_max;
+    std::vector<int> pa, pb;
+    const int want = 2 * std::min(4 * P->batch, std::max(1, n * (n + 1) / 4));
+    for (int i = 0; i < n && (int)pa.size() < want; ++i)
+        for (int j = i; j < n && (int)pa.size() < want; ++j) {
+            pa.push_back(i);
+            pb.push_back(j);
+        }
+    std::vector<Quad> q;
+    pack_pairs(pa, pb, q);
+    const int K = (int)q.size();
+    cudaStream_t ts = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&] {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (ts) cudaStreamDestroy(ts);
+    };
+    if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return fail(ACE_ERR_CUDA, "autotune: stream or event creation failed");
+    }
+    int rc = ACE_OK;
+    float best = 1e30f;
+    int best_v = 1, best_s = 2;
+    do {
+        if ((rc = upload_quads(P, q, ts)) != ACE_OK) break;
+        if ((rc = grow(&P->d_epart, &P->epart_cap, (size_t)K * P->ntiles_last * 2)) != ACE_OK) break;
+        if (cudaMemsetAsync(P->d_phi, 0, (size_t)n * P->N * sizeof(R), ts) != cudaSuccess ||
+            cudaMemsetAsync(P->d_acc, 0, (size_t)n * P->N * sizeof(R), ts) != cudaSuccess) {
+            rc = fail(ACE_ERR_CUDA, "autotune: memset failed");
+            break;
+        }
+        R* phi = (R*)P->d_phi;
+        R* acc = (R*)P->d_acc;
+        for (const Cand& c : cand) {
+            set_variant(P, c.v, c.streams);
+            for (int rep = 0; rep < 3 && rc == ACE_OK; ++rep) {
+                if (rep == 1 && cudaEventRecord(e0, ts) != cudaSuccess) rc = fail(ACE_ERR_CUDA, "autotune: event");
+                if (rc == ACE_OK) rc = run_pairs<R>(P, phi, phi, acc, acc, 1, P->d_quads, K, P->d_epart, ts);
+            }
+            if (rc != ACE_OK) break;
+            float ms = 0;
+            if (cudaEventRecord(e1, ts) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = fail(ACE_ERR_CUDA, "autotune: timing failed");
+                break;
+            }
+            P->tune_ms[c.slot] = ms / 2;
+            if (ms < best) {
+                best = ms;
+                best_v = c.v;
+                best_s = c.streams;
+            }
+        }
+        if (rc == ACE_OK) rc = check_device_error(P, ts);
+    } while (false);
+    cleanup();
+    set_variant(P, best_v, best_s);
+    P->pair_transforms = 0;
+    P->launches = 0;
+    return rc;
 }
 
 template <typename R>
@@ -766,7 +874,6 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     if (const char* env = std::getenv("ACE_LOOKAHEAD")) P->lookahead = std::max(0, std::atoi(env));
     if (const char* env = std::getenv("ACE_PAIR_TILE")) P->pair_tile = std::max(0, std::atoi(env));
     if (opts && opts->pair_streams > 0) P->pair_streams = opts->pair_streams;
-    if (const char* env = std::getenv("ACE_PAIR_STREAMS")) P->pair_streams = std::max(1, std::atoi(env));
     if (const char* env = std::getenv("ACE_PAIR_SUB")) P->pair_sub = std::max(0, std::atoi(env));
     ACE_TRY(setup_shapes<R>(P));
     // the compile-time plane kernels of N % 16 == 0 boxes keep x swizzled per row
@@ -775,35 +882,32 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     // dropped) at every stored position of the spectrum, computed in double
     P->zline = P->s_xy.cube && P->s_z.cube && zline_group(P->n[0]) > 0;
     if (const char* env = std::getenv("ACE_ZLINE")) P->zline = P->zline && std::atoi(env) != 0;
-    // transposed-plane pair passes: opt-in (ACE_TPLANE=1); at 96^3 their
-    // forward pass is faster and their inverse pass slower than the tile passes
-    P->tplane = false;
-    if (const char* env = std::getenv("ACE_TPLANE"))
-        P->tplane = P->zline && tplane_supported(P->n[0]) && std::atoi(env) != 0;
-    if (const char* env = std::getenv("ACE_FUSED"))
-        P->fused = P->zline && tplane_supported(P->n[0]) && std::atoi(env) != 0;
-    if (P->fused) P->tplane = true;  // the pipeline stores transposed planes
-    if (const char* env = std::getenv("ACE_FUSED_LAG")) P->fused_lag = std::max(1, std::atoi(env));
-    if (const char* env = std::getenv("ACE_FUSED_FLAGS")) P->fused_flags = std::atoi(env);
-    if (const char* env = std::getenv("ACE_FUSED_SLOTS")) P->fused_slots = std::max(2 * P->fused_lag + 1, std::atoi(env));
     if (P->zline) {
         const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
-        std::vector<float> kern((size_t)P->N);
+        const bool with_t = tplane_supported(n0);
+        std::vector<float> kern((size_t)P->N), kern_t(with_t ? (size_t)P->N : 0);
         auto fold = [](int k, int n) { return k < n - n / 2 ? k : k - n; };
         for (int z = 0; z < n0; ++z)
             for (int y = 0; y < n1; ++y)
                 for (int xs = 0; xs < n2; ++xs) {
-                    const int xp = swz && !P->tplane ? plane_swizzle(xs, y) : xs;
-                    const int m[3] = {fold(frq[0][z], n0), fold(frq[1][y], n1), fold(frq[2][xp], n2)};
-                    double g2 = 0;
-                    for (int c = 0; c < 3; ++c) {
-                        const double g = m[0] * P->b[c] + m[1] * P->b[3 + c] + m[2] * P->b[6 + c];
-                        g2 += g * g;
+                    double g2[2];
+                    for (int v = 0; v < 2; ++v) {  // v = 0: swizzled slot xs of row y; 1: plain position xs
+                        const int xp = (v == 0 && swz) ? plane_swizzle(xs, y) : xs;
+                        const int m[3] = {fold(frq[0][z], n0), fold(frq[1][y], n1), fold(frq[2][xp], n2)};
+                        g2[v] = 0;
+                        for (int c = 0; c < 3; ++c) {
+                            const double g = m[0] * P->b[c] + m[1] * P->b[3 + c] + m[2] * P->b[6 + c];
+                            g2[v] += g * g;
+                        }
                     }
-                    // stored (y, x) slot, or (x, y) for transposed planes
-                    const size_t at = P->tplane ? ((size_t)z * n2 + xs) * n1 + y : ((size_t)z * n1 + y) * n2 + xs;
-                    kern[at] = g2 > 0 ? (float)(4 * M_PI / (g2 * (double)P->N)) : 0.0f;
+                    auto k = [&](double q2) { return q2 > 0 ? (float)(4 * M_PI / (q2 * (double)P->N)) : 0.0f; };
+                    kern[((size_t)z * n1 + y) * n2 + xs] = k(g2[0]);
+                    if (with_t) kern_t[((size_t)z * n2 + xs) * n1 + y] = k(g2[1]);  // plane stored [x][y]
                 }
+        if (with_t) {
+            ACE_TRY(dalloc((void**)&P->d_kern_t, kern_t.size() * sizeof(float)));
+            ACE_CK(cudaMemcpy(P->d_kern_t, kern_t.data(), kern_t.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
         ACE_TRY(dalloc((void**)&P->d_kern, kern.size() * sizeof(float)));
         ACE_CK(cudaMemcpy(P->d_kern, kern.data(), kern.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
@@ -850,7 +954,7 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
         return fail(ACE_ERR_OOM, "pinned host allocation failed");
     }
     ACE_CK(cudaMemset(P->d_err, 0, sizeof(int)));
-    return ACE_OK;
+    return choose_pair_variant<R>(P, opts);
 }
 
 }  // namespace
@@ -1105,6 +1209,15 @@ int ace_last_intermediates(ace_plan* plan, void* W_G, double* M, void* stream) {
         ACE_CK(cudaMemcpyAsync(W_G, plan->d_WG, (size_t)n * plan->npw * 2 * plan->esz, cudaMemcpyDeviceToDevice, st));
     if (M) ACE_CK(cudaMemcpyAsync(M, plan->d_M, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToHost, st));
     ACE_CK(cudaStreamSynchronize(st));
+    return ACE_OK;
+}
+
+int ace_plan_config(const ace_plan* plan, int* pair_variant, int* pair_streams, float* tune_ms) {
+    if (!plan) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (pair_variant) *pair_variant = plan->variant;
+    if (pair_streams) *pair_streams = plan->variant == 3 ? 1 : plan->pair_streams;
+    if (tune_ms)
+        for (int i = 0; i < 4; ++i) tune_ms[i] = plan->tune_ms[i];
     return ACE_OK;
 }
 

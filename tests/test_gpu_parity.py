@@ -221,3 +221,51 @@ def test_split_build_over_shards_matches_oracle(prec, world):
         K_ref = oracle.ace_apply(ref["xi"], tr, ref["miller"])
         assert rel(K, K_ref) <= tol["K"]
         plan.close()
+
+
+@pytest.mark.parametrize("variant,streams", [(1, 1), (1, 2), (2, 1), (2, 2), (3, 0)])
+def test_pair_variants_match_oracle(variant, streams):
+    """Every pair-pass variant (tile passes, transposed-plane passes, the
+    persistent pipeline), on one and two streams, all pairs and a screened
+    list, on the 32^3 cube: E_x, W_G and K psi against the oracle."""
+    tol = TOL["mixed"]
+    s = gen.config_small()
+    n = len(s["psi"])
+    keep = [(i, j) for i in range(n) for j in range(i, n) if i == j or (3 * i + j) % 4 != 1]
+    rp = np.zeros(n + 1, dtype=np.int32)
+    for i, _ in keep:
+        rp[i + 1] += 1
+    screened = (np.cumsum(rp).astype(np.int32), np.array([j for _, j in keep], dtype=np.int32))
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "mixed", pair_streams=streams, pair_variant=variant)
+    cfg = plan.config()
+    assert cfg["pair_variant"] == variant
+    psi = dev(s["psi"], plan)
+    tr = gen.random_trials(s["cell"], s["ecut"], 6, seed=7)
+    for pairs in (None, screened):
+        ref = oracle.ace_build(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"], pairs=pairs)
+        xi, E = ace.ace_build(plan, psi, s["alpha"], pairs=pairs)
+        W, _ = ace.ace_last_intermediates(plan, n)
+        assert abs(E - ref["E_x"]) / s["n_atom"] <= tol["E"]
+        assert rel(host(W), ref["W_G"]) <= tol["W"]
+        K = host(ace.ace_apply(plan, xi, dev(tr, plan)))
+        assert rel(K, oracle.ace_apply(ref["xi"], tr, ref["miller"])) <= tol["K"]
+    plan.close()
+
+
+def test_automatic_variant_choice_and_rejections():
+    s = gen.config_small()
+    n = len(s["psi"])
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "mixed")  # 32^3: all variants apply, timed
+    cfg = plan.config()
+    assert cfg["pair_variant"] in (1, 2, 3) and cfg["pair_streams"] in (1, 2)
+    assert set(cfg["tune_ms"]) == {"tile_1_stream", "tile_2_streams", "planes", "pipeline"}
+    plan.close()
+    p64 = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "fp64")
+    assert p64.config()["pair_variant"] == 1 and p64.config()["tune_ms"] == {}
+    p64.close()
+    small = small_system()
+    for v in (2, 3):  # 16^3 has no compile-time kernels, double has none either
+        with pytest.raises(ace.AceError):
+            ace.Plan(small["grid"], small["cell"], small["ecut"], 5, "mixed", pair_variant=v)
+        with pytest.raises(ace.AceError):
+            ace.Plan(s["grid"], s["cell"], s["ecut"], n, "fp64", pair_variant=v)
