@@ -49,6 +49,7 @@ def _load():
             "orc_exchange_rows": [P, i32, i32, P, P, P, f64, P, P, i32, P, i32, P],
             "orc_pair_energy": [P, P, i32, P, P, P, P],
             "orc_to_real": [P, i32, i32, P, P, P, P],
+            "orc_overlap": [P, i32, i32, P, P, P, P],
             "orc_gamma_gram": [P, i32, P, i32, i32, P, P],
             "orc_cholesky": [P, i32, P],
             "orc_ace_build": [P, i32, i32, P, P, P, f64, P, P, i32, P, P, P, P],
@@ -162,6 +163,30 @@ def to_real(psi, cell, grid, ecut):
     out = np.zeros((psi.shape[0],) + tuple(int(g) for g in grid))
     _check(_load().orc_to_real(_p(psi), psi.shape[0], len(m), _p(m), _p(_grid(grid)), _p(_cell(cell)), _p(out)))
     return out
+
+
+def overlap(psi, cell, grid, ecut):
+    """S_ij = integral |phi_i phi_j| dr (the s-MTACE screening overlap, Section 2.4), FP64."""
+    psi = _c128(np.atleast_2d(psi))
+    m = half_sphere(cell, ecut)
+    n = psi.shape[0]
+    S = np.zeros((n, n))
+    _check(_load().orc_overlap(_p(psi), n, len(m), _p(m), _p(_grid(grid)), _p(_cell(cell)), _p(S)))
+    return S
+
+
+def screened_pairs(S, rho_cut):
+    """CSR (row_ptr, col) of the pairs i <= j kept by the s-MTACE criterion
+    S_ij >= rho_cut, with the diagonal always kept."""
+    n = S.shape[0]
+    rp = np.zeros(n + 1, dtype=np.int32)
+    cols = []
+    for i in range(n):
+        for j in range(i, n):
+            if i == j or S[i, j] >= rho_cut:
+                cols.append(j)
+        rp[i + 1] = len(cols)
+    return rp, np.array(cols, dtype=np.int32)
 
 
 def gamma_gram(a, b, miller):

@@ -682,6 +682,37 @@ int orc_to_real(const double *psi_G, int n, int npw, const int32_t *miller, cons
     return ORC_OK;
 }
 
+/* Orbital overlap of the s-MTACE screening (Section 2.4):
+ *   S_ij = integral |phi_i(r) phi_j(r)| dr = (Omega / N) sum_r |phi_i(r)| |phi_j(r)|
+ * on the real-space grid, for every i, j (S is n x n, row-major; computed for
+ * i <= j and mirrored). */
+int orc_overlap(const double *psi_G, int n, int npw, const int32_t *miller, const int grid[3], const double cell[9],
+                double *S)
+{
+    grid_t g;
+    int st = grid_init(&g, grid, cell, npw, miller);
+    if (st) return st;
+    double *f = malloc(sizeof(double) * (size_t)n * g.N);
+    cplx *box = malloc(sizeof(cplx) * g.N);
+    if (!f || !box) {
+        free(f);
+        free(box);
+        return ORC_ERR_OOM;
+    }
+    for (int i = 0; i < n; ++i) to_real(&g, (const cplx *)psi_G + (long)i * npw, box, f + (long)i * g.N);
+    const double dv = g.omega / (double)g.N;
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) {
+            const double *a = f + (long)i * g.N, *b = f + (long)j * g.N;
+            double sum = 0.0;
+            for (long r = 0; r < g.N; ++r) sum += fabs(a[r] * b[r]);
+            S[(long)i * n + j] = S[(long)j * n + i] = sum * dv;
+        }
+    free(f);
+    free(box);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------ ACE (Section 2.2) */
 
 /* Gram matrix G_ij = <a_i|b_j> (full-sphere inner product of real functions). */

@@ -299,3 +299,81 @@ def test_exchange_rows_match_full_exchange(small):
     Ws, _ = oracle.exchange(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"], pairs=pairs)
     Wr = oracle.exchange_rows(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"], [1, 4, 2], pairs=pairs)
     assert np.abs(Wr - Ws[[1, 4, 2]]).max() < 1e-16
+
+
+# ---------------------------------------------------------------- s-MTACE overlap (Section 2.4)
+
+def test_overlap_diagonal_symmetry_and_bounds():
+    """Orthonormal orbitals: S_ii = <phi_i|phi_i> = 1 (the grid sum of phi^2 is
+    the inner product), S symmetric, 0 <= S_ij <= 1 (Cauchy-Schwarz)."""
+    cfg = gen.config_small()
+    S = oracle.overlap(cfg["psi"], cfg["cell"], cfg["grid"], cfg["ecut"])
+    assert np.allclose(np.diag(S), 1.0, atol=1e-12)
+    assert np.array_equal(S, S.T)
+    assert S.min() >= 0 and S.max() <= 1 + 1e-12
+
+
+def test_overlap_of_two_cosines_is_separable():
+    """phi_1 = sqrt(2/Omega) cos(2 pi x / L), phi_2 = sqrt(2/Omega) cos(2 pi y / L):
+    the grid integral of |phi_1 phi_2| factorises into 1-D sums,
+    S_12 = 2 A^2 with A = (1/n) sum_x |cos(2 pi x / n)|."""
+    L, ecut, n = 10.0, 5.0, 18
+    cell = gen.cubic_cell(L)
+    m = gen.half_sphere(cell, ecut)
+    psi = np.zeros((2, len(m)), dtype=np.complex128)
+    for row, target in ((0, (1, 0, 0)), (1, (0, 1, 0))):
+        k = np.where((m == target).all(1))[0][0]
+        psi[row, k] = 1 / np.sqrt(2)
+    S = oracle.overlap(psi, cell, (n, n, n), ecut)
+    A = np.abs(np.cos(2 * np.pi * np.arange(n) / n)).mean()
+    assert abs(S[0, 1] - 2 * A * A) < 1e-13
+    assert np.allclose(np.diag(S), 1.0, atol=1e-13)
+
+
+@pytest.mark.parametrize("d", [0.0, 1.0, 2.5, 4.0])
+def test_overlap_of_two_gaussians_closed_form(d):
+    """Two normalised Gaussians g_sigma at distance d (positive functions):
+    integral g_1 g_2 = exp(-d^2 / (4 sigma^2)).  The product is band-limited
+    below the grid's Nyquist frequency, so the grid sum is exact; the
+    truncation of the coefficient sphere and the periodic images are below
+    1e-12 at these sizes."""
+    L, ecut, sigma, n = 20.0, 80.0, 1.0, 64
+    cell = gen.cubic_cell(L)
+    m = gen.half_sphere(cell, ecut)
+    R1 = np.array([10.0, 10.0, 10.0])
+    R2 = R1 + np.array([d, 0.0, 0.0])
+    psi = np.stack([gen.gaussian_sum_coefficients(cell, m, [R], [sigma], [1.0]) for R in (R1, R2)])
+    S = oracle.overlap(psi, cell, (n, n, n), ecut)
+    assert abs(S[0, 1] - np.exp(-d * d / (4 * sigma * sigma))) < 1e-10
+    assert abs(S[0, 0] - 1.0) < 1e-10
+
+
+def test_overlap_brute_force_on_a_tiny_grid():
+    """phi(r) by direct summation over the plane waves (no FFT), S by direct
+    sums, against the oracle's FFT route."""
+    cell = gen.cubic_cell(6.0)
+    ecut, n = 6.0, 8
+    psi = gen.random_orbitals(cell, ecut, 3, seed=4)
+    m = gen.half_sphere(cell, ecut)
+    G = gen.gvectors(cell, m)
+    omega = abs(np.linalg.det(cell))
+    ax = np.arange(n) / n
+    X, Y, Z = np.meshgrid(ax, ax, ax, indexing="ij")
+    r = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1) @ cell  # fractional -> cartesian
+    ph = np.exp(1j * (r @ G.T))  # [N][n_pw_half]
+    f = []
+    for c in psi:
+        full = ph @ c + np.conj(ph[:, 1:]) @ np.conj(c[1:])  # c(-G) = c(G)*
+        f.append(full.real / np.sqrt(omega))
+    f = np.array(f)
+    S_ref = np.abs(f[:, None, :] * f[None, :, :]).sum(-1) * omega / n ** 3
+    S = oracle.overlap(psi, cell, (n, n, n), ecut)
+    assert np.max(np.abs(S - S_ref)) < 1e-12
+
+
+def test_screened_pairs_rule():
+    S = np.array([[1.0, 0.3, 0.01], [0.3, 1.0, 0.02], [0.01, 0.02, 1.0]])
+    rp, col = oracle.screened_pairs(S, 0.02)
+    assert rp.tolist() == [0, 2, 4, 5] and col.tolist() == [0, 1, 1, 2, 2]
+    rp, col = oracle.screened_pairs(S, 2.0)  # the diagonal is always kept
+    assert rp.tolist() == [0, 1, 2, 3] and col.tolist() == [0, 1, 2]
