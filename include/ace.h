@@ -143,6 +143,24 @@ int ace_build_pairs(ace_plan* plan, const void* psi_G, int n_occ, double alpha, 
 int ace_build_finish(ace_plan* plan, const void* psi_G, int n_occ, const void* W_G, void* xi, void* stream);
 
 /*
+ * Orbital screening of s-MTACE (Section 2.4): the overlaps
+ *   S_ij = integral |phi_i(r) phi_j(r)| dr = (Omega / N) sum_r |phi_i(r)| |phi_j(r)|
+ * of the real-space orbitals on the plan's grid, and the pairs the paper keeps,
+ * S_ij >= rho_cut (i <= j; the diagonal always), as the CSR that ace_build
+ * takes.  Single-precision plans form S on the tcgen05 tensor cores (TF32
+ * hi/lo split, FP32 slices summed in FP64), double plans on CUDA cores.
+ *   psi_G        [n_occ][n_pw_half] device, as ace_build
+ *   pair_row_ptr [n_occ + 1] host output
+ *   pair_col     host output, room for n_occ (n_occ + 1) / 2 entries
+ *   n_pairs      host output (may be NULL): kept pairs
+ *   S            [n_occ][n_occ] host output (may be NULL)
+ * Synchronises the stream.  Pairs whose S lies within rounding of rho_cut may
+ * fall either way.
+ */
+int ace_overlap_screen(ace_plan* plan, const void* psi_G, int n_occ, double rho_cut, int32_t* pair_row_ptr,
+                       int32_t* pair_col, int* n_pairs, double* S, void* stream);
+
+/*
  * Apply the compressed operator (Eq. 5, an inner MTS step):
  *   Kpsi = -xi (xi^T psi), with the Gamma-point inner product
  *   <a|b> = 2 Re sum_{half} a^* b - a(0) b(0).

@@ -24,7 +24,7 @@ _ERRORS = {-1: "ACE_ERR_INVALID_ARG", -2: "ACE_ERR_GRID_TOO_SMALL", -3: "ACE_ERR
 SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_apply", "hfx_apply_exact",
            "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc",
            "ace_build_batched", "ace_save", "ace_load", "ace_build_pairs", "ace_build_finish",
-           "ace_plan_config")
+           "ace_plan_config", "ace_overlap_screen")
 
 _lib = None
 
@@ -80,6 +80,7 @@ def load(build_if_missing=False):
     lib.ace_apply.argtypes = [P, P, i32, P, i32, P, P]
     lib.ace_build_pairs.argtypes = [P, P, i32, f64, P, P, P, ctypes.POINTER(f64), P]
     lib.ace_build_finish.argtypes = [P, P, i32, P, P, P]
+    lib.ace_overlap_screen.argtypes = [P, P, i32, f64, P, P, ctypes.POINTER(i32), P, P]
     lib.ace_plan_config.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
     lib.ace_apply_noalloc.argtypes = [P, i32, P, i32, i32, i32, P, P]
     lib.hfx_apply_exact.argtypes = [P, P, i32, f64, P, i32, P, P]
@@ -232,6 +233,22 @@ def ace_build_pairs(plan, psi_G, alpha, pairs=None, W_G=None, stream=None):
                                   col.ctypes.data_as(ctypes.c_void_p) if col is not None else None,
                                   _ptr(W_G), ctypes.byref(E), _stream(stream)))
     return W_G, E.value
+
+
+def ace_overlap_screen(plan, psi_G, rho_cut, stream=None):
+    """s-MTACE screening (Section 2.4): returns (pairs, S) with pairs = (row_ptr,
+    col) of the i <= j kept by S_ij = int |phi_i phi_j| >= rho_cut (diagonal
+    always) and S the [n_occ][n_occ] overlaps (float64 numpy)."""
+    psi_G = plan._vec(psi_G, "psi_G")
+    n = psi_G.shape[0]
+    rp = np.zeros(n + 1, dtype=np.int32)
+    col = np.zeros(max(1, n * (n + 1) // 2), dtype=np.int32)
+    S = np.zeros((n, n), dtype=np.float64)
+    npairs = ctypes.c_int(0)
+    _check(load().ace_overlap_screen(plan.handle, _ptr(psi_G), n, float(rho_cut), rp.ctypes.data_as(ctypes.c_void_p),
+                                     col.ctypes.data_as(ctypes.c_void_p), ctypes.byref(npairs),
+                                     S.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return (rp, col[:npairs.value].copy()), S
 
 
 def ace_build_finish(plan, psi_G, W_G, xi=None, stream=None):

@@ -712,6 +712,62 @@ int hfx_impl(ace_plan* P, const void* psi_occ, int n_occ, double alpha, const vo
     return ACE_OK;
 }
 
+// s-MTACE screening (Section 2.4): S_ij = integral |phi_i phi_j| dr on the
+// grid, (Omega / N) sum_r |phi_i(r)| |phi_j(r)|, a Gram product of |phi| over
+// the N grid points (tcgen05 in single precision), then the kept pairs i <= j
+// with S_ij >= rho_cut (the diagonal always) as a CSR.
+template <typename R>
+int overlap_impl(ace_plan* P, const void* psi_G, int n, double rho_cut, int32_t* rp, int32_t* col, int* n_pairs,
+                 double* S_out, cudaStream_t st) {
+    ACE_TRY(check_gamma<R>(P, psi_G, n, st));
+    std::vector<Quad> oq = orbital_quads(n);
+    ACE_TRY(upload_quads(P, oq, st));
+    R* phi = (R*)P->d_phi;
+    ACE_TRY(run_to_real<R>(P, (const cx<R>*)psi_G, P->d_quads, (int)oq.size(), phi, st));
+    const long long K = P->N;
+    const double scale = P->omega / (double)P->N;
+    mark(P, PH_GRAM, st);
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+        if (P->tensor_gram && K % 2 == 0) {
+            // K-slices of at most 16384 points (each summed in FP32 in TMEM,
+            // the slices in FP64), at least about two blocks per SM
+            const long long tiles = (long long)((n + 127) / 128) * ((n + 127) / 128);
+            long long kc = (K + std::max<long long>(1, 304 / tiles) - 1) / std::max<long long>(1, 304 / tiles);
+            kc = std::min<long long>(16384, (kc + 31) / 32 * 32);
+            const int nchunk = (int)((K + kc - 1) / kc);
+            ACE_TRY(grow(&P->d_part, &P->part_cap, ((size_t)nchunk * n * n + 1) / 2));
+            float* part = reinterpret_cast<float*>(P->d_part);
+            ACE_CKL(launch_overlap_partial_umma((const float*)phi, n, K, kc, part, P->d_err, st));
+            ACE_CKL(launch_overlap_finish<float>(part, nchunk, n, scale, P->d_M, st));
+            done = true;
+        }
+    }
+    if (!done) {
+        const long long tiles = (long long)((n + 63) / 64) * ((n + 63) / 64);
+        int nchunk = (int)std::max<long long>(1, (2 * 152 + tiles - 1) / tiles);
+        nchunk = (int)std::min<long long>(nchunk, std::max<long long>(1, K / 256));
+        ACE_TRY(grow(&P->d_part, &P->part_cap, (size_t)nchunk * n * n));
+        ACE_CKL(launch_overlap_partial<R>(phi, n, K, nchunk, P->d_part, st));
+        ACE_CKL(launch_overlap_finish<double>(P->d_part, nchunk, n, scale, P->d_M, st));
+    }
+    mark(P, PH_IDLE, st);
+    std::vector<double> S((size_t)n * n);
+    ACE_CK(cudaMemcpyAsync(S.data(), P->d_M, S.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaStreamSynchronize(st));
+    ACE_TRY(check_device_error(P, st));
+    int q = 0;
+    rp[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int j = i; j < n; ++j)
+            if (i == j || S[(size_t)i * n + j] >= rho_cut) col[q++] = j;
+        rp[i + 1] = q;
+    }
+    if (n_pairs) *n_pairs = q;
+    if (S_out) std::memcpy(S_out, S.data(), S.size() * sizeof(double));
+    return ACE_OK;
+}
+
 template <typename R>
 int apply_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, void* out, cudaStream_t st) {
     ACE_TRY(grow(&P->d_C, &P->C_cap, (size_t)T * n_occ));
@@ -1034,6 +1090,18 @@ int ace_build_pairs(ace_plan* plan, const void* psi_G, int n_occ, double alpha, 
     return plan->prec == ACE_FP64
                ? pairs_impl<double>(plan, psi_G, n_occ, alpha, pair_row_ptr, pair_col, W_G, E_part, st)
                : pairs_impl<float>(plan, psi_G, n_occ, alpha, pair_row_ptr, pair_col, W_G, E_part, st);
+}
+
+int ace_overlap_screen(ace_plan* plan, const void* psi_G, int n_occ, double rho_cut, int32_t* pair_row_ptr,
+                       int32_t* pair_col, int* n_pairs, double* S, void* stream) {
+    if (!plan || !psi_G || !pair_row_ptr || !pair_col) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (n_occ < 1 || n_occ > plan->n_occ_max) return fail(ACE_ERR_INVALID_ARG, "n_occ out of range");
+    if (!(rho_cut >= 0)) return fail(ACE_ERR_INVALID_ARG, "rho_cut must be >= 0");
+    DeviceGuard g(plan->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->prec == ACE_FP64
+               ? overlap_impl<double>(plan, psi_G, n_occ, rho_cut, pair_row_ptr, pair_col, n_pairs, S, st)
+               : overlap_impl<float>(plan, psi_G, n_occ, rho_cut, pair_row_ptr, pair_col, n_pairs, S, st);
 }
 
 int ace_build_finish(ace_plan* plan, const void* psi_G, int n_occ, const void* W_G, void* xi, void* stream) {

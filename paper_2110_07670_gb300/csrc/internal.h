@@ -156,6 +156,16 @@ cudaError_t launch_gram_partial(const R* A, const R* B, int m, int n, long long 
 int gram_umma_chunks(long long K);
 cudaError_t launch_gram_partial_umma(const float* A, const float* B, int m, int n, long long K, float* P, int* err,
                                      cudaStream_t st);
+// Overlap partials |A|^T |A| (A [m][K], K-slices of kchunk, a multiple of 32,
+// each accumulated in TMEM) on tcgen05: P [ceil(K / kchunk)][m][m] float.
+cudaError_t launch_overlap_partial_umma(const float* A, int m, long long K, long long kchunk, float* P, int* err,
+                                        cudaStream_t st);
+// The same on CUDA cores with double partials over nchunk K-slices.
+template <typename R>
+cudaError_t launch_overlap_partial(const R* A, int m, long long K, int nchunk, double* P, cudaStream_t st);
+// G [m][m] = scale * sum over the slices of the partials.
+template <typename PT>
+cudaError_t launch_overlap_finish(const PT* P, int nchunk, int m, double scale, double* G, cudaStream_t st);
 // launch_gram_finish for single-precision partials
 cudaError_t launch_gram_finish_f32(const float* P, int nchunk, const float* A, const float* B, int m, int n,
                                    long long K, double* G, int ldg, cudaStream_t st);

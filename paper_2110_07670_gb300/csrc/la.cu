@@ -51,7 +51,7 @@ constexpr int GT = 64, GK = 32;
 
 template <typename R>
 __global__ void __launch_bounds__(256) gram_partial_kernel(const R* __restrict__ A, const R* __restrict__ B, int m,
-                                                           int n, long long K, long long kchunk,
+                                                           int n, long long K, long long kchunk, int absval,
                                                            double* __restrict__ P) {
     __shared__ R As[GK][GT + 1];
     __shared__ R Bs[GK][GT + 1];
@@ -68,8 +68,14 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const R* __restrict__
         for (int e = threadIdx.x; e < GT * GK; e += 256) {
             const int r = e / GK, c = e % GK;
             const long long k = k0 + c;
-            As[c][r] = (i0 + r < m && k < kend) ? A[(long long)(i0 + r) * K + k] : R(0);
-            Bs[c][r] = (j0 + r < n && k < kend) ? B[(long long)(j0 + r) * K + k] : R(0);
+            R av = (i0 + r < m && k < kend) ? A[(long long)(i0 + r) * K + k] : R(0);
+            R bv = (j0 + r < n && k < kend) ? B[(long long)(j0 + r) * K + k] : R(0);
+            if (absval) {
+                av = av < R(0) ? -av : av;
+                bv = bv < R(0) ? -bv : bv;
+            }
+            As[c][r] = av;
+            Bs[c][r] = bv;
         }
         __syncthreads();
         R s[4][4];
@@ -116,6 +122,17 @@ __global__ void gram_finish_kernel(const PT* __restrict__ P, int nchunk, const R
     const double g0 = double(A[(long long)i * K]) * double(B[(long long)j * K]) +
                       double(A[(long long)i * K + 1]) * double(B[(long long)j * K + 1]);
     G[(long long)i * ldg + j] = 2.0 * s - g0;
+}
+
+// Overlap matrix from per-chunk partials: G[i][j] = scale sum_c P[c][i][j].
+template <typename PT>
+__global__ void overlap_finish_kernel(const PT* __restrict__ P, int nchunk, int m, double scale,
+                                      double* __restrict__ G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += double(P[(long long)c * m * m + e]);
+    G[e] = scale * s;
 }
 
 // ------------------------------------------------------------ NN product
@@ -300,7 +317,7 @@ cudaError_t launch_gram_partial(const R* A, const R* B, int m, int n, long long 
     long long kc = (K + nchunk - 1) / nchunk;
     kc = (kc + GK - 1) / GK * GK;
     dim3 grid((m + GT - 1) / GT, (n + GT - 1) / GT, nchunk);
-    gram_partial_kernel<R><<<grid, 256, 0, st>>>(A, B, m, n, K, kc, P);
+    gram_partial_kernel<R><<<grid, 256, 0, st>>>(A, B, m, n, K, kc, 0, P);
     return cudaGetLastError();
 }
 
@@ -311,6 +328,23 @@ cudaError_t launch_gram_finish(const double* P, int nchunk, const R* A, const R*
     gram_finish_kernel<R, double><<<(tot + 255) / 256, 256, 0, st>>>(P, nchunk, A, B, m, n, K, G, ldg);
     return cudaGetLastError();
 }
+
+template <typename R>
+cudaError_t launch_overlap_partial(const R* A, int m, long long K, int nchunk, double* P, cudaStream_t st) {
+    long long kc = (K + nchunk - 1) / nchunk;
+    kc = (kc + GK - 1) / GK * GK;
+    dim3 grid((m + GT - 1) / GT, (m + GT - 1) / GT, nchunk);
+    gram_partial_kernel<R><<<grid, 256, 0, st>>>(A, A, m, m, K, kc, 1, P);
+    return cudaGetLastError();
+}
+
+template <typename PT>
+cudaError_t launch_overlap_finish(const PT* P, int nchunk, int m, double scale, double* G, cudaStream_t st) {
+    overlap_finish_kernel<PT><<<(m * m + 255) / 256, 256, 0, st>>>(P, nchunk, m, scale, G);
+    return cudaGetLastError();
+}
+template cudaError_t launch_overlap_finish<float>(const float*, int, int, double, double*, cudaStream_t);
+template cudaError_t launch_overlap_finish<double>(const double*, int, int, double, double*, cudaStream_t);
 
 cudaError_t launch_gram_finish_f32(const float* P, int nchunk, const float* A, const float* B, int m, int n,
                                    long long K, double* G, int ldg, cudaStream_t st) {
@@ -352,7 +386,8 @@ cudaError_t launch_energy_reduce(const double* e_part, const Quad* quads, int nt
     template cudaError_t launch_gram_finish<R>(const double*, int, const R*, const R*, int, int, long long,     \
                                                double*, int, cudaStream_t);                                     \
     template cudaError_t launch_gemm_nn<R>(const double*, int, int, const R*, long long, double, R*, bool,      \
-                                           cudaStream_t, bool);
+                                           cudaStream_t, bool);                                                 \
+    template cudaError_t launch_overlap_partial<R>(const R*, int, long long, int, double*, cudaStream_t);
 ACE_INST(float)
 ACE_INST(double)
 #undef ACE_INST

@@ -96,12 +96,12 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
 
 __global__ void __launch_bounds__(NTHR, 2)
     gram_partial_umma(const float* __restrict__ A, const float* __restrict__ B, int m, int n, long long K,
-                      float* __restrict__ P, int* err) {
+                      long long kchunk, int absval, float* __restrict__ P, int* err) {
     extern __shared__ unsigned char smem_raw[];
     GramSmem& sm = *reinterpret_cast<GramSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TN;
-    const long long k0 = (long long)blockIdx.z * KCHUNK;
-    const int nst = (int)(((K - k0 < KCHUNK ? K - k0 : KCHUNK) + TK - 1) / TK);
+    const long long k0 = (long long)blockIdx.z * kchunk;
+    const int nst = (int)(((K - k0 < kchunk ? K - k0 : kchunk) + TK - 1) / TK);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0) {
@@ -141,6 +141,10 @@ __global__ void __launch_bounds__(NTHR, 2)
                     x[u] = __ldg(reinterpret_cast<const float2*>(src));
                 else
                     x[u].x = __ldg(src);
+                if (absval) {
+                    x[u].x = fabsf(x[u].x);
+                    x[u].y = fabsf(x[u].y);
+                }
             }
         }
     };
@@ -232,7 +236,18 @@ cudaError_t launch_gram_partial_umma(const float* A, const float* B, int m, int 
     cudaError_t e = cudaFuncSetAttribute(gram_partial_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((m + TM - 1) / TM, (n + TN - 1) / TN, gram_umma_chunks(K));
-    gram_partial_umma<<<grid, NTHR, smem, st>>>(A, B, m, n, K, P, err);
+    gram_partial_umma<<<grid, NTHR, smem, st>>>(A, B, m, n, K, (long long)KCHUNK, 0, P, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_overlap_partial_umma(const float* A, int m, long long K, long long kchunk, float* P, int* err,
+                                        cudaStream_t st) {
+    if (K % 2 != 0 || kchunk % TK != 0 || kchunk <= 0 || ((uintptr_t)A % 8)) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(GramSmem) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(gram_partial_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((m + TM - 1) / TM, (m + TM - 1) / TM, (unsigned)((K + kchunk - 1) / kchunk));
+    gram_partial_umma<<<grid, NTHR, smem, st>>>(A, A, m, m, K, kchunk, 1, P, err);
     return cudaGetLastError();
 }
 

@@ -148,3 +148,16 @@ def test_save_load_roundtrip():
         other = ace.Plan((36, 36, 36), cfg["cell"], cfg["ecut"], 8, "mixed")
         with pytest.raises(ace.AceError):
             ace.ace_load(other, path)
+
+
+def test_overlap_screen_water32_grid():
+    """The screening overlap on the 96^3 / 80 Ry water-box grid (the first 32
+    of the 128 orbitals; tcgen05 path, K = 96^3 grid points in 304 slices)
+    against the oracle, element by element."""
+    cfg = gen.config_water32()
+    psi = cfg["psi"][:32]
+    S_ref = oracle.overlap(psi, cfg["cell"], cfg["grid"], cfg["ecut"])
+    plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], 32, "mixed")
+    pairs, S = ace.ace_overlap_screen(plan, torch.from_numpy(psi.astype(np.complex64)).cuda(), 2.5e-2)
+    assert np.abs(S - S_ref).max() <= 2e-5
+    plan.close()

@@ -269,3 +269,40 @@ def test_automatic_variant_choice_and_rejections():
             ace.Plan(small["grid"], small["cell"], small["ecut"], 5, "mixed", pair_variant=v)
         with pytest.raises(ace.AceError):
             ace.Plan(s["grid"], s["cell"], s["ecut"], n, "fp64", pair_variant=v)
+
+
+def _csr_set(pairs):
+    rp, col = pairs
+    return {(i, int(j)) for i in range(len(rp) - 1) for j in col[rp[i]:rp[i + 1]]}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_overlap_screen_matches_oracle(prec):
+    """s-MTACE screening (Section 2.4) on localised orbitals (32^3 cube): S
+    element by element, the kept pairs at the paper's three rho_cut values
+    (identical except pairs within the S tolerance of rho_cut, which may fall
+    either way), and the screened build against the oracle's on the same list."""
+    tol_S = 1e-12 if prec == "fp64" else 2e-5
+    cell = gen.cubic_cell(14.0)
+    ecut, grid, n = 30.0, (32, 32, 32), 16
+    psi, _ = gen.localized_orbitals(14.0, ecut, n, seed=21)
+    S_ref = oracle.overlap(psi, cell, grid, ecut)
+    plan = ace.Plan(grid, cell, ecut, n, prec)
+    d = dev(psi, plan)
+    for rho_cut in (2.5e-2, 1.0e-2, 2.0e-3):
+        pairs, S = ace.ace_overlap_screen(plan, d, rho_cut)
+        assert np.abs(S - S_ref).max() <= tol_S
+        got, ref = _csr_set(pairs), _csr_set(oracle.screened_pairs(S_ref, rho_cut))
+        for i, j in got ^ ref:
+            assert abs(S_ref[i, j] - rho_cut) <= tol_S
+        assert all((i, i) in got for i in range(n))
+    # the screened build on the GPU's list (rho_cut 1e-2) against the oracle's build on it
+    pairs, _ = ace.ace_overlap_screen(plan, d, 1.0e-2)
+    ref = oracle.ace_build(psi, cell, grid, ecut, 0.25, pairs=pairs)
+    xi, E = ace.ace_build(plan, d, 0.25, pairs=pairs)
+    tol = TOL[prec]
+    assert abs(E - ref["E_x"]) / (3 * n / 4) <= tol["E"] * (1 if prec == "mixed" else abs(ref["E_x"]))
+    tr = gen.random_trials(cell, ecut, 4, seed=3)
+    K = host(ace.ace_apply(plan, xi, dev(tr, plan)))
+    assert rel(K, oracle.ace_apply(ref["xi"], tr, ref["miller"])) <= tol["K"]
+    plan.close()
