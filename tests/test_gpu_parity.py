@@ -306,3 +306,32 @@ def test_overlap_screen_matches_oracle(prec):
     K = host(ace.ace_apply(plan, xi, dev(tr, plan)))
     assert rel(K, oracle.ace_apply(ref["xi"], tr, ref["miller"])) <= tol["K"]
     plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_mts_harness_matches_oracle(prec):
+    """The MTS loop (Section 2.3): ACE built once on Phi_0, inner steps on
+    drifting orbitals; the fast energy sum <phi_k|K_0 phi_k>, the exact E_x on
+    Phi_k and their difference against the oracle, and dE(0) = 0."""
+    from paper_2110_07670_gb300 import mts
+    s = gen.config_small()
+    n = len(s["psi"])
+    D = gen.random_orbitals(s["cell"], s["ecut"], n, seed=33)
+    at = lambda k: mts.drifted_orbitals(s["psi"], D, 0.02, k)
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, prec)
+    rec = mts.run(plan, s["psi"], s["alpha"], at, n_inner=3, every=1)
+    plan.close()
+    ref0 = oracle.ace_build(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    tol = 1e-10 if prec == "fp64" else 1e-6
+    assert abs(rec[0]["dE"]) == 0.0
+    for r in rec[1:]:
+        phik = at(r["k"])
+        E_ace = mts.gamma_energy(phik, oracle.ace_apply(ref0["xi"], phik, ref0["miller"]))
+        E_ex = oracle.exchange(phik, s["cell"], s["grid"], s["ecut"], s["alpha"])[1]
+        scale = 1.0 if prec == "mixed" else abs(E_ex)
+        assert abs(r["E_ACE"] - E_ace) / s["n_atom"] <= tol * scale
+        assert abs(r["E_exact"] - E_ex) / s["n_atom"] <= tol * scale
+        assert abs(r["dE"] - (E_ex - E_ace)) / s["n_atom"] <= 2 * tol * scale
+    # the ACE energy of Phi_0 itself is the exact one (exactness on span(Phi_0))
+    assert abs(mts.gamma_energy(s["psi"], oracle.ace_apply(ref0["xi"], s["psi"], ref0["miller"])) - ref0["E_x"]) \
+        <= 1e-10 * abs(ref0["E_x"])

@@ -377,3 +377,15 @@ def test_screened_pairs_rule():
     assert rp.tolist() == [0, 2, 4, 5] and col.tolist() == [0, 1, 1, 2, 2]
     rp, col = oracle.screened_pairs(S, 2.0)  # the diagonal is always kept
     assert rp.tolist() == [0, 1, 2, 3] and col.tolist() == [0, 1, 2]
+
+
+def test_mts_drift_keeps_orthonormal_gamma_orbitals():
+    """The harness's drifted orbitals stay Gamma-symmetric and orthonormal."""
+    from paper_2110_07670_gb300 import mts
+    cfg = gen.config_small()
+    D = gen.random_orbitals(cfg["cell"], cfg["ecut"], 8, seed=33)
+    for k in (0, 1, 5):
+        c = mts.drifted_orbitals(cfg["psi"], D, 0.02, k)
+        assert np.all(c[:, 0].imag == 0)
+        assert np.allclose(gen.gamma_overlap(c, c), np.eye(8), atol=1e-12)
+    assert np.allclose(mts.drifted_orbitals(cfg["psi"], D, 0.02, 0), cfg["psi"], atol=1e-12)
