@@ -120,6 +120,25 @@ int ace_build(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const 
               const int32_t* pair_col, void* xi, double* E_x, void* stream);
 
 /*
+ * ace_build without host synchronisation, for CUDA-graph capture and
+ * overlapped work: the same work enqueued on `stream` (no Gamma-point check of
+ * psi_G: ace_build does it), the status and E_x left in the plan's pinned
+ * result slots, read by ace_build_result once the stream (or the graph launch)
+ * has completed.
+ * Capture: enqueued while `stream` is capturing, the call records its copies
+ * and kernels into the graph and allocates nothing; run the same call (same
+ * n_occ, same pair list length) once outside capture first, or it fails with
+ * ACE_ERR_INVALID_ARG.  A replay reads psi_G, writes xi and uploads the pair
+ * list last enqueued on the plan.  ace_apply may be captured the same way.
+ * One build per plan at a time: ace_build_result before the next enqueue.
+ */
+int ace_build_async(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const int32_t* pair_row_ptr,
+                    const int32_t* pair_col, void* xi, void* stream);
+/* Wait for `stream`, then E_x (may be NULL) of the last enqueued build;
+ * ACE_ERR_NOT_POSDEF or ACE_ERR_TIMEOUT as ace_build. */
+int ace_build_result(ace_plan* plan, double* E_x, void* stream);
+
+/*
  * The two halves of ace_build, for a build whose pairs are split over several
  * GPUs (the pair terms of Eq. 2-4 are independent; W and E_x are sums over
  * pairs, so the only exchange is one sum over the shards):

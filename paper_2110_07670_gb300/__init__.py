@@ -24,7 +24,7 @@ _ERRORS = {-1: "ACE_ERR_INVALID_ARG", -2: "ACE_ERR_GRID_TOO_SMALL", -3: "ACE_ERR
 SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_apply", "hfx_apply_exact",
            "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc",
            "ace_build_batched", "ace_save", "ace_load", "ace_build_pairs", "ace_build_finish",
-           "ace_plan_config", "ace_overlap_screen")
+           "ace_plan_config", "ace_overlap_screen", "ace_build_async", "ace_build_result")
 
 _lib = None
 
@@ -80,6 +80,8 @@ def load(build_if_missing=False):
     lib.ace_apply.argtypes = [P, P, i32, P, i32, P, P]
     lib.ace_build_pairs.argtypes = [P, P, i32, f64, P, P, P, ctypes.POINTER(f64), P]
     lib.ace_build_finish.argtypes = [P, P, i32, P, P, P]
+    lib.ace_build_async.argtypes = [P, P, i32, f64, P, P, P, P]
+    lib.ace_build_result.argtypes = [P, ctypes.POINTER(f64), P]
     lib.ace_overlap_screen.argtypes = [P, P, i32, f64, P, P, ctypes.POINTER(i32), P, P]
     lib.ace_plan_config.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
     lib.ace_apply_noalloc.argtypes = [P, i32, P, i32, i32, i32, P, P]
@@ -233,6 +235,36 @@ def ace_build_pairs(plan, psi_G, alpha, pairs=None, W_G=None, stream=None):
                                   col.ctypes.data_as(ctypes.c_void_p) if col is not None else None,
                                   _ptr(W_G), ctypes.byref(E), _stream(stream)))
     return W_G, E.value
+
+
+def ace_build_async(plan, psi_G, alpha, pairs=None, xi=None, stream=None):
+    """Enqueue a build without host synchronisation (CUDA-graph capturable once
+    the same call has run outside capture); returns xi.  Read E_x with
+    ace_build_result after the stream completes.  The pair arrays are kept
+    on the plan object until the next enqueue."""
+    import torch
+    psi_G = plan._vec(psi_G, "psi_G")
+    n_occ = psi_G.shape[0]
+    if xi is None:
+        xi = torch.empty_like(psi_G)
+    plan._vec(xi, "xi")
+    rp = col = None
+    if pairs is not None:
+        rp = np.ascontiguousarray(pairs[0], dtype=np.int32)
+        col = np.ascontiguousarray(pairs[1], dtype=np.int32)
+    plan._async_pairs = (rp, col)
+    _check(load().ace_build_async(plan.handle, _ptr(psi_G), n_occ, float(alpha),
+                                  rp.ctypes.data_as(ctypes.c_void_p) if rp is not None else None,
+                                  col.ctypes.data_as(ctypes.c_void_p) if col is not None else None,
+                                  _ptr(xi), _stream(stream)))
+    return xi
+
+
+def ace_build_result(plan, stream=None):
+    """E_x of the last ace_build_async (waits for the stream)."""
+    E = ctypes.c_double(0.0)
+    _check(load().ace_build_result(plan.handle, ctypes.byref(E), _stream(stream)))
+    return E.value
 
 
 def ace_overlap_screen(plan, psi_G, rho_cut, stream=None):

@@ -17,6 +17,18 @@ using namespace ace;
 namespace {
 
 thread_local std::string g_err;
+// set while a call enqueues onto a capturing stream: no allocation, no timing
+// events, no host synchronisation may happen then
+thread_local bool g_capture = false;
+
+bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
 
 int fail(int code, const std::string& msg) {
     g_err = msg;
@@ -141,6 +153,9 @@ struct ace_plan {
         double E;
     };
     Result* h_res = nullptr;  // pinned host slots for the asynchronous build result
+    Quad* h_quads = nullptr;  // pinned staging of the quads
+    size_t hq_cap = 0;
+    cudaEvent_t quads_ev = nullptr;
     // timing: events recorded at phase boundaries; each interval belongs to the
     // phase of the event that opens it (PH_IDLE closes a call)
     bool timing = false;
@@ -163,7 +178,7 @@ enum Phase { PH_IDLE = -1, PH_ORB = 0, PH_PFWD, PH_PCOUL, PH_PINV, PH_W2G, PH_GR
              PH_PAIRWALL, PH_N };
 
 void mark(ace_plan* P, int phase, cudaStream_t st, int lane = 0) {
-    if (!P->timing) return;
+    if (!P->timing || g_capture) return;
     cudaEvent_t e;
     if (!P->ev_pool.empty()) {
         e = P->ev_pool.back();
@@ -179,6 +194,9 @@ void mark(ace_plan* P, int phase, cudaStream_t st, int lane = 0) {
 template <typename T>
 int grow(T** p, size_t* cap, size_t need) {
     if (need <= *cap) return ACE_OK;
+    if (g_capture)
+        return fail(ACE_ERR_INVALID_ARG,
+                    "the call needs device memory the plan has not allocated yet; run it once outside stream capture");
     if (*p) cudaFree(*p);
     *p = nullptr;
     *cap = 0;
@@ -553,9 +571,28 @@ int check_gamma(ace_plan* P, const void* psi, int n, cudaStream_t st) {
     return ACE_OK;
 }
 
+// The quads go through the plan's pinned staging buffer (a captured copy
+// reads it when the graph runs).  Outside capture, the previous upload from it
+// is waited for before it is rewritten.
 int upload_quads(ace_plan* P, const std::vector<Quad>& q, cudaStream_t st) {
     ACE_TRY(grow(&P->d_quads, &P->quads_cap, q.size()));
-    ACE_CK(cudaMemcpyAsync(P->d_quads, q.data(), q.size() * sizeof(Quad), cudaMemcpyHostToDevice, st));
+    if (!P->quads_ev) ACE_CK(cudaEventCreateWithFlags(&P->quads_ev, cudaEventDisableTiming));
+    if (!g_capture) ACE_CK(cudaEventSynchronize(P->quads_ev));
+    if (q.size() > P->hq_cap) {
+        if (g_capture)
+            return fail(ACE_ERR_INVALID_ARG, "pair list longer than any enqueued on this plan outside stream capture");
+        if (P->h_quads) cudaFreeHost(P->h_quads);
+        P->h_quads = nullptr;
+        P->hq_cap = 0;
+        if (cudaMallocHost((void**)&P->h_quads, q.size() * sizeof(Quad)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ACE_ERR_OOM, "pinned host allocation failed");
+        }
+        P->hq_cap = q.size();
+    }
+    std::memcpy(P->h_quads, q.data(), q.size() * sizeof(Quad));
+    ACE_CK(cudaMemcpyAsync(P->d_quads, P->h_quads, q.size() * sizeof(Quad), cudaMemcpyHostToDevice, st));
+    if (!g_capture) ACE_CK(cudaEventRecord(P->quads_ev, st));
     return ACE_OK;
 }
 
@@ -780,6 +817,9 @@ int apply_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, v
 
 void free_plan(ace_plan* P) {
     if (P->h_res) cudaFreeHost(P->h_res);
+    if (P->quads_ev) cudaEventSynchronize(P->quads_ev);
+    if (P->h_quads) cudaFreeHost(P->h_quads);
+    if (P->quads_ev) cudaEventDestroy(P->quads_ev);
     for (auto& m : P->marks) cudaEventDestroy(m.ev);
     for (auto e : P->ev_pool) cudaEventDestroy(e);
     for (auto s2 : P->aux) cudaStreamDestroy(s2);
@@ -1079,6 +1119,28 @@ int ace_build(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const 
                                   : build_impl<float>(plan, psi_G, n_occ, alpha, pair_row_ptr, pair_col, xi, E_x, st);
 }
 
+int ace_build_async(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const int32_t* pair_row_ptr,
+                    const int32_t* pair_col, void* xi, void* stream) {
+    if (!plan || !psi_G || !xi) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (n_occ < 1 || n_occ > plan->n_occ_max) return fail(ACE_ERR_INVALID_ARG, "n_occ out of range");
+    if ((pair_row_ptr == nullptr) != (pair_col == nullptr))
+        return fail(ACE_ERR_INVALID_ARG, "pair_row_ptr and pair_col must both be set or both be NULL");
+    DeviceGuard g(plan->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    g_capture = capturing(st);
+    const int rc = plan->prec == ACE_FP64
+                       ? build_enqueue<double>(plan, psi_G, n_occ, alpha, pair_row_ptr, pair_col, xi, st)
+                       : build_enqueue<float>(plan, psi_G, n_occ, alpha, pair_row_ptr, pair_col, xi, st);
+    g_capture = false;
+    return rc;
+}
+
+int ace_build_result(ace_plan* plan, double* E_x, void* stream) {
+    if (!plan) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    DeviceGuard g(plan->dev);
+    return build_finish(plan, E_x, (cudaStream_t)stream);
+}
+
 int ace_build_pairs(ace_plan* plan, const void* psi_G, int n_occ, double alpha, const int32_t* pair_row_ptr,
                     const int32_t* pair_col, void* W_G, double* E_part, void* stream) {
     if (!plan || !psi_G || !W_G) return fail(ACE_ERR_INVALID_ARG, "null argument");
@@ -1119,8 +1181,11 @@ int ace_apply(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T,
     if (T == 0) return ACE_OK;
     DeviceGuard g(plan->dev);
     cudaStream_t st = (cudaStream_t)stream;
-    return plan->prec == ACE_FP64 ? apply_impl<double>(plan, xi, n_occ, psi, T, Kpsi, st)
-                                  : apply_impl<float>(plan, xi, n_occ, psi, T, Kpsi, st);
+    g_capture = capturing(st);
+    const int rc = plan->prec == ACE_FP64 ? apply_impl<double>(plan, xi, n_occ, psi, T, Kpsi, st)
+                                          : apply_impl<float>(plan, xi, n_occ, psi, T, Kpsi, st);
+    g_capture = false;
+    return rc;
 }
 
 int hfx_apply_exact(ace_plan* plan, const void* psi_occ, int n_occ, double alpha, const void* psi, int T,

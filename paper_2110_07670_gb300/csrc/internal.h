@@ -124,6 +124,17 @@ struct PipeArgs {
 };
 cudaError_t pipeline_pair_launch(int n, const PassArgs& a, const PipeArgs& p, cudaStream_t st);
 
+// True while `st` records into a CUDA graph: launchers then leave kernel
+// attributes alone (set by the same launch outside capture before).
+inline bool stream_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 // compile-time cube passes (cube_*.cu), single precision
 cudaError_t cube_pass_launch(int n, const PassArgs& a, const PassShape& s, int pro, int epi, int mid, int sgn,
                              int batch, cudaStream_t st);

@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pa
 template <typename Shape, typename R, int PRO, int EPI, int MID, int SGN>
 cudaError_t launch_one(const PassArgs& a, const PassShape& s, int batch, cudaStream_t st) {
     auto k = tile_pass<Shape, R, PRO, EPI, MID, SGN>;
-    if (s.smem > 48 * 1024) {
+    if (s.smem > 48 * 1024 && !stream_capturing(st)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
         if (e != cudaSuccess) return e;
     }

@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) inv_accum(Pass
 
 template <typename K>
 cudaError_t launch_plane(K k, size_t smem, int n, int nt, const PassArgs& a, int batch, cudaStream_t st) {
-    if (smem > 48 * 1024) {
+    if (smem > 48 * 1024 && !stream_capturing(st)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }

@@ -233,8 +233,10 @@ cudaError_t launch_gram_partial_umma(const float* A, const float* B, int m, int 
                                      cudaStream_t st) {
     if (K % 2 != 0 || ((uintptr_t)A % 8) || ((uintptr_t)B % 8)) return cudaErrorInvalidValue;
     const size_t smem = sizeof(GramSmem) + 1024;
-    cudaError_t e = cudaFuncSetAttribute(gram_partial_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (!stream_capturing(st)) {
+        cudaError_t e = cudaFuncSetAttribute(gram_partial_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     dim3 grid((m + TM - 1) / TM, (n + TN - 1) / TN, gram_umma_chunks(K));
     gram_partial_umma<<<grid, NTHR, smem, st>>>(A, B, m, n, K, (long long)KCHUNK, 0, P, err);
     return cudaGetLastError();

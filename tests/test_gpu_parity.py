@@ -335,3 +335,35 @@ def test_mts_harness_matches_oracle(prec):
     # the ACE energy of Phi_0 itself is the exact one (exactness on span(Phi_0))
     assert abs(mts.gamma_energy(s["psi"], oracle.ace_apply(ref0["xi"], s["psi"], ref0["miller"])) - ref0["E_x"]) \
         <= 1e-10 * abs(ref0["E_x"])
+
+
+@pytest.mark.parametrize("variant", [1, 3])
+def test_cuda_graph_capture_of_build_and_apply(variant):
+    """ace_build_async + ace_apply captured in one CUDA graph (after one run
+    outside capture): replays match the oracle, and a replay after new
+    orbitals are copied into the captured input buffer builds from them."""
+    s = gen.config_small()
+    n = len(s["psi"])
+    psi2 = gen.random_orbitals(s["cell"], s["ecut"], n, seed=44)
+    tr_h = gen.random_trials(s["cell"], s["ecut"], 5, seed=45)
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "mixed", pair_variant=variant)
+    psi = dev(s["psi"], plan)
+    tr = dev(tr_h, plan)
+    xi = torch.empty_like(psi)
+    K = torch.empty_like(tr)
+    ace.ace_build_async(plan, psi, s["alpha"], xi=xi)  # outside capture: allocations, attributes
+    ace.ace_apply(plan, xi, tr, out=K)
+    ace.ace_build_result(plan)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ace.ace_build_async(plan, psi, s["alpha"], xi=xi)
+        ace.ace_apply(plan, xi, tr, out=K)
+    for orb in (s["psi"], psi2):
+        psi.copy_(dev(orb, plan))
+        g.replay()
+        E = ace.ace_build_result(plan)
+        ref = oracle.ace_build(orb, s["cell"], s["grid"], s["ecut"], s["alpha"])
+        assert abs(E - ref["E_x"]) / s["n_atom"] <= TOL["mixed"]["E"]
+        assert rel(host(K), oracle.ace_apply(ref["xi"], tr_h, ref["miller"])) <= TOL["mixed"]["K"]
+    del g
+    plan.close()
