@@ -374,6 +374,51 @@ def run_ours(args):
         s_mtace["mts_exact_over_inner"] = ms_per_step / min(ts_)
         del Kp
 
+    # ---- the same step replayed from a CUDA graph (build + apply captured once),
+    # and on the small 8-orbital / 32^3 case, where launches dominate
+    graph = None
+    if world == 1:
+        def graph_ms(pl, ps, trs, steps):
+            xg = torch.empty_like(ps)
+            kg = torch.empty_like(trs)
+            ace.ace_build_async(pl, ps, cfg["alpha"], xi=xg)
+            ace.ace_apply(pl, xg, trs, out=kg)
+            ace.ace_build_result(pl)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                ace.ace_build_async(pl, ps, cfg["alpha"], xi=xg)
+                ace.ace_apply(pl, xg, trs, out=kg)
+            g.replay()
+            torch.cuda.synchronize()
+            eager, replay = [], []
+            for _ in range(steps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                ace.ace_build(pl, ps, cfg["alpha"], xi=xg)
+                ace.ace_apply(pl, xg, trs, out=kg)
+                b.record()
+                torch.cuda.synchronize()
+                eager.append(a.elapsed_time(b))
+                a.record()
+                g.replay()
+                b.record()
+                torch.cuda.synchronize()
+                ace.ace_build_result(pl)
+                replay.append(a.elapsed_time(b))
+            del g
+            return statistics.median(eager), statistics.median(replay)
+        e_ms, r_ms = graph_ms(plan, psi, tr, 3)
+        import gen
+        small = gen.config_small()
+        ps_ = ace.Plan(small["grid"], small["cell"], small["ecut"], 8, "mixed")
+        psi_s = torch.from_numpy(small["psi"].astype(np.complex64)).cuda()
+        tr_s = torch.from_numpy(gen.random_trials(small["cell"], small["ecut"], 8, 2).astype(np.complex64)).cuda()
+        e1, r1 = graph_ms(ps_, psi_s, tr_s, 20)
+        ps_.close()
+        graph = {"workload_ms_eager": e_ms, "workload_ms_graph": r_ms, "workload_pairs_per_s_graph": npairs / (r_ms / 1e3),
+                 "small_8orb_32cubed_ms_eager": e1, "small_8orb_32cubed_ms_graph": r1}
+
     # ---- end to end through the public API with host buffers
     psi_h = torch.from_numpy(cfg["psi"].astype(np.complex64)).pin_memory()
     tr_h = torch.from_numpy(my_trials.astype(np.complex64)).pin_memory()
@@ -440,7 +485,7 @@ def run_ours(args):
                        "pair_kernels": kcfg},
             "ace_builds_per_s": builds, "E_x": E_mixed, "fp64_gpu": fp64,
             "phases_ms_per_step": {k: v / args.steps for k, v in stats.items() if k.endswith("_ms")},
-            "s_mtace": s_mtace,
+            "s_mtace": s_mtace, "cuda_graph": graph,
             "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clocks}
     print(json.dumps(line), flush=True)
