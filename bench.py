@@ -491,7 +491,7 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(n_occ, batch=64):
+def profile_case(n_occ, batch=64, pair_variant=1, pair_streams=1):
     """One small ACE build on the 96^3 workload grid (n_occ orbitals): the
     case the ncu captures under profiles/ run."""
     import torch
@@ -499,10 +499,29 @@ def profile_case(n_occ, batch=64):
     import gen
     import paper_2110_07670_gb300 as ace
     psi, _ = gen.water_orbitals(18.6, 80.0, n_occ, 2)
-    plan = ace.Plan((96, 96, 96), gen.cubic_cell(18.6), 80.0, n_occ, "mixed", pair_batch=batch)
+    plan = ace.Plan((96, 96, 96), gen.cubic_cell(18.6), 80.0, n_occ, "mixed", pair_batch=batch,
+                    pair_variant=pair_variant, pair_streams=pair_streams)
     xi, E = ace.ace_build(plan, torch.from_numpy(psi.astype(np.complex64)).cuda(), 0.25)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": n_occ, "E_x": E}))
+
+
+def profile_overlap(n_occ, reps=3):
+    """The s-MTACE overlap screen (Section 2.4) of the first n_occ of the 128
+    water-box orbitals on the 96^3 grid: the |phi| Gram on tcgen05 that the
+    ncu captures under profiles/ run."""
+    import torch
+
+    import gen
+    import paper_2110_07670_gb300 as ace
+    psi, _ = gen.water_orbitals(18.6, 80.0, 128, 2)
+    plan = ace.Plan((96, 96, 96), gen.cubic_cell(18.6), 80.0, n_occ, "mixed", pair_variant=1)
+    d = torch.from_numpy(psi[:n_occ].astype(np.complex64)).cuda()
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        pairs, _ = ace.ace_overlap_screen(plan, d, 2.5e-2)
+        ms = (time.perf_counter() - t0) * 1e3
+    print(json.dumps({"profile_overlap": n_occ, "pairs_kept": int(pairs[0][-1]), "ms": ms}))
 
 
 def profile_apply(T, reps=3):
@@ -548,9 +567,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", type=int, default=0, help="run one small build with this many orbitals")
     ap.add_argument("--profile-apply", type=int, default=0, help="run ACE applies on this many trial vectors")
+    ap.add_argument("--profile-overlap", type=int, default=0, help="run the overlap screen on this many orbitals")
+    ap.add_argument("--pair-variant", type=int, default=1, help="pair-pass kernels of --profile-case (1, 2, 3)")
+    ap.add_argument("--pair-streams", type=int, default=1, help="pair streams of --profile-case")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case)
+        profile_case(args.profile_case, pair_variant=args.pair_variant, pair_streams=args.pair_streams)
+        return
+    if args.profile_overlap:
+        profile_overlap(args.profile_overlap)
         return
     if args.profile_apply:
         profile_apply(args.profile_apply)
