@@ -288,7 +288,8 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     kcfg = plan.config()
     variant, streams = kcfg["pair_variant"], kcfg["pair_streams"]
-    vname = {1: "tile passes", 2: "transposed-plane passes", 3: "persistent pipeline kernel"}[variant]
+    vname = {1: "tile passes", 2: "transposed-plane passes", 3: "persistent pipeline kernel",
+             4: "plane-kernel forward pass, tile passes after it"}[variant]
     group = 32 if (variant != 3 and streams == 2) else 64  # transforms per launch (algorithmic count)
     pbg, _ = pass_bytes(n, N, batch=group)
     pipe_bytes = sum(pbg.values())  # per build
@@ -307,14 +308,16 @@ def run_ours(args):
         ps.close()
         pb64, nl64 = pass_bytes(n, N, batch=64)
         per_pass = {}
-        per_pass["variant"] = "tile passes" if variant != 2 else "transposed-plane passes"
+        per_pass["variant"] = {1: "tile passes", 2: "transposed-plane passes", 3: "tile passes",
+                               4: "hybrid"}[variant]
         for k in ("pair_fwd", "pair_coulomb", "pair_inv"):
             ms = st1[k + "_ms"] / 2
             per_pass[k] = {"ms_per_build": ms, "launches_per_build": nl64,
                            "algorithmic_bytes_per_launch": pb64[k] / nl64,
                            "achieved_gbs": pb64[k] / (ms / 1e3) / 1e9 if ms > 0 else 0.0,
                            "frac": (pb64[k] / (ms / 1e3) / 1e9) / hbm if ms > 0 else 0.0,
-                           "traffic_per_launch": MEASURED_TRAFFIC_PER_LAUNCH[k] if variant != 2 else None}
+                           "traffic_per_launch": MEASURED_TRAFFIC_PER_LAUNCH[k]
+                           if variant in (1, 3) or (variant == 4 and k != "pair_fwd") else None}
     layout = ("one launch for all transforms" if variant == 3 else
               "32-transform sub-batches on 2 streams" if streams == 2 else "64-transform launches on one stream")
     roofline = {"bound": "hbm",

@@ -75,7 +75,8 @@ typedef struct {
     int pair_streams;  /* streams the pair sub-batches overlap on; 0 = automatic,
                           1 = every pass in order on the call's stream */
     int pair_variant;  /* kernels of the pair passes (Eq. 2-4): 1 tile passes, 2 transposed-
-                          plane passes, 3 one persistent kernel for all three passes (2 and 3:
+                          plane passes, 3 one persistent kernel for all three passes, 4 the
+                          plane-kernel forward pass with the tile passes after it (2, 3, 4:
                           single precision, n^3 boxes with n in {32, 80, 96, 160});
                           0 = automatic: where several apply (and pair_streams is 0, both 1
                           and 2 streams) they are timed at plan creation on the plan's own
@@ -94,10 +95,10 @@ int ace_plan_create(ace_plan** plan, const int grid[3], const double cell[9], do
 
 void ace_plan_destroy(ace_plan* plan);
 
-/* The plan's pair-pass kernels: pair_variant (1, 2 or 3 as in ace_opts),
- * pair_streams, and, where plan creation timed them, tune_ms[4] = ms per
+/* The plan's pair-pass kernels: pair_variant (1 to 4 as in ace_opts),
+ * pair_streams, and, where plan creation timed them, tune_ms[5] = ms per
  * timing run of {tile passes on 1 stream, on 2 streams, transposed-plane
- * passes, persistent kernel} (0 = not timed).  Any output may be NULL. */
+ * passes, persistent kernel, hybrid} (0 = not timed).  Any output may be NULL. */
 int ace_plan_config(const ace_plan* plan, int* pair_variant, int* pair_streams, float* tune_ms);
 
 /* Number of half-sphere plane waves and, when miller != NULL, their Miller

@@ -106,8 +106,9 @@ struct ace_plan {
     bool zline = false;        // per-pencil Coulomb pass (zline.cuh) with the kernel table d_kern
     float* d_kern = nullptr;   // 4 pi / |G|^2 / N in the tile passes' spectrum layout (zline only)
     float* d_kern_t = nullptr; // the same for transposed planes (n % 16 == 0 cubes)
-    int variant = 1;           // pair passes: 1 tile, 2 transposed planes, 3 persistent pipeline
-    float tune_ms[4] = {0, 0, 0, 0};  // autotune timings: tile x1 stream, tile x2, planes x2, pipeline
+    int variant = 1;           // pair passes: 1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid
+    bool hybrid = false;       // variant 4: plane-kernel P1 in the tile layout, then the tile P2 / P3
+    float tune_ms[5] = {0, 0, 0, 0, 0};  // autotune: tile x1 stream, tile x2, planes x2, pipeline, hybrid x2
     bool tplane = false;       // pair passes with transposed spectrum planes (plane.cuh; needs zline)
     int pair_tile = 0;         // pairs ordered in pair_tile x pair_tile orbital blocks (0: row by row; env ACE_PAIR_TILE)
     int pair_streams = 2;      // concurrent streams of pair sub-batches
@@ -391,6 +392,12 @@ int pair_batch(ace_plan* P, PassArgs& a, int nb, cudaStream_t st, int lane) {
         ACE_CKL(zline_coulomb_launch(P->n[0], a, nb, st));
         mark(P, PH_PINV, st, lane);
         ACE_CKL(tplane_pair_launch(P->n[0], 1, a, nb, st));
+    } else if (P->hybrid) {
+        ACE_CKL(tplane_pair_launch(P->n[0], 2, a, nb, st));
+        mark(P, PH_PCOUL, st, lane);
+        ACE_CKL(zline_coulomb_launch(P->n[0], a, nb, st));
+        mark(P, PH_PINV, st, lane);
+        ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_LOAD, EPI_ACCUM, MID_NONE, +1, nb, st));
     } else if (P->fused_xy) {
         ACE_CKL(launch_pass<R>(a, P->s_xy, PRO_PAIR, EPI_STORE, MID_NONE, -1, nb, st));
         mark(P, PH_PCOUL, st, lane);
@@ -837,6 +844,7 @@ void set_variant(ace_plan* P, int v, int streams) {
     P->variant = v;
     P->tplane = v == 2 || v == 3;
     P->fused = v == 3;
+    P->hybrid = v == 4;
     P->pair_streams = streams;
 }
 
@@ -849,10 +857,10 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     const int req = opts ? opts->pair_variant : 0;
     const int fixed_streams = opts && opts->pair_streams > 0 ? opts->pair_streams : 0;
     const bool t_ok = sizeof(R) == 4 && P->zline && P->d_kern_t != nullptr;
-    if (req < 0 || req > 3) return fail(ACE_ERR_INVALID_ARG, "pair_variant must be 0 (automatic), 1, 2 or 3");
-    if ((req == 2 || req == 3) && !t_ok)
+    if (req < 0 || req > 4) return fail(ACE_ERR_INVALID_ARG, "pair_variant must be 0 (automatic), 1, 2, 3 or 4");
+    if (req >= 2 && !t_ok)
         return fail(ACE_ERR_INVALID_ARG,
-                    "pair_variant 2 and 3 need a single-precision n^3 plan with n in {32, 80, 96, 160}");
+                    "pair_variant 2, 3 and 4 need a single-precision n^3 plan with n in {32, 80, 96, 160}");
     if (req > 0) {
         set_variant(P, req, fixed_streams ? fixed_streams : 2);
         return ACE_OK;
@@ -866,6 +874,7 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     if (t_ok) {
         cand.push_back({2, fixed_streams ? fixed_streams : 2, 2});
         cand.push_back({3, 1, 3});
+        cand.push_back({4, fixed_streams ? fixed_streams : 2, 4});
     }
     if (sizeof(R) != 4 || cand.size() == 1) {  // double plans: no timing, the two-stream tile passes
         set_variant(P, 1, fixed_streams ? fixed_streams : 2);
@@ -1350,7 +1359,7 @@ int ace_plan_config(const ace_plan* plan, int* pair_variant, int* pair_streams, 
     if (pair_variant) *pair_variant = plan->variant;
     if (pair_streams) *pair_streams = plan->variant == 3 ? 1 : plan->pair_streams;
     if (tune_ms)
-        for (int i = 0; i < 4; ++i) tune_ms[i] = plan->tune_ms[i];
+        for (int i = 0; i < 5; ++i) tune_ms[i] = plan->tune_ms[i];
     return ACE_OK;
 }
 

@@ -109,10 +109,12 @@ __device__ __forceinline__ void prefetch_planes(const PassArgs& a, const Quad& q
 }
 
 // Plane z of one transform (quad q): pair product, 2-D forward FFT, and the
-// plane stored transposed into spec_t (the transform's spectrum).  tw holds
-// the N twiddles in shared memory (visible to the block); the block's threads
-// all call this.
-template <int N>
+// plane stored into spec_t (the transform's spectrum): transposed ([x][y]),
+// or with NATURAL in the tile passes' layout (row y, x position p in slot
+// plane_swizzle(p, y)), through the shared tile and one more block barrier.
+// tw holds the N twiddles in shared memory (visible to the block); the
+// block's threads all call this.
+template <int N, bool NATURAL = false>
 __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q, int z, cx<float>* tile,
                                                const cx<float>* tw, cx<float>* spec_t) {
     using G = Geo<N>;
@@ -173,20 +175,35 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
     }
     __syncwarp();
     if (active) {
-        const cx<float>* row = tile + line * G::P;
+        cx<float>* row = tile + line * G::P;
         cx<float>* out = spec_t + plane0 + line;
         for (int b = h; b < G::B1; b += 2) {
             cx<float> u[G::R1];
 #pragma unroll
             for (int k = 0; k < G::R1; ++k) u[k] = row[b * G::R1 + k];
             Dft<G::R1, -1, float>::run(u);
+            if constexpr (NATURAL) {
 #pragma unroll
-            for (int s = 0; s < G::R1; ++s) out[(long long)(b * G::R1 + s) * N] = u[s];
+                for (int s = 0; s < G::R1; ++s) row[b * G::R1 + s] = u[s];
+            } else {
+#pragma unroll
+                for (int s = 0; s < G::R1; ++s) out[(long long)(b * G::R1 + s) * N] = u[s];
+            }
+        }
+    }
+    if constexpr (NATURAL) {
+        // rows out with the lanes along x: 32 consecutive positions per warp,
+        // permuted within 16-blocks by the slot swizzle, stay coalesced
+        __syncthreads();
+        cx<float>* out = spec_t + plane0;
+        for (int e = threadIdx.x; e < N * N; e += G::NT) {
+            const int y = e / N, x = e - y * N;
+            out[y * N + plane_swizzle(x, y)] = tile[y * G::P + x];
         }
     }
 }
 
-template <int N>
+template <int N, bool NATURAL>
 __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) pair_fwd(PassArgs a) {
     using G = Geo<N>;
     constexpr long long NN = (long long)N * N, N3 = NN * N;
@@ -200,7 +217,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) pair_fwd(PassA
     if (threadIdx.x == 32 && a.lookahead > 0 && t + a.lookahead < (int)gridDim.y && (NN * 4) % 16 == 0)
         prefetch_planes(a, a.quads[a.t0 + t + a.lookahead], plane0, (uint32_t)(NN * 4), N3, false);
     __syncthreads();
-    pair_fwd_plane<N>(a, q, z, tile, tw, reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride);
+    pair_fwd_plane<N, NATURAL>(a, q, z, tile, tw, reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride);
 }
 
 // Inputs of the inverse pass: thread (row y, half h) needs the transposed
@@ -431,11 +448,16 @@ cudaError_t launch_plane(K k, size_t smem, int n, int nt, const PassArgs& a, int
 
 }  // namespace plane_detail
 
-// which: 0 = pair product + forward plane FFT, 1 = inverse plane FFT + accumulation
+// which: 0 = pair product + forward plane FFT (transposed planes out),
+// 1 = inverse plane FFT + accumulation, 2 = the forward pass with the tile
+// passes' plane layout out (the hybrid variant)
 template <int N>
 cudaError_t tplane_launch(int which, const PassArgs& a, int batch, cudaStream_t st) {
     using G = plane_detail::Geo<N>;
-    if (which == 0) return plane_detail::launch_plane(plane_detail::pair_fwd<N>, G::smem, N, G::NT, a, batch, st);
+    if (which == 0)
+        return plane_detail::launch_plane(plane_detail::pair_fwd<N, false>, G::smem, N, G::NT, a, batch, st);
+    if (which == 2)
+        return plane_detail::launch_plane(plane_detail::pair_fwd<N, true>, G::smem, N, G::NT, a, batch, st);
     return plane_detail::launch_plane(plane_detail::inv_accum<N>, G::smem, N, G::NT, a, batch, st);
 }
 
