@@ -1050,7 +1050,7 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     ACE_TRY(dalloc((void**)&P->d_M, nn * sizeof(double)));
     ACE_TRY(dalloc((void**)&P->d_L, nn * sizeof(double)));
     ACE_TRY(dalloc((void**)&P->d_Linv, nn * sizeof(double)));
-    ACE_TRY(dalloc((void**)&P->d_E, sizeof(double)));
+    ACE_TRY(dalloc((void**)&P->d_E, (1 + 16384) * sizeof(double)));  // E_x, then the energy reduction's block sums
     ACE_TRY(dalloc((void**)&P->d_status, sizeof(int)));
     ACE_TRY(dalloc((void**)&P->d_err, sizeof(int)));
     if (cudaMallocHost((void**)&P->h_res, sizeof(ace_plan::Result)) != cudaSuccess) {

@@ -197,7 +197,8 @@ cudaError_t launch_gemm_nn(const double* A, int m, int k, const R* B, long long 
 cudaError_t launch_neg_cholesky_inverse(const double* M, int n, double* L, double* Linv, int* status,
                                         cudaStream_t st);
 
-// E = -alpha * wscale * sum_t sum_tile (w1 e1 + w2 e2), deterministic order.
+// E[0] = coef * sum_t sum_tile (w1 e1 + w2 e2), deterministic order; E[1 ..]
+// holds up to 16384 block sums (room for 1 + 16384 doubles).
 cudaError_t launch_energy_reduce(const double* e_part, const Quad* quads, int ntrans, int ntiles, double coef,
                                  double* E, cudaStream_t st);
 

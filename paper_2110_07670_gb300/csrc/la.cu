@@ -293,6 +293,96 @@ __global__ void __launch_bounds__(1024) energy_reduce_kernel(const double* __res
     if (threadIdx.x == 0) *E = coef * red[0];
 }
 
+// The same reduction in two fixed-order stages: block b sums transforms
+// b ER_T .. b ER_T + ER_T - 1 (a warp per transform, lanes over the planes)
+// into out[b]; energy_final_kernel adds the block sums in order.
+constexpr int ER_T = 32, ER_MAXB = 1 << 14;
+__global__ void __launch_bounds__(256) energy_partial_kernel(const double* __restrict__ e_part,
+                                                             const Quad* __restrict__ quads, int ntrans,
+                                                             int ntiles, double* __restrict__ out) {
+    __shared__ double ws[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int tt = warp; tt < ER_T; tt += 8) {
+        const int t = blockIdx.x * ER_T + tt;
+        if (t >= ntrans) break;
+        const Quad q = quads[t];
+        double e1 = 0.0, e2 = 0.0;
+        for (int k = lane; k < ntiles; k += 32) {
+            e1 += e_part[((long long)t * ntiles + k) * 2];
+            e2 += e_part[((long long)t * ntiles + k) * 2 + 1];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            e1 += __shfl_xor_sync(0xffffffffu, e1, o);
+            e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        }
+        acc += (q.a != q.b ? 2.0 : 1.0) * e1 + (q.c >= 0 ? (q.c != q.d ? 2.0 : 1.0) * e2 : 0.0);
+    }
+    if (lane == 0) ws[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += ws[w];
+        out[blockIdx.x] = s;
+    }
+}
+
+__global__ void energy_final_kernel(const double* __restrict__ part, int nb, double coef, double* __restrict__ E) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) s += part[b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *E = coef * s;
+}
+
+// -M = L L^T and L^-1 with both in shared memory (n^2 doubles, n <= 160):
+// right-looking Cholesky in place, L copied out, then L^-1 in the same
+// buffer, one column per thread, reading L back through L1.
+__global__ void __launch_bounds__(1024) neg_cholesky_inverse_smem_kernel(const double* __restrict__ M, int n,
+                                                                          double* __restrict__ L,
+                                                                          double* __restrict__ Linv,
+                                                                          int* __restrict__ status) {
+    extern __shared__ double A[];
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        A[e] = i >= j ? -0.5 * (M[(long long)i * n + j] + M[(long long)j * n + i]) : 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            const double d = A[k * n + k];
+            if (!(d > 0.0)) bad = 1;
+            A[k * n + k] = d > 0.0 ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        const double dkk = A[k * n + k];
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * n + k] /= dkk;
+        __syncthreads();
+        const int m = n - k - 1;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = k + 1 + e / m, j = k + 1 + e % m;
+            if (j <= i) A[i * n + j] -= A[i * n + k] * A[j * n + k];
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) L[e] = A[e];
+    __syncthreads();
+    // column j of L^-1 by forward substitution, kept in A's column j
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        for (int i = 0; i < j; ++i) A[i * n + j] = 0.0;
+        A[j * n + j] = 1.0 / L[(long long)j * n + j];
+        for (int i = j + 1; i < n; ++i) {
+            double s = 0.0;
+            for (int k = j; k < i; ++k) s += L[(long long)i * n + k] * A[k * n + j];
+            A[i * n + j] = -s / L[(long long)i * n + i];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Linv[e] = A[e];
+    if (threadIdx.x == 0) *status = bad;
+}
+
 }  // namespace
 
 template <typename R>
@@ -366,13 +456,29 @@ cudaError_t launch_gemm_nn(const double* A, int m, int k, const R* B, long long 
 
 cudaError_t launch_neg_cholesky_inverse(const double* M, int n, double* L, double* Linv, int* status,
                                         cudaStream_t st) {
-    neg_cholesky_inverse_kernel<<<1, 1024, 0, st>>>(M, n, L, Linv, status);
+    const size_t smem = (size_t)n * n * sizeof(double);
+    if (smem <= 200 * 1024) {
+        static const cudaError_t attr = cudaFuncSetAttribute(
+            neg_cholesky_inverse_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (attr != cudaSuccess) return attr;
+        neg_cholesky_inverse_smem_kernel<<<1, 1024, smem, st>>>(M, n, L, Linv, status);
+    } else {
+        neg_cholesky_inverse_kernel<<<1, 1024, 0, st>>>(M, n, L, Linv, status);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_energy_reduce(const double* e_part, const Quad* quads, int ntrans, int ntiles, double coef,
                                  double* E, cudaStream_t st) {
-    energy_reduce_kernel<<<1, 1024, 0, st>>>(e_part, quads, ntrans, ntiles, coef, E);
+    // stage 1: blocks of ER_T transforms into per-block sums (in E[1 ..]);
+    // stage 2: one warp adds them in block order
+    const int nb = std::max(1, (ntrans + ER_T - 1) / ER_T);
+    if (nb > ER_MAXB) {
+        energy_reduce_kernel<<<1, 1024, 0, st>>>(e_part, quads, ntrans, ntiles, coef, E);
+        return cudaGetLastError();
+    }
+    energy_partial_kernel<<<nb, 256, 0, st>>>(e_part, quads, ntrans, ntiles, E + 1);
+    energy_final_kernel<<<1, 32, 0, st>>>(E + 1, nb, coef, E);
     return cudaGetLastError();
 }
 
