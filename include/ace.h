@@ -289,6 +289,16 @@ typedef struct {
 int ace_set_timing(ace_plan* plan, int enable);
 int ace_get_stats(ace_plan* plan, ace_stats* stats);
 
+/*
+ * The failure path of the library's bounded device-side waits, exercised
+ * without a fault (the paper has no counterpart): one block waits, for at
+ * most limit_ms (1 .. 2000), on a barrier that nothing completes, exactly as
+ * a bulk copy or a pipeline dependency that never arrives would be waited
+ * for.  Returns ACE_ERR_TIMEOUT, as a real time-out does; the plan and the
+ * CUDA context stay usable.  Synchronises the stream.
+ */
+int ace_check_timeout_path(ace_plan* plan, int limit_ms, void* stream);
+
 /* Message of this thread's last error ("" if none); returns its length. */
 int ace_last_error(char* buf, int len);
 

@@ -24,7 +24,8 @@ _ERRORS = {-1: "ACE_ERR_INVALID_ARG", -2: "ACE_ERR_GRID_TOO_SMALL", -3: "ACE_ERR
 SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_apply", "hfx_apply_exact",
            "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc",
            "ace_build_batched", "ace_save", "ace_load", "ace_build_pairs", "ace_build_finish",
-           "ace_plan_config", "ace_overlap_screen", "ace_build_async", "ace_build_result")
+           "ace_plan_config", "ace_overlap_screen", "ace_build_async", "ace_build_result",
+           "ace_check_timeout_path")
 
 _lib = None
 
@@ -81,6 +82,7 @@ def load(build_if_missing=False):
     lib.ace_build_pairs.argtypes = [P, P, i32, f64, P, P, P, ctypes.POINTER(f64), P]
     lib.ace_build_finish.argtypes = [P, P, i32, P, P, P]
     lib.ace_build_async.argtypes = [P, P, i32, f64, P, P, P, P]
+    lib.ace_check_timeout_path.argtypes = [P, i32, P]
     lib.ace_build_result.argtypes = [P, ctypes.POINTER(f64), P]
     lib.ace_overlap_screen.argtypes = [P, P, i32, f64, P, P, ctypes.POINTER(i32), P, P]
     lib.ace_plan_config.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
@@ -100,11 +102,16 @@ def load(build_if_missing=False):
     return lib
 
 
+def last_error():
+    """Message of this thread's last library error ("" if none)."""
+    buf = ctypes.create_string_buffer(512)
+    load().ace_last_error(buf, 512)
+    return buf.value.decode()
+
+
 def _check(code):
     if code != 0:
-        buf = ctypes.create_string_buffer(512)
-        load().ace_last_error(buf, 512)
-        raise AceError(code, buf.value.decode())
+        raise AceError(code, last_error())
 
 
 def _stream(stream):
@@ -259,6 +266,12 @@ def ace_build_async(plan, psi_G, alpha, pairs=None, xi=None, stream=None):
                                   col.ctypes.data_as(ctypes.c_void_p) if col is not None else None,
                                   _ptr(xi), _stream(stream)))
     return xi
+
+
+def ace_check_timeout_path(plan, limit_ms=50, stream=None):
+    """Run the bounded-wait failure path once (a wait nothing completes);
+    returns the status code (ACE_ERR_TIMEOUT expected) without raising."""
+    return int(load().ace_check_timeout_path(plan.handle, int(limit_ms), _stream(stream)))
 
 
 def ace_build_result(plan, stream=None):

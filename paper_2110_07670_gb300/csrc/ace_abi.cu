@@ -1354,6 +1354,16 @@ int ace_last_intermediates(ace_plan* plan, void* W_G, double* M, void* stream) {
     return ACE_OK;
 }
 
+int ace_check_timeout_path(ace_plan* plan, int limit_ms, void* stream) {
+    if (!plan || limit_ms < 1 || limit_ms > 2000) return fail(ACE_ERR_INVALID_ARG, "limit_ms must be 1 .. 2000");
+    ace_plan* P = plan;
+    DeviceGuard g(P->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    ACE_CKL(launch_wait_for_nothing(P->d_err, limit_ms, st));
+    ACE_CK(cudaStreamSynchronize(st));
+    return check_device_error(P, st);
+}
+
 int ace_plan_config(const ace_plan* plan, int* pair_variant, int* pair_streams, float* tune_ms) {
     if (!plan) return fail(ACE_ERR_INVALID_ARG, "null argument");
     if (pair_variant) *pair_variant = plan->variant;

@@ -2,6 +2,7 @@
 // products of the ACE construction and apply, the FP64 Cholesky, and the
 // exchange-energy reduction (arXiv:2110.07670 Section 2.2 and Eq. 4-5).
 #include "internal.h"
+#include "tma.cuh"
 
 namespace ace {
 
@@ -383,7 +384,26 @@ __global__ void __launch_bounds__(1024) neg_cholesky_inverse_smem_kernel(const d
     if (threadIdx.x == 0) *status = bad;
 }
 
+// One block waits (bounded) on an mbarrier that expects 16 bytes no copy
+// will ever deliver: the time-out path of every bounded wait, without a fault
+// (nothing is in flight when the block leaves).
+__global__ void wait_for_nothing_kernel(int* err, unsigned long long limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&bar, 16);
+    }
+    __syncthreads();
+    mbar_wait_bounded(&bar, 0, err, 1, limit_ns);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_for_nothing(int* err, int limit_ms, cudaStream_t st) {
+    wait_for_nothing_kernel<<<1, 32, 0, st>>>(err, (unsigned long long)limit_ms * 1000000ull);
+    return cudaGetLastError();
+}
 
 template <typename R>
 cudaError_t launch_scatter(const cx<R>* psi, const Quad* quads, int t0, int batch, int npw, const int* ip,

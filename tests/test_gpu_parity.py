@@ -367,3 +367,19 @@ def test_cuda_graph_capture_of_build_and_apply(variant):
         assert rel(host(K), oracle.ace_apply(ref["xi"], tr_h, ref["miller"])) <= TOL["mixed"]["K"]
     del g
     plan.close()
+
+
+def test_bounded_wait_timeout_path_and_recovery():
+    """A device wait that nothing completes gives up after its limit and the
+    call returns ACE_ERR_TIMEOUT (no fault, nothing in flight); the plan and
+    the context stay usable: a build right after matches the oracle."""
+    s = small_system()
+    n = len(s["psi"])
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "mixed")
+    assert ace.ace_check_timeout_path(plan, 50) == -6
+    assert "timed out" in ace.last_error()
+    ref = oracle.ace_build(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    _, E = ace.ace_build(plan, dev(s["psi"], plan), s["alpha"])
+    assert abs(E - ref["E_x"]) / s["n_atom"] <= TOL["mixed"]["E"]
+    assert ace.ace_check_timeout_path(plan, 0) == -1  # limit out of range
+    plan.close()
