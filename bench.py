@@ -216,7 +216,8 @@ def run_ours(args):
     my_trials = trials[t_lo:t_hi]
 
     def setup(prec):
-        plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, prec)
+        plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, prec,
+                        pair_variant=(args.pair_variant or 0) if prec == "mixed" else 0)
         dt = np.complex64 if prec == "mixed" else np.complex128
         psi = torch.from_numpy(cfg["psi"].astype(dt)).cuda()
         tr = torch.from_numpy(my_trials.astype(dt)).cuda()
@@ -571,11 +572,12 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0, help="run one small build with this many orbitals")
     ap.add_argument("--profile-apply", type=int, default=0, help="run ACE applies on this many trial vectors")
     ap.add_argument("--profile-overlap", type=int, default=0, help="run the overlap screen on this many orbitals")
-    ap.add_argument("--pair-variant", type=int, default=1, help="pair-pass kernels of --profile-case (1, 2, 3)")
+    ap.add_argument("--pair-variant", type=int, default=None,
+                    help="pair-pass kernels (1-4); default: autotuned, and 1 for --profile-case")
     ap.add_argument("--pair-streams", type=int, default=1, help="pair streams of --profile-case")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case, pair_variant=args.pair_variant, pair_streams=args.pair_streams)
+        profile_case(args.profile_case, pair_variant=args.pair_variant or 1, pair_streams=args.pair_streams)
         return
     if args.profile_overlap:
         profile_overlap(args.profile_overlap)
