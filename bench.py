@@ -135,10 +135,12 @@ def pass_bytes(n, N, esz=4, batch=64):
 
 
 # DRAM bytes per launch (64 transforms) of the pair passes on this workload,
-# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; see
-# profiles/dram_pair_passes_water32_96cubed.md), for the kernels that run by
-# default; None where the kernel changed since the capture.
-MEASURED_TRAFFIC_PER_LAUNCH = {"pair_fwd": 0.8625e9, "pair_coulomb": 0.8464e9, "pair_inv": 1.7938e9}
+# from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum; see
+# profiles/dram_pair_passes_water32_96cubed.md): the tile-pass forward kernel,
+# the plane-kernel forward pass of the hybrid variant, and the Coulomb and
+# accumulation kernels both variants share.
+MEASURED_TRAFFIC_PER_LAUNCH = {"pair_fwd": 0.8625e9, "pair_fwd_hybrid": 0.8690e9, "pair_coulomb": 0.8472e9,
+                               "pair_inv": 1.7969e9}
 
 
 def cpu_baseline(cfg, rows=5):
@@ -296,7 +298,9 @@ def run_ours(args):
     pipe_bytes = sum(pbg.values())  # per build
     pair_wall = stats["pair_wall_ms"] / args.steps
     achieved = pipe_bytes / (pair_wall / 1e3) / 1e9 if pair_wall > 0 else 0.0
-    traffic_step = sum(MEASURED_TRAFFIC_PER_LAUNCH.values()) * (stats["pair_transforms"] / args.steps) / 64
+    fwd_key = "pair_fwd_hybrid" if variant == 4 else "pair_fwd"
+    traffic_step = (MEASURED_TRAFFIC_PER_LAUNCH[fwd_key] + MEASURED_TRAFFIC_PER_LAUNCH["pair_coulomb"] +
+                    MEASURED_TRAFFIC_PER_LAUNCH["pair_inv"]) * (stats["pair_transforms"] / args.steps) / 64
     # each pass alone (one stream, 64-transform launches), timed the same way:
     # the chosen variant's passes, or the tile passes when the choice is the
     # persistent kernel (which has no separate passes)
@@ -317,16 +321,16 @@ def run_ours(args):
                            "algorithmic_bytes_per_launch": pb64[k] / nl64,
                            "achieved_gbs": pb64[k] / (ms / 1e3) / 1e9 if ms > 0 else 0.0,
                            "frac": (pb64[k] / (ms / 1e3) / 1e9) / hbm if ms > 0 else 0.0,
-                           "traffic_per_launch": MEASURED_TRAFFIC_PER_LAUNCH[k]
-                           if variant in (1, 3) or (variant == 4 and k != "pair_fwd") else None}
+                           "traffic_per_launch": MEASURED_TRAFFIC_PER_LAUNCH[fwd_key if k == "pair_fwd" else k]
+                           if variant in (1, 3, 4) else None}
     layout = ("one launch for all transforms" if variant == 3 else
               "32-transform sub-batches on 2 streams" if streams == 2 else "64-transform launches on one stream")
     roofline = {"bound": "hbm",
                 "kernel": f"pair pipeline: P1 + P2 + P3 ({vname}), {layout}",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-                "traffic": traffic_step if world == 1 and variant == 1 else None,
-                "traffic_unit": "bytes per build (sum of the three tile passes' DRAM bytes from the ncu "
-                "capture, scaled from 64-transform launches)",
+                "traffic": traffic_step if world == 1 and variant in (1, 4) else None,
+                "traffic_unit": "bytes per build (sum of the three passes' DRAM bytes from the ncu "
+                "captures, scaled from 64-transform launches)",
                 "algorithmic_bytes_per_build": pipe_bytes, "pair_wall_ms_per_build": pair_wall,
                 "share_of_step": pair_wall / max(stats["total_ms"] / args.steps, 1e-9),
                 "per_pass_alone": per_pass}
