@@ -296,6 +296,8 @@ def run_ours(args):
     group = 32 if (variant != 3 and streams == 2) else 64  # transforms per launch (algorithmic count)
     pbg, _ = pass_bytes(n, N, batch=group)
     pipe_bytes = sum(pbg.values())  # per build
+    if world > 1:  # this rank's shard of the pairs: its share of the transforms
+        pipe_bytes *= (stats["pair_transforms"] / args.steps) / len(pair_quads(n))
     pair_wall = stats["pair_wall_ms"] / args.steps
     achieved = pipe_bytes / (pair_wall / 1e3) / 1e9 if pair_wall > 0 else 0.0
     fwd_key = "pair_fwd_hybrid" if variant == 4 else "pair_fwd"
