@@ -383,3 +383,18 @@ def test_bounded_wait_timeout_path_and_recovery():
     assert abs(E - ref["E_x"]) / s["n_atom"] <= TOL["mixed"]["E"]
     assert ace.ace_check_timeout_path(plan, 0) == -1  # limit out of range
     plan.close()
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+def test_hfx_exact_every_variant(variant):
+    """The exact exchange on trial vectors (one-sided accumulation: trials x
+    occupied pairs) through every pair-pass variant on the 32^3 cube, against
+    the oracle's V_X psi; an odd number of trials leaves a half-empty
+    transform."""
+    s = gen.config_small()
+    trials = gen.random_trials(s["cell"], s["ecut"], 7, seed=12)
+    ref = oracle.vx_apply(s["psi"], trials, s["cell"], s["grid"], s["ecut"], s["alpha"])
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], len(s["psi"]), "mixed", pair_variant=variant)
+    out = host(ace.hfx_apply_exact(plan, dev(s["psi"], plan), s["alpha"], dev(trials, plan)))
+    assert rel(out, ref) <= TOL["mixed"]["W"]
+    plan.close()
