@@ -76,8 +76,9 @@ typedef struct {
                           1 = every pass in order on the call's stream */
     int pair_variant;  /* kernels of the pair passes (Eq. 2-4): 1 tile passes, 2 transposed-
                           plane passes, 3 one persistent kernel for all three passes, 4 the
-                          plane-kernel forward pass with the tile passes after it (2, 3, 4:
-                          single precision, n^3 boxes with n in {32, 80, 96, 160});
+                          plane-kernel forward pass with the tile passes after it (2 and 3:
+                          single precision, n^3 boxes with n in {32, 80, 96, 160}; 4: single
+                          precision, n in {32, 60, 80, 90, 96, 100, 108, 120, 160});
                           0 = automatic: where several apply (and pair_streams is 0, both 1
                           and 2 streams) they are timed at plan creation on the plan's own
                           buffers and the fastest is kept (see ace_plan_config) */

@@ -857,10 +857,14 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     const int req = opts ? opts->pair_variant : 0;
     const int fixed_streams = opts && opts->pair_streams > 0 ? opts->pair_streams : 0;
     const bool t_ok = sizeof(R) == 4 && P->zline && P->d_kern_t != nullptr;
+    const bool h_ok = sizeof(R) == 4 && P->zline;  // every compile-time cube
     if (req < 0 || req > 4) return fail(ACE_ERR_INVALID_ARG, "pair_variant must be 0 (automatic), 1, 2, 3 or 4");
-    if (req >= 2 && !t_ok)
+    if ((req == 2 || req == 3) && !t_ok)
         return fail(ACE_ERR_INVALID_ARG,
-                    "pair_variant 2, 3 and 4 need a single-precision n^3 plan with n in {32, 80, 96, 160}");
+                    "pair_variant 2 and 3 need a single-precision n^3 plan with n in {32, 80, 96, 160}");
+    if (req == 4 && !h_ok)
+        return fail(ACE_ERR_INVALID_ARG,
+                    "pair_variant 4 needs a single-precision n^3 plan with n in {32, 60, 80, 90, 96, 100, 108, 120, 160}");
     if (req > 0) {
         set_variant(P, req, fixed_streams ? fixed_streams : 2);
         return ACE_OK;
@@ -874,8 +878,8 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     if (t_ok) {
         cand.push_back({2, fixed_streams ? fixed_streams : 2, 2});
         cand.push_back({3, 1, 3});
-        cand.push_back({4, fixed_streams ? fixed_streams : 2, 4});
     }
+    if (h_ok) cand.push_back({4, fixed_streams ? fixed_streams : 2, 4});
     if (sizeof(R) != 4 || cand.size() == 1) {  // double plans: no timing, the two-stream tile passes
         set_variant(P, 1, fixed_streams ? fixed_streams : 2);
         return ACE_OK;

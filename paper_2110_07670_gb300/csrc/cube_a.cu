@@ -20,5 +20,6 @@ template cudaError_t tplane_launch<32>(int, const PassArgs&, int, cudaStream_t);
 template cudaError_t tplane_launch<80>(int, const PassArgs&, int, cudaStream_t);
 template cudaError_t pipeline_launch<32>(const PassArgs&, const PipeArgs&, cudaStream_t);
 template cudaError_t pipeline_launch<80>(const PassArgs&, const PipeArgs&, cudaStream_t);
+template cudaError_t tplane_launch<60>(int, const PassArgs&, int, cudaStream_t);
 
 }  // namespace ace

@@ -18,5 +18,7 @@ template cudaError_t zline_launch<96>(const PassArgs&, int, cudaStream_t);
 template cudaError_t zline_launch<100>(const PassArgs&, int, cudaStream_t);
 template cudaError_t tplane_launch<96>(int, const PassArgs&, int, cudaStream_t);
 template cudaError_t pipeline_launch<96>(const PassArgs&, const PipeArgs&, cudaStream_t);
+template cudaError_t tplane_launch<90>(int, const PassArgs&, int, cudaStream_t);
+template cudaError_t tplane_launch<100>(int, const PassArgs&, int, cudaStream_t);
 
 }  // namespace ace

@@ -18,5 +18,7 @@ template cudaError_t zline_launch<120>(const PassArgs&, int, cudaStream_t);
 template cudaError_t zline_launch<160>(const PassArgs&, int, cudaStream_t);
 template cudaError_t tplane_launch<160>(int, const PassArgs&, int, cudaStream_t);
 template cudaError_t pipeline_launch<160>(const PassArgs&, const PipeArgs&, cudaStream_t);
+template cudaError_t tplane_launch<108>(int, const PassArgs&, int, cudaStream_t);
+template cudaError_t tplane_launch<120>(int, const PassArgs&, int, cudaStream_t);
 
 }  // namespace ace

@@ -51,16 +51,26 @@ cudaError_t zline_coulomb_launch(int n, const PassArgs& a, int batch, cudaStream
 
 #define ACE_TPLANE_DECL(N) extern template cudaError_t tplane_launch<N>(int, const PassArgs&, int, cudaStream_t);
 ACE_TPLANE_DECL(32)
+ACE_TPLANE_DECL(60)
 ACE_TPLANE_DECL(80)
+ACE_TPLANE_DECL(90)
 ACE_TPLANE_DECL(96)
+ACE_TPLANE_DECL(100)
+ACE_TPLANE_DECL(108)
+ACE_TPLANE_DECL(120)
 ACE_TPLANE_DECL(160)
 #undef ACE_TPLANE_DECL
 
 cudaError_t tplane_pair_launch(int n, int which, const PassArgs& a, int batch, cudaStream_t st) {
     switch (n) {
         case 32: return tplane_launch<32>(which, a, batch, st);
+        case 60: return tplane_launch<60>(which, a, batch, st);
         case 80: return tplane_launch<80>(which, a, batch, st);
+        case 90: return tplane_launch<90>(which, a, batch, st);
         case 96: return tplane_launch<96>(which, a, batch, st);
+        case 100: return tplane_launch<100>(which, a, batch, st);
+        case 108: return tplane_launch<108>(which, a, batch, st);
+        case 120: return tplane_launch<120>(which, a, batch, st);
         case 160: return tplane_launch<160>(which, a, batch, st);
         default: return cudaErrorInvalidValue;
     }

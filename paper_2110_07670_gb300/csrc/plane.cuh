@@ -35,7 +35,6 @@ template <int N>
 struct Geo {
     using PL = CPlan<N>;
     static_assert(PL::stages == 2, "plane passes assume two stages per axis");
-    static_assert(N % 16 == 0, "the vector epilogue tiles planes by 4 rows x 16 columns");
     static constexpr int R0 = PL::radix(0), R1 = PL::radix(1);
     static constexpr int M0 = N / R0;  // stage-0 butterflies per line (stride M0)
     static constexpr int B1 = N / R1;  // stage-1 butterflies per line (adjacent)
@@ -198,7 +197,7 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
         cx<float>* out = spec_t + plane0;
         for (int e = threadIdx.x; e < N * N; e += G::NT) {
             const int y = e / N, x = e - y * N;
-            out[y * N + plane_swizzle(x, y)] = tile[y * G::P + x];
+            out[y * N + (cube_swizzle(N) ? plane_swizzle(x, y) : x)] = tile[y * G::P + x];
         }
     }
 }
@@ -270,6 +269,7 @@ template <int N>
 __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q, int z, cx<float>* tile,
                                                 const cx<float>* tw, double* red, double* e_dst) {
     using G = Geo<N>;
+    static_assert(N % 16 == 0, "the vector epilogue tiles planes by 4 rows x 16 columns");
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     const long long plane0 = (long long)z * NN;
     const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
@@ -454,11 +454,15 @@ cudaError_t launch_plane(K k, size_t smem, int n, int nt, const PassArgs& a, int
 template <int N>
 cudaError_t tplane_launch(int which, const PassArgs& a, int batch, cudaStream_t st) {
     using G = plane_detail::Geo<N>;
-    if (which == 0)
-        return plane_detail::launch_plane(plane_detail::pair_fwd<N, false>, G::smem, N, G::NT, a, batch, st);
     if (which == 2)
         return plane_detail::launch_plane(plane_detail::pair_fwd<N, true>, G::smem, N, G::NT, a, batch, st);
-    return plane_detail::launch_plane(plane_detail::inv_accum<N>, G::smem, N, G::NT, a, batch, st);
+    if constexpr (N % 16 != 0) {
+        return cudaErrorInvalidValue;  // transposed planes: n % 16 == 0 only
+    } else {
+        if (which == 0)
+            return plane_detail::launch_plane(plane_detail::pair_fwd<N, false>, G::smem, N, G::NT, a, batch, st);
+        return plane_detail::launch_plane(plane_detail::inv_accum<N>, G::smem, N, G::NT, a, batch, st);
+    }
 }
 
 }  // namespace ace

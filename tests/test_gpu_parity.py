@@ -398,3 +398,25 @@ def test_hfx_exact_every_variant(variant):
     out = host(ace.hfx_apply_exact(plan, dev(s["psi"], plan), s["alpha"], dev(trials, plan)))
     assert rel(out, ref) <= TOL["mixed"]["W"]
     plan.close()
+
+
+@pytest.mark.parametrize("grid", [60, 90, 108])
+def test_hybrid_variant_on_cubes_without_transposed_planes(grid):
+    """Pair variant 4 (plane-kernel forward pass into the tile layout, no
+    slot swizzle when n % 16 != 0) on cubes the transposed passes do not
+    cover: E_x, W_G and K psi against the oracle."""
+    cell = gen.cubic_cell(12.0)
+    ecut = 30.0
+    psi = gen.random_orbitals(cell, ecut, 5, seed=grid)
+    s = dict(cell=cell, grid=(grid,) * 3, ecut=ecut, alpha=0.25, psi=psi, n_atom=3 * 5 / 4)
+    ref = oracle.ace_build(psi, cell, s["grid"], ecut, 0.25)
+    plan = ace.Plan(s["grid"], cell, ecut, 5, "mixed", pair_variant=4)
+    assert plan.config()["pair_variant"] == 4
+    xi, E = ace.ace_build(plan, dev(psi, plan), 0.25)
+    W, _ = ace.ace_last_intermediates(plan, 5)
+    assert abs(E - ref["E_x"]) / s["n_atom"] <= TOL["mixed"]["E"]
+    assert rel(host(W), ref["W_G"]) <= TOL["mixed"]["W"]
+    tr = gen.random_trials(cell, ecut, 3, seed=1)
+    assert rel(host(ace.ace_apply(plan, xi, dev(tr, plan))), oracle.ace_apply(ref["xi"], tr, ref["miller"])) \
+        <= TOL["mixed"]["K"]
+    plan.close()
