@@ -292,9 +292,8 @@ def run_ours(args):
     kcfg = plan.config()
     variant, streams = kcfg["pair_variant"], kcfg["pair_streams"]
     vname = {1: "tile passes", 2: "transposed-plane passes", 3: "persistent pipeline kernel",
-             4: "plane-kernel forward pass, tile passes after it",
-             5: "tile passes, each accumulation pass sharing a launch with the next pair-product pass"}[variant]
-    group = 32 if (variant == 5 or (variant != 3 and streams == 2)) else 64  # transforms per launch
+             4: "plane-kernel forward pass, tile passes after it"}[variant]
+    group = 32 if (variant != 3 and streams == 2) else 64  # transforms per launch (algorithmic count)
     pbg, _ = pass_bytes(n, N, batch=group)
     pipe_bytes = sum(pbg.values())  # per build
     if world > 1:  # this rank's shard of the pairs: its share of the transforms
@@ -310,14 +309,14 @@ def run_ours(args):
     per_pass = None
     if world == 1:
         ps = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, "mixed", pair_streams=1,
-                      pair_variant=variant if variant not in (3, 5) else 1)
+                      pair_variant=variant if variant != 3 else 1)
         xs = torch.empty_like(psi)
         _, _, st1 = timed_steps(ps, psi, tr, xs, K, 2, 1, with_timing=True)
         ps.close()
         pb64, nl64 = pass_bytes(n, N, batch=64)
         per_pass = {}
         per_pass["variant"] = {1: "tile passes", 2: "transposed-plane passes", 3: "tile passes",
-                               4: "hybrid", 5: "tile passes"}[variant]
+                               4: "hybrid"}[variant]
         for k in ("pair_fwd", "pair_coulomb", "pair_inv"):
             ms = st1[k + "_ms"] / 2
             per_pass[k] = {"ms_per_build": ms, "launches_per_build": nl64,
@@ -325,14 +324,13 @@ def run_ours(args):
                            "achieved_gbs": pb64[k] / (ms / 1e3) / 1e9 if ms > 0 else 0.0,
                            "frac": (pb64[k] / (ms / 1e3) / 1e9) / hbm if ms > 0 else 0.0,
                            "traffic_per_launch": MEASURED_TRAFFIC_PER_LAUNCH[fwd_key if k == "pair_fwd" else k]
-                           if variant in (1, 3, 4, 5) else None}
+                           if variant in (1, 3, 4) else None}
     layout = ("one launch for all transforms" if variant == 3 else
-              "32-transform batches on one stream" if variant == 5 else
               "32-transform sub-batches on 2 streams" if streams == 2 else "64-transform launches on one stream")
     roofline = {"bound": "hbm",
                 "kernel": f"pair pipeline: P1 + P2 + P3 ({vname}), {layout}",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-                "traffic": traffic_step if world == 1 and variant in (1, 4, 5) else None,
+                "traffic": traffic_step if world == 1 and variant in (1, 4) else None,
                 "traffic_unit": "bytes per build (sum of the three passes' DRAM bytes from the ncu "
                 "captures, scaled from 64-transform launches)",
                 "algorithmic_bytes_per_build": pipe_bytes, "pair_wall_ms_per_build": pair_wall,

@@ -165,13 +165,13 @@ class Plan:
 
     def config(self):
         """dict(pair_variant, pair_streams, tune_ms) of the pair-pass kernels
-        (1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid, 5 paired launches)."""
+        (1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid)."""
         v, st = ctypes.c_int(0), ctypes.c_int(0)
-        tm = (ctypes.c_float * 6)()
+        tm = (ctypes.c_float * 5)()
         _check(load().ace_plan_config(self.handle, ctypes.byref(v), ctypes.byref(st), tm))
         return {"pair_variant": v.value, "pair_streams": st.value,
                 "tune_ms": {k: round(float(x), 3) for k, x in
-                            zip(("tile_1_stream", "tile_2_streams", "planes", "pipeline", "hybrid", "duo"), tm)
+                            zip(("tile_1_stream", "tile_2_streams", "planes", "pipeline", "hybrid"), tm)
                             if x > 0}}
 
     def _vec(self, t, name):
@@ -186,8 +186,7 @@ def ace_plan_create(grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0
     """kernels: 0 fastest available, 1 CUDA-core Gram products, 2 also generic FFT passes;
     pair_streams: 0 automatic, 1 every pair pass in order on the call's stream;
     pair_variant: 0 automatic (timed at creation), 1 tile passes, 2 transposed planes,
-    3 persistent pipeline, 4 hybrid (plane-kernel forward pass, tile passes after it),
-    5 tile passes with each batch's accumulation and the next batch's pair product in one launch."""
+    3 persistent pipeline, 4 hybrid (plane-kernel forward pass, tile passes after it)."""
     return Plan(grid, cell, ecut, n_occ_max, precision, pair_batch, kernels, pair_streams, pair_variant)
 
 

@@ -108,8 +108,7 @@ struct ace_plan {
     float* d_kern_t = nullptr; // the same for transposed planes (n % 16 == 0 cubes)
     int variant = 1;           // pair passes: 1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid
     bool hybrid = false;       // variant 4: plane-kernel P1 in the tile layout, then the tile P2 / P3
-    bool duo = false;          // variant 5: tile passes, P3 of a batch and P1 of the next in one launch
-    float tune_ms[6] = {0, 0, 0, 0, 0, 0};  // autotune: tile x1 stream, tile x2, planes x2, pipeline, hybrid x2, duo
+    float tune_ms[5] = {0, 0, 0, 0, 0};  // autotune: tile x1 stream, tile x2, planes x2, pipeline, hybrid x2
     bool tplane = false;       // pair passes with transposed spectrum planes (plane.cuh; needs zline)
     int pair_tile = 0;         // pairs ordered in pair_tile x pair_tile orbital blocks (0: row by row; env ACE_PAIR_TILE)
     int pair_streams = 2;      // concurrent streams of pair sub-batches
@@ -454,37 +453,6 @@ int run_pairs(ace_plan* P, const R* fl, const R* fr, R* accl, R* accr, int symme
         P->pair_transforms += ntrans;
         mark(P, PH_PAIRWALL, st);
         ACE_CKL(pipeline_pair_launch(P->n[0], a, pa, st));
-        return ACE_OK;
-    }
-    if (P->duo && ntrans > 0) {
-        // one stream; the accumulation pass of batch k and the pair-product
-        // pass of batch k + 1 share a launch (alternating spectrum halves)
-        const int b = std::max(1, P->batch / 2);
-        const int K = (ntrans + b - 1) / b;
-        auto args_of = [&](int k) {
-            PassArgs ak = a;
-            ak.t0 = k * b;
-            ak.src = ak.dst = (cx<R>*)P->d_spec + (size_t)(k % 2) * b * P->N;
-            return ak;
-        };
-        auto cnt = [&](int k) { return std::min(b, ntrans - k * b); };
-        P->pair_transforms += ntrans;
-        mark(P, PH_PAIRWALL, st);
-        PassArgs a1 = args_of(0);
-        ACE_CKL(launch_pass<R>(a1, P->s_xy, PRO_PAIR, EPI_STORE, MID_NONE, -1, cnt(0), st));
-        for (int k = 0; k < K; ++k) {
-            PassArgs ak = args_of(k);
-            if (P->zline)
-                ACE_CKL(zline_coulomb_launch(P->n[0], ak, cnt(k), st));
-            else
-                ACE_CKL(launch_pass<R>(ak, P->s_z, PRO_LOAD, EPI_STORE, MID_COULOMB, -1, cnt(k), st));
-            if (k + 1 < K) {
-                PassArgs an = args_of(k + 1);
-                ACE_CKL(cube_duo_launch(P->n[0], ak, an, P->s_xy, cnt(k), cnt(k + 1), st));
-            } else {
-                ACE_CKL(launch_pass<R>(ak, P->s_xy, PRO_LOAD, EPI_ACCUM, MID_NONE, +1, cnt(k), st));
-            }
-        }
         return ACE_OK;
     }
     const int S = std::min(P->pair_streams, P->batch);
@@ -877,7 +845,6 @@ void set_variant(ace_plan* P, int v, int streams) {
     P->tplane = v == 2 || v == 3;
     P->fused = v == 3;
     P->hybrid = v == 4;
-    P->duo = v == 5;
     P->pair_streams = streams;
 }
 
@@ -891,13 +858,13 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     const int fixed_streams = opts && opts->pair_streams > 0 ? opts->pair_streams : 0;
     const bool t_ok = sizeof(R) == 4 && P->zline && P->d_kern_t != nullptr;
     const bool h_ok = sizeof(R) == 4 && P->zline;  // every compile-time cube
-    if (req < 0 || req > 5) return fail(ACE_ERR_INVALID_ARG, "pair_variant must be 0 (automatic) or 1 .. 5");
+    if (req < 0 || req > 4) return fail(ACE_ERR_INVALID_ARG, "pair_variant must be 0 (automatic), 1, 2, 3 or 4");
     if ((req == 2 || req == 3) && !t_ok)
         return fail(ACE_ERR_INVALID_ARG,
                     "pair_variant 2 and 3 need a single-precision n^3 plan with n in {32, 80, 96, 160}");
-    if ((req == 4 || req == 5) && !h_ok)
-        return fail(ACE_ERR_INVALID_ARG, "pair_variant 4 and 5 need a single-precision n^3 plan with n in "
-                                         "{32, 60, 80, 90, 96, 100, 108, 120, 160}");
+    if (req == 4 && !h_ok)
+        return fail(ACE_ERR_INVALID_ARG,
+                    "pair_variant 4 needs a single-precision n^3 plan with n in {32, 60, 80, 90, 96, 100, 108, 120, 160}");
     if (req > 0) {
         set_variant(P, req, fixed_streams ? fixed_streams : 2);
         return ACE_OK;
@@ -912,10 +879,7 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
         cand.push_back({2, fixed_streams ? fixed_streams : 2, 2});
         cand.push_back({3, 1, 3});
     }
-    if (h_ok) {
-        cand.push_back({4, fixed_streams ? fixed_streams : 2, 4});
-        cand.push_back({5, 1, 5});
-    }
+    if (h_ok) cand.push_back({4, fixed_streams ? fixed_streams : 2, 4});
     if (sizeof(R) != 4 || cand.size() == 1) {  // double plans: no timing, the two-stream tile passes
         set_variant(P, 1, fixed_streams ? fixed_streams : 2);
         return ACE_OK;
@@ -1407,9 +1371,9 @@ int ace_check_timeout_path(ace_plan* plan, int limit_ms, void* stream) {
 int ace_plan_config(const ace_plan* plan, int* pair_variant, int* pair_streams, float* tune_ms) {
     if (!plan) return fail(ACE_ERR_INVALID_ARG, "null argument");
     if (pair_variant) *pair_variant = plan->variant;
-    if (pair_streams) *pair_streams = (plan->variant == 3 || plan->variant == 5) ? 1 : plan->pair_streams;
+    if (pair_streams) *pair_streams = plan->variant == 3 ? 1 : plan->pair_streams;
     if (tune_ms)
-        for (int i = 0; i < 6; ++i) tune_ms[i] = plan->tune_ms[i];
+        for (int i = 0; i < 5; ++i) tune_ms[i] = plan->tune_ms[i];
     return ACE_OK;
 }
 

@@ -21,11 +21,5 @@ template cudaError_t tplane_launch<80>(int, const PassArgs&, int, cudaStream_t);
 template cudaError_t pipeline_launch<32>(const PassArgs&, const PipeArgs&, cudaStream_t);
 template cudaError_t pipeline_launch<80>(const PassArgs&, const PipeArgs&, cudaStream_t);
 template cudaError_t tplane_launch<60>(int, const PassArgs&, int, cudaStream_t);
-template cudaError_t pass_detail::duo_cube<32>(const PassArgs&, const PassArgs&, const PassShape&, int, int,
-                                                 cudaStream_t);
-template cudaError_t pass_detail::duo_cube<60>(const PassArgs&, const PassArgs&, const PassShape&, int, int,
-                                                 cudaStream_t);
-template cudaError_t pass_detail::duo_cube<80>(const PassArgs&, const PassArgs&, const PassShape&, int, int,
-                                                 cudaStream_t);
 
 }  // namespace ace

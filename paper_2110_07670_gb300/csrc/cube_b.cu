@@ -20,11 +20,5 @@ template cudaError_t tplane_launch<96>(int, const PassArgs&, int, cudaStream_t);
 template cudaError_t pipeline_launch<96>(const PassArgs&, const PipeArgs&, cudaStream_t);
 template cudaError_t tplane_launch<90>(int, const PassArgs&, int, cudaStream_t);
 template cudaError_t tplane_launch<100>(int, const PassArgs&, int, cudaStream_t);
-template cudaError_t pass_detail::duo_cube<90>(const PassArgs&, const PassArgs&, const PassShape&, int, int,
-                                                 cudaStream_t);
-template cudaError_t pass_detail::duo_cube<96>(const PassArgs&, const PassArgs&, const PassShape&, int, int,
-                                                 cudaStream_t);
-template cudaError_t pass_detail::duo_cube<100>(const PassArgs&, const PassArgs&, const PassShape&, int, int,
-                                                 cudaStream_t);
 
 }  // namespace ace

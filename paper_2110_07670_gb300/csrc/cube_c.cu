@@ -20,11 +20,5 @@ template cudaError_t tplane_launch<160>(int, const PassArgs&, int, cudaStream_t)
 template cudaError_t pipeline_launch<160>(const PassArgs&, const PipeArgs&, cudaStream_t);
 template cudaError_t tplane_launch<108>(int, const PassArgs&, int, cudaStream_t);
 template cudaError_t tplane_launch<120>(int, const PassArgs&, int, cudaStream_t);
-template cudaError_t pass_detail::duo_cube<108>(const PassArgs&, const PassArgs&, const PassShape&, int, int,
-                                                 cudaStream_t);
-template cudaError_t pass_detail::duo_cube<120>(const PassArgs&, const PassArgs&, const PassShape&, int, int,
-                                                 cudaStream_t);
-template cudaError_t pass_detail::duo_cube<160>(const PassArgs&, const PassArgs&, const PassShape&, int, int,
-                                                 cudaStream_t);
 
 }  // namespace ace

@@ -93,39 +93,6 @@ cudaError_t pipeline_pair_launch(int n, const PassArgs& a, const PipeArgs& p, cu
     }
 }
 
-namespace pass_detail {
-#define ACE_DUO_DECL(N)                                                                                      \
-    extern template cudaError_t duo_cube<N>(const PassArgs&, const PassArgs&, const PassShape&, int, int,   \
-                                            cudaStream_t);
-ACE_DUO_DECL(32)
-ACE_DUO_DECL(60)
-ACE_DUO_DECL(80)
-ACE_DUO_DECL(90)
-ACE_DUO_DECL(96)
-ACE_DUO_DECL(100)
-ACE_DUO_DECL(108)
-ACE_DUO_DECL(120)
-ACE_DUO_DECL(160)
-#undef ACE_DUO_DECL
-}  // namespace pass_detail
-
-cudaError_t cube_duo_launch(int n, const PassArgs& a3, const PassArgs& a1, const PassShape& s, int n3, int n1,
-                            cudaStream_t st) {
-    using namespace pass_detail;
-    switch (n) {
-        case 32: return duo_cube<32>(a3, a1, s, n3, n1, st);
-        case 60: return duo_cube<60>(a3, a1, s, n3, n1, st);
-        case 80: return duo_cube<80>(a3, a1, s, n3, n1, st);
-        case 90: return duo_cube<90>(a3, a1, s, n3, n1, st);
-        case 96: return duo_cube<96>(a3, a1, s, n3, n1, st);
-        case 100: return duo_cube<100>(a3, a1, s, n3, n1, st);
-        case 108: return duo_cube<108>(a3, a1, s, n3, n1, st);
-        case 120: return duo_cube<120>(a3, a1, s, n3, n1, st);
-        case 160: return duo_cube<160>(a3, a1, s, n3, n1, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 cudaError_t cube_pass_launch(int n, const PassArgs& a, const PassShape& s, int pro, int epi, int mid, int sgn,
                              int batch, cudaStream_t st) {
     using namespace pass_detail;

@@ -107,10 +107,6 @@ constexpr int zline_group(int n) {
     return 0;
 }
 cudaError_t zline_coulomb_launch(int n, const PassArgs& a, int batch, cudaStream_t st);
-// The accumulation pass of one batch and the pair-product pass of the next in
-// one launch (compile-time plane kernels; a3 over n3, a1 over n1 transforms).
-cudaError_t cube_duo_launch(int n, const PassArgs& a3, const PassArgs& a1, const PassShape& s, int n3, int n1,
-                            cudaStream_t st);
 // plane passes with transposed spectrum planes (plane.cuh), N^3 boxes with
 // N % 16 == 0: which = 0 pair product + forward, 1 inverse + exchange accumulation
 constexpr bool tplane_supported(int n) { return n % 16 == 0; }

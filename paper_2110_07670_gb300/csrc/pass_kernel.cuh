@@ -257,9 +257,8 @@ struct CubeShape {
     }
 };
 
-// One tile (tile_id of ntiles) of transform t (of nbatch in the launch).
 template <typename Shape, typename R, int PRO, int EPI, int MID, int SGN>
-__device__ __forceinline__ void tile_pass_body(const PassArgs& a, int tile_id, int t, int ntiles, int nbatch) {
+__global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pass(PassArgs a) {
     const Shape S(a);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
@@ -273,7 +272,9 @@ __device__ __forceinline__ void tile_pass_body(const PassArgs& a, int tile_id, i
     // (gt[3 j + c] axis 0, then axis 1, then axis 2; positions hold digit-reversed frequencies)
     R* gt = reinterpret_cast<R*>(twz + ((S.axes & 4) ? S.n0 : 0));
 
+    const int t = blockIdx.y;
     const int tiles_x = S.n2 / S.tx, tiles_y = S.n1 / S.ty;
+    const int tile_id = blockIdx.x;
     const int bx = tile_id % tiles_x, by = (tile_id / tiles_x) % tiles_y, bz = tile_id / (tiles_x * tiles_y);
     const int z0 = bz * S.tz, y0 = by * S.ty, x0 = bx * S.tx;
     const long long N = (long long)S.n0 * S.n1 * S.n2;
@@ -334,7 +335,7 @@ __device__ __forceinline__ void tile_pass_body(const PassArgs& a, int tile_id, i
     if (threadIdx.x >= 32 && threadIdx.x < 64) {
         const int lane = threadIdx.x - 32;
         const int tn = t + a.lookahead;
-        const bool ahead = a.lookahead > 0 && tn < nbatch;
+        const bool ahead = a.lookahead > 0 && tn < (int)gridDim.y;
         if (S.tx == S.n2 && S.ty == S.n1 && lane == 0) {
             const long long off = (long long)z0 * S.n1 * S.n2;
             const uint32_t bytes = (uint32_t)((long long)S.tz * S.n1 * S.n2 * sizeof(R));
@@ -628,41 +629,13 @@ __device__ __forceinline__ void tile_pass_body(const PassArgs& a, int tile_id, i
                 s1 += red[2 * w];
                 s2 += red[2 * w + 1];
             }
-            double* dst = a.e_part + ((long long)(a.t0 + t) * ntiles + tile_id) * 2;
+            double* dst = a.e_part + ((long long)(a.t0 + t) * gridDim.x + tile_id) * 2;
             dst[0] = s1;
             dst[1] = s2;
         }
     }
 }
 
-
-template <typename Shape, typename R, int PRO, int EPI, int MID, int SGN>
-__global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pass(PassArgs a) {
-    tile_pass_body<Shape, R, PRO, EPI, MID, SGN>(a, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
-}
-
-// Two independent passes of the same tile geometry in one launch, over
-// different transforms: blocks alternate between pass A (na transforms) and
-// pass B (nb transforms) while both have tiles left, so a bandwidth-bound
-// pass and a latency-bound pass share every SM.
-template <typename Shape, typename R, int PA, int EA, int SA, int PB, int EB, int SB>
-__global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks)
-    tile_pass_duo(PassArgs a, PassArgs b, int ntiles, int na, int nb) {
-    const int ca = ntiles * na, cb = ntiles * nb, m = ca < cb ? ca : cb;
-    const int blk = blockIdx.x;
-    int role, i;
-    if (blk < 2 * m) {
-        role = blk & 1;
-        i = blk >> 1;
-    } else {
-        role = ca > cb ? 0 : 1;
-        i = m + (blk - 2 * m);
-    }
-    if (role == 0)
-        tile_pass_body<Shape, R, PA, EA, MID_NONE, SA>(a, i % ntiles, i / ntiles, ntiles, na);
-    else
-        tile_pass_body<Shape, R, PB, EB, MID_NONE, SB>(b, i % ntiles, i / ntiles, ntiles, nb);
-}
 
 template <typename Shape, typename R, int PRO, int EPI, int MID, int SGN>
 cudaError_t launch_one(const PassArgs& a, const PassShape& s, int batch, cudaStream_t st) {
@@ -694,20 +667,6 @@ cudaError_t dispatch(const PassArgs& a, const PassShape& s, int pro, int epi, in
     if (pro == PRO_PACK2 && epi == EPI_STORE && sgn < 0)
         return launch_one<Shape, R, PRO_PACK2, EPI_STORE, MID_NONE, -1>(a, s, batch, st);
     return cudaErrorInvalidValue;
-}
-
-// The accumulation pass of one batch (a3, n3 transforms) and the pair-product
-// pass of the next (a1, n1 transforms) in one launch of the plane geometry.
-template <int N>
-cudaError_t duo_cube(const PassArgs& a3, const PassArgs& a1, const PassShape& s, int n3, int n1, cudaStream_t st) {
-    using XY = CubeShape<N, 1, N, N, cube_xy_threads(N)>;
-    auto k = tile_pass_duo<XY, float, PRO_LOAD, EPI_ACCUM, +1, PRO_PAIR, EPI_STORE, -1>;
-    if (s.smem > 48 * 1024 && !stream_capturing(st)) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
-        if (e != cudaSuccess) return e;
-    }
-    k<<<N * (n3 + n1), s.threads, s.smem, st>>>(a3, a1, N, n3, n1);
-    return cudaGetLastError();
 }
 
 // Cube kernels: the plane geometry carries the pair/accumulate/split/pack

@@ -223,7 +223,7 @@ def test_split_build_over_shards_matches_oracle(prec, world):
         plan.close()
 
 
-@pytest.mark.parametrize("variant,streams", [(1, 1), (1, 2), (2, 1), (2, 2), (3, 0), (4, 1), (4, 2), (5, 0)])
+@pytest.mark.parametrize("variant,streams", [(1, 1), (1, 2), (2, 1), (2, 2), (3, 0), (4, 1), (4, 2)])
 def test_pair_variants_match_oracle(variant, streams):
     """Every pair-pass variant (tile passes, transposed-plane passes, the
     persistent pipeline), on one and two streams, all pairs and a screened
@@ -258,13 +258,13 @@ def test_automatic_variant_choice_and_rejections():
     plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "mixed")  # 32^3: all variants apply, timed
     cfg = plan.config()
     assert cfg["pair_variant"] in (1, 2, 3) and cfg["pair_streams"] in (1, 2)
-    assert set(cfg["tune_ms"]) == {"tile_1_stream", "tile_2_streams", "planes", "pipeline", "hybrid", "duo"}
+    assert set(cfg["tune_ms"]) == {"tile_1_stream", "tile_2_streams", "planes", "pipeline", "hybrid"}
     plan.close()
     p64 = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "fp64")
     assert p64.config()["pair_variant"] == 1 and p64.config()["tune_ms"] == {}
     p64.close()
     small = small_system()
-    for v in (2, 3, 4, 5):  # 16^3 has no compile-time kernels, double has none either
+    for v in (2, 3, 4):  # 16^3 has no compile-time kernels, double has none either
         with pytest.raises(ace.AceError):
             ace.Plan(small["grid"], small["cell"], small["ecut"], 5, "mixed", pair_variant=v)
         with pytest.raises(ace.AceError):
@@ -385,7 +385,7 @@ def test_bounded_wait_timeout_path_and_recovery():
     plan.close()
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_hfx_exact_every_variant(variant):
     """The exact exchange on trial vectors (one-sided accumulation: trials x
     occupied pairs) through every pair-pass variant on the 32^3 cube, against
