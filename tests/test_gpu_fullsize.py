@@ -44,15 +44,22 @@ def _lib():
     ace.load()
 
 
-def check_full(cfg, rows, pairs=None, n_trials=8):
+_ORACLE_ROWS = {}
+
+
+def check_full(cfg, rows, pairs=None, n_trials=8, pair_variant=0):
     n = len(cfg["psi"])
-    plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, "mixed")
+    plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, "mixed", pair_variant=pair_variant)
     xi, E = ace.ace_build(plan, dev(cfg["psi"], plan), cfg["alpha"], pairs=pairs)
     W, M = ace.ace_last_intermediates(plan, n)
     Wh = host(W)
     m = oracle.half_sphere(cfg["cell"], cfg["ecut"])
     # sampled rows of W against the oracle
-    Wref = oracle.exchange_rows(cfg["psi"], cfg["cell"], cfg["grid"], cfg["ecut"], cfg["alpha"], rows, pairs=pairs)
+    key = (cfg["name"], tuple(rows), pairs is None)
+    if key not in _ORACLE_ROWS:  # the oracle rows once per workload, for every variant
+        _ORACLE_ROWS[key] = oracle.exchange_rows(cfg["psi"], cfg["cell"], cfg["grid"], cfg["ecut"], cfg["alpha"],
+                                                 rows, pairs=pairs)
+    Wref = _ORACLE_ROWS[key]
     assert rel(Wh[rows], Wref) <= 2e-6
     # their row energies
     e_ref = np.array([oracle.gamma_gram(cfg["psi"][i], Wref[k], m)[0, 0] for k, i in enumerate(rows)])
@@ -74,9 +81,17 @@ def check_full(cfg, rows, pairs=None, n_trials=8):
     return E
 
 
-def test_water32_full_size():
-    """128 orbitals, 96^3, the bench workload."""
-    check_full(gen.config_water32(), rows=[0, 77, 127])
+_WATER32 = None
+
+
+@pytest.mark.parametrize("pair_variant", [0, 1, 2, 3, 4])
+def test_water32_full_size(pair_variant):
+    """128 orbitals, 96^3, the bench workload (4128 transforms: many
+    batches), with the autotuned choice and every pair-pass variant."""
+    global _WATER32
+    if _WATER32 is None:
+        _WATER32 = gen.config_water32()
+    check_full(_WATER32, rows=[0, 77, 127], pair_variant=pair_variant)
 
 
 def test_water64_full_size():

@@ -420,3 +420,18 @@ def test_hybrid_variant_on_cubes_without_transposed_planes(grid):
     assert rel(host(ace.ace_apply(plan, xi, dev(tr, plan))), oracle.ace_apply(ref["xi"], tr, ref["miller"])) \
         <= TOL["mixed"]["K"]
     plan.close()
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+def test_pair_variants_odd_pair_count(variant):
+    """Six orbitals on the 32^3 cube: 21 pairs, so the last packed transform
+    carries one pair; every variant against the oracle."""
+    s = gen.config_small()
+    psi = s["psi"][:6]
+    ref = oracle.ace_build(psi, s["cell"], s["grid"], s["ecut"], s["alpha"])
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], 6, "mixed", pair_variant=variant)
+    xi, E = ace.ace_build(plan, dev(psi, plan), s["alpha"])
+    W, _ = ace.ace_last_intermediates(plan, 6)
+    assert abs(E - ref["E_x"]) / (3 * 6 / 4) <= TOL["mixed"]["E"]
+    assert rel(host(W), ref["W_G"]) <= TOL["mixed"]["W"]
+    plan.close()
