@@ -60,6 +60,8 @@ def _load():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int if name != "orc_fft3d" else None
+        lib.orc_set_coulomb_cutoff.argtypes = [f64]
+        lib.orc_set_coulomb_cutoff.restype = None
         _lib = lib
     return _lib
 
@@ -108,6 +110,30 @@ def _csr(pairs):
         return None, None
     rp, col = pairs
     return np.ascontiguousarray(rp, dtype=np.int32), np.ascontiguousarray(col, dtype=np.int32)
+
+
+class coulomb_cutoff:
+    """Context in which every oracle call uses the Coulomb interaction cut off
+    at r = rc (bohr): K(G) = 4 pi (1 - cos(|G| rc)) / |G|^2, K(0) = 2 pi rc^2
+    (Spencer & Alavi, Phys. Rev. B 77, 193110 (2008)); rc = 0 restores 4 pi / |G|^2
+    with G = 0 dropped."""
+
+    def __init__(self, rc):
+        self.rc = float(rc)
+
+    def __enter__(self):
+        _load().orc_set_coulomb_cutoff(ctypes.c_double(self.rc))
+        return self
+
+    def __exit__(self, *exc):
+        _load().orc_set_coulomb_cutoff(ctypes.c_double(0.0))
+        return False
+
+
+def sphere_radius(cell):
+    """(3 Omega / 4 pi)^(1/3): the radius of the sphere of the cell's volume,
+    the usual cutoff of the truncated interaction."""
+    return float((3.0 * abs(np.linalg.det(np.asarray(cell, dtype=np.float64).reshape(3, 3))) / (4.0 * np.pi)) ** (1.0 / 3.0))
 
 
 def exchange(psi, cell, grid, ecut, alpha, pairs=None, nthreads=0, times=False):

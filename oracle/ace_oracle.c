@@ -25,6 +25,11 @@
  * no density-sphere mask; the ACE construction (not printed in the paper) is
  * the standard Cholesky form above.
  *
+ * Alternative G=0 treatment (orc_set_coulomb_cutoff): the Coulomb interaction
+ * cut off at r = R_c (Spencer & Alavi, Phys. Rev. B 77, 193110 (2008)), whose
+ * Fourier transform is K(G) = 4 pi (1 - cos(|G| R_c)) / |G|^2 and
+ * K(0) = 2 pi R_c^2.
+ *
  * Parity of every function here is pinned by tests against things other than
  * this file: a brute-force DFT, closed-form Coulomb energies (plane waves and
  * Gaussians), Table 1's plane-wave counts, and invariants of V_X.
@@ -204,12 +209,21 @@ static long box_index(const grid_t *g, int h, int k, int l)
     return ((long)wrap(h, g->n[0]) * g->n[1] + wrap(k, g->n[1])) * g->n[2] + wrap(l, g->n[2]);
 }
 
-/* Coulomb kernel 4 pi / |G|^2 for box entry (i0,i1,i2); G = 0 dropped. */
+/* Truncation radius of the Coulomb interaction; 0: the bare 1/r with G = 0 dropped. */
+static double coulomb_rc = 0.0;
+
+void orc_set_coulomb_cutoff(double rc) { coulomb_rc = rc > 0.0 ? rc : 0.0; }
+
+/* Coulomb kernel for box entry (i0,i1,i2): 4 pi / |G|^2 with G = 0 dropped,
+ * or, with a cutoff R_c, the transform of 1/r restricted to r < R_c. */
 static double coulomb(const grid_t *g, int i0, int i1, int i2)
 {
     double G[3];
     gvec(g->b, fold(i0, g->n[0]), fold(i1, g->n[1]), fold(i2, g->n[2]), G);
     double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+    if (coulomb_rc > 0.0)
+        return g2 == 0.0 ? 2.0 * M_PI * coulomb_rc * coulomb_rc
+                         : 4.0 * M_PI * (1.0 - cos(sqrt(g2) * coulomb_rc)) / g2;
     return g2 == 0.0 ? 0.0 : 4.0 * M_PI / g2;
 }
 

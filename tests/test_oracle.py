@@ -174,6 +174,89 @@ def test_gaussian_self_energy_madelung(sigma, L, n):
         assert abs(e - golden["gaussian_sigma1_L20"]) < 1e-11
 
 
+# ------------------------------------ truncated Coulomb (alternative G = 0)
+
+def _k_trunc(q2, rc):
+    """Transform of 1/r cut off at r = rc, written from the radial integral
+    4 pi int_0^rc sin(q r) / q dr (q > 0) and 4 pi int_0^rc r dr (q = 0)."""
+    if q2 == 0:
+        return 2 * np.pi * rc ** 2
+    q = np.sqrt(q2)
+    return 4 * np.pi / q * (1 - np.cos(q * rc)) / q
+
+
+@pytest.mark.parametrize("rc", [3.0, 6.2035049089940])
+def test_truncated_plane_wave_self_energy(rc):
+    """rho = (1 + cos 2G.r) / Omega: the G = 0 term K(0) / Omega and the 2G
+    harmonic K(2G) / (2 Omega)."""
+    L, ecut, grid = 10.0, 30.0, (18, 18, 18)
+    cell = gen.cubic_cell(L)
+    m = oracle.half_sphere(cell, ecut)
+    c = _cos_orbital(m, (1, 2, 0))
+    with oracle.coulomb_cutoff(rc):
+        e = oracle.pair_energy(c, c, cell, grid, ecut)
+    G2 = (2 * np.pi / L) ** 2 * 5
+    expect = _k_trunc(0.0, rc) / L ** 3 + _k_trunc(4 * G2, rc) / (2 * L ** 3)
+    assert abs(e - expect) < 5e-14 * abs(expect)
+    # the context restores the dropped G = 0 term
+    assert abs(oracle.pair_energy(c, c, cell, grid, ecut) - np.pi / (2 * L ** 3 * G2)) < 1e-15
+
+
+def test_truncated_plane_wave_pair_energy():
+    L, ecut, grid, rc = 10.0, 30.0, (18, 18, 18), 4.5
+    cell = gen.cubic_cell(L)
+    m = oracle.half_sphere(cell, ecut)
+    g1, g2 = np.array((1, 2, 0)), np.array((0, -1, 3))
+    ca, cb = _cos_orbital(m, g1), _cos_orbital(m, g2)
+    with oracle.coulomb_cutoff(rc):
+        e = oracle.pair_energy(ca, cb, cell, grid, ecut)
+    f = (2 * np.pi / L) ** 2
+    expect = (_k_trunc(f * ((g1 - g2) ** 2).sum(), rc) + _k_trunc(f * ((g1 + g2) ** 2).sum(), rc)) / (2 * L ** 3)
+    assert abs(e - expect) < 5e-14 * abs(expect)
+
+
+@pytest.mark.parametrize("sigma,L,n,rc", [(1.0, 20.0, 96, None), (0.8, 14.0, 64, 6.0)])
+def test_truncated_gaussian_self_energy(sigma, L, n, rc):
+    """A normalised Gaussian's density interacting through 1/r cut off at rc
+    (no periodic image reaches the sphere): its self-convolution is a Gaussian
+    of exponent 1 / (2 sigma^2), so e = sqrt(2/pi)/sigma (1 - exp(-rc^2 / (2 sigma^2)))
+    exactly, with no Madelung term."""
+    ecut = 80.0
+    cell = gen.cubic_cell(L)
+    if rc is None:
+        rc = oracle.sphere_radius(cell)
+        assert abs(rc - L * (3 / (4 * np.pi)) ** (1 / 3)) < 1e-12
+    m = oracle.half_sphere(cell, ecut)
+    c = gen.gaussian_sum_coefficients(cell, m, [np.array([3.0, 4.0, 5.0])], [sigma], [1.0])
+    with oracle.coulomb_cutoff(rc):
+        e = oracle.pair_energy(c, c, cell, (n, n, n), ecut)
+    expect = np.sqrt(2 / np.pi) / sigma * (1 - np.exp(-rc ** 2 / (2 * sigma ** 2)))
+    assert abs(e - expect) < 1e-10
+
+
+def test_truncated_exchange_invariants():
+    """With the cut-off interaction V_X stays Hermitian and negative, and the
+    ACE operator stays exact on span(Phi) with E_x = tr(M)."""
+    cell = gen.cubic_cell(7.0)
+    ecut, grid, alpha = 14.0, (16, 16, 16), 0.25
+    psi = gen.random_orbitals(cell, ecut, 5, seed=11)
+    trials = gen.random_trials(cell, ecut, 3, seed=12)
+    m = oracle.half_sphere(cell, ecut)
+    rc = oracle.sphere_radius(cell)
+    with oracle.coulomb_cutoff(rc):
+        V = oracle.vx_apply(psi, trials, cell, grid, ecut, alpha)
+        ref = oracle.ace_build(psi, cell, grid, ecut, alpha)
+        Kphi = oracle.ace_apply(ref["xi"], psi, m)
+    A = oracle.gamma_gram(trials, V, m)
+    assert np.abs(A - A.T).max() < 1e-13 * np.abs(A).max()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).max() < 1e-14
+    assert abs(ref["E_x"] - np.trace(ref["M"])) < 1e-13 * abs(ref["E_x"])
+    assert np.abs(Kphi - ref["W_G"]).max() < 1e-12 * np.abs(ref["W_G"]).max()
+    # the G = 0 term alone shifts every diagonal pair energy by K(0) / Omega
+    ref0 = oracle.ace_build(psi, cell, grid, ecut, alpha)
+    assert abs(ref["E_x"] - ref0["E_x"]) > 1e-6
+
+
 # ------------------------------------------------------------ invariants
 
 @pytest.fixture(scope="module")
