@@ -82,6 +82,14 @@ typedef struct {
                           0 = automatic: where several apply (and pair_streams is 0, both 1
                           and 2 streams) they are timed at plan creation on the plan's own
                           buffers and the fastest is kept (see ace_plan_config) */
+    double coulomb_rc; /* G = 0 treatment of the Poisson solve (Eq. 3): 0 = the bare
+                          4 pi / |G|^2 with the G = 0 term dropped (neutralising
+                          background); > 0 = the interaction 1/r cut off at r = coulomb_rc
+                          bohr (Spencer & Alavi, Phys. Rev. B 77, 193110 (2008)):
+                          4 pi (1 - cos(|G| R_c)) / |G|^2, and 2 pi R_c^2 at G = 0; the
+                          usual choice is R_c = (3 Omega / 4 pi)^(1/3).  Negative or
+                          non-finite: ACE_ERR_INVALID_ARG.  Applies to every build and to
+                          hfx_apply_exact of the plan. */
 } ace_opts;
 
 /*

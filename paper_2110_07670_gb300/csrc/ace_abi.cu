@@ -2,6 +2,7 @@
 // which the kernels run for the ACE build, the ACE apply and the exact
 // exchange apply (arXiv:2110.07670 Sections 2.1-2.2, Eq. 2-5).
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -106,6 +107,8 @@ struct ace_plan {
     bool zline = false;        // per-pencil Coulomb pass (zline.cuh) with the kernel table d_kern
     float* d_kern = nullptr;   // 4 pi / |G|^2 / N in the tile passes' spectrum layout (zline only)
     float* d_kern_t = nullptr; // the same for transposed planes (n % 16 == 0 cubes)
+    double coul_rc = 0;        // Coulomb cutoff radius (0: 4 pi / |G|^2 with G = 0 dropped)
+    void* d_kern_r = nullptr;  // cut-off kernel for the Coulomb stage of the tile passes, R[n0][n1][n2]
     int variant = 1;           // pair passes: 1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid
     bool hybrid = false;       // variant 4: plane-kernel P1 in the tile layout, then the tile P2 / P3
     float tune_ms[5] = {0, 0, 0, 0, 0};  // autotune: tile x1 stream, tile x2, planes x2, pipeline, hybrid x2
@@ -321,6 +324,8 @@ PassArgs base_args(const ace_plan* P) {
     a.err = P->d_err;
     a.lookahead = P->lookahead;
     a.kern = P->tplane ? P->d_kern_t : P->d_kern;
+    a.kern_inline = P->d_kern_r != nullptr;  // built only for plans without the per-pencil pass
+    if (a.kern_inline) a.kern = P->d_kern_r;
     for (int d = 0; d < 3; ++d) a.freq[d] = P->d_freq[d];
     return a;
 }
@@ -834,7 +839,7 @@ void free_plan(ace_plan* P) {
     if (P->fork_ev) cudaEventDestroy(P->fork_ev);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
                     P->d_WG, P->d_M, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
-                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_kern_t, P->d_pipe};
+                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_kern_t, P->d_kern_r, P->d_pipe};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -987,38 +992,58 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     ACE_TRY(setup_shapes<R>(P));
     // the compile-time plane kernels of N % 16 == 0 boxes keep x swizzled per row
     const bool swz = P->s_xy.cube && cube_swizzle(P->n[2]);
-    // per-pencil Coulomb pass: its kernel 4 pi / |G|^2 / N (Eq. 3, G = 0
-    // dropped) at every stored position of the spectrum, computed in double
+    // Coulomb tables K(G) / N (Eq. 3) at every stored position of the spectrum,
+    // computed in double: the per-pencil pass always reads one; the Coulomb
+    // stage of the tile passes reads one only for the cut-off interaction (for
+    // the bare 4 pi / |G|^2 it forms the factor from G itself).
+    if (opts) P->coul_rc = opts->coulomb_rc;
     P->zline = P->s_xy.cube && P->s_z.cube && zline_group(P->n[0]) > 0;
     if (const char* env = std::getenv("ACE_ZLINE")) P->zline = P->zline && std::atoi(env) != 0;
-    if (P->zline) {
+    const bool inline_tab = P->coul_rc > 0 && !P->zline;
+    if (P->zline || inline_tab) {
         const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
-        const bool with_t = tplane_supported(n0);
-        std::vector<float> kern((size_t)P->N), kern_t(with_t ? (size_t)P->N : 0);
+        const bool with_t = P->zline && tplane_supported(n0);
+        const bool swz_i = P->s_z.cube && cube_swizzle(n2);  // x slots of the tile passes' Coulomb stage
+        std::vector<float> kern(P->zline ? (size_t)P->N : 0), kern_t(with_t ? (size_t)P->N : 0);
+        std::vector<R> kern_r(inline_tab ? (size_t)P->N : 0);
         auto fold = [](int k, int n) { return k < n - n / 2 ? k : k - n; };
+        auto g2_at = [&](int z, int y, int xp) {
+            const int m[3] = {fold(frq[0][z], n0), fold(frq[1][y], n1), fold(frq[2][xp], n2)};
+            double q2 = 0;
+            for (int c = 0; c < 3; ++c) {
+                const double g = m[0] * P->b[c] + m[1] * P->b[3 + c] + m[2] * P->b[6 + c];
+                q2 += g * g;
+            }
+            return q2;
+        };
+        // 4 pi / |G|^2 with G = 0 dropped, or the transform of 1/r cut off at
+        // R_c: 4 pi (1 - cos(|G| R_c)) / |G|^2, and 2 pi R_c^2 at G = 0
+        const double rc = P->coul_rc;
+        auto k = [&](double q2) {
+            if (rc > 0) return (q2 > 0 ? 4 * M_PI * (1 - std::cos(std::sqrt(q2) * rc)) / q2 : 2 * M_PI * rc * rc) /
+                               (double)P->N;
+            return q2 > 0 ? 4 * M_PI / (q2 * (double)P->N) : 0.0;
+        };
         for (int z = 0; z < n0; ++z)
             for (int y = 0; y < n1; ++y)
                 for (int xs = 0; xs < n2; ++xs) {
-                    double g2[2];
-                    for (int v = 0; v < 2; ++v) {  // v = 0: swizzled slot xs of row y; 1: plain position xs
-                        const int xp = (v == 0 && swz) ? plane_swizzle(xs, y) : xs;
-                        const int m[3] = {fold(frq[0][z], n0), fold(frq[1][y], n1), fold(frq[2][xp], n2)};
-                        g2[v] = 0;
-                        for (int c = 0; c < 3; ++c) {
-                            const double g = m[0] * P->b[c] + m[1] * P->b[3 + c] + m[2] * P->b[6 + c];
-                            g2[v] += g * g;
-                        }
-                    }
-                    auto k = [&](double q2) { return q2 > 0 ? (float)(4 * M_PI / (q2 * (double)P->N)) : 0.0f; };
-                    kern[((size_t)z * n1 + y) * n2 + xs] = k(g2[0]);
-                    if (with_t) kern_t[((size_t)z * n2 + xs) * n1 + y] = k(g2[1]);  // plane stored [x][y]
+                    const size_t e = ((size_t)z * n1 + y) * n2 + xs;
+                    if (P->zline) kern[e] = (float)k(g2_at(z, y, swz ? plane_swizzle(xs, y) : xs));
+                    if (with_t) kern_t[((size_t)z * n2 + xs) * n1 + y] = (float)k(g2_at(z, y, xs));  // plane [x][y]
+                    if (inline_tab) kern_r[e] = (R)k(g2_at(z, y, swz_i ? plane_swizzle(xs, y) : xs));
                 }
         if (with_t) {
             ACE_TRY(dalloc((void**)&P->d_kern_t, kern_t.size() * sizeof(float)));
             ACE_CK(cudaMemcpy(P->d_kern_t, kern_t.data(), kern_t.size() * sizeof(float), cudaMemcpyHostToDevice));
         }
-        ACE_TRY(dalloc((void**)&P->d_kern, kern.size() * sizeof(float)));
-        ACE_CK(cudaMemcpy(P->d_kern, kern.data(), kern.size() * sizeof(float), cudaMemcpyHostToDevice));
+        if (P->zline) {
+            ACE_TRY(dalloc((void**)&P->d_kern, kern.size() * sizeof(float)));
+            ACE_CK(cudaMemcpy(P->d_kern, kern.data(), kern.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
+        if (inline_tab) {
+            ACE_TRY(dalloc(&P->d_kern_r, kern_r.size() * sizeof(R)));
+            ACE_CK(cudaMemcpy(P->d_kern_r, kern_r.data(), kern_r.size() * sizeof(R), cudaMemcpyHostToDevice));
+        }
     }
     std::vector<int> ip(P->npw), in(P->npw);
     for (int p = 0; p < P->npw; ++p) {
@@ -1078,6 +1103,8 @@ int ace_plan_create(ace_plan** plan, const int grid[3], const double cell[9], do
         return fail(ACE_ERR_INVALID_ARG, "ecut must be > 0, n_occ_max >= 1, precision ACE_FP64 or ACE_MIXED");
     for (int d = 0; d < 3; ++d)
         if (grid[d] < 1 || grid[d] > 4096) return fail(ACE_ERR_INVALID_ARG, "grid extent out of range");
+    if (opts && !(std::isfinite(opts->coulomb_rc) && opts->coulomb_rc >= 0))
+        return fail(ACE_ERR_INVALID_ARG, "coulomb_rc must be finite and >= 0");
     ace_plan* P = new ace_plan();
     cudaGetDevice(&P->dev);
     P->prec = precision;
@@ -1280,12 +1307,17 @@ int ace_build_batched(ace_system* sys, int n_sys, void* stream) {
 }
 
 namespace {
-const char kSaveMagic[8] = {'A', 'C', 'E', 'X', 'I', '0', '0', '1'};
+// Version 2 appends the Coulomb cutoff; version 1 files (no cutoff field)
+// were written with the bare kernel and load as coulomb_rc = 0.
+const char kSaveMagic[8] = {'A', 'C', 'E', 'X', 'I', '0', '0', '2'};
+const char kSaveMagicV1[8] = {'A', 'C', 'E', 'X', 'I', '0', '0', '1'};
 struct SaveHeader {
     char magic[8];
     int32_t precision, grid[3], n_occ, n_pw_half;
     double cell[9], ecut, alpha, E_x;
+    double coulomb_rc;
 };
+constexpr size_t kHeaderV1 = offsetof(SaveHeader, coulomb_rc);
 }  // namespace
 
 int ace_save(const char* path, const ace_plan* plan, const void* xi, int n_occ, double alpha, double E_x,
@@ -1308,6 +1340,7 @@ int ace_save(const char* path, const ace_plan* plan, const void* xi, int n_occ, 
     h.ecut = plan->ecut;
     h.alpha = alpha;
     h.E_x = E_x;
+    h.coulomb_rc = plan->coul_rc;
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(ACE_ERR_INVALID_ARG, std::string("ace_save: cannot open ") + path);
     const bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(buf.data(), 1, bytes, f) == bytes;
@@ -1320,16 +1353,23 @@ int ace_load(const char* path, const ace_plan* plan, void* xi, int* n_occ, doubl
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(ACE_ERR_INVALID_ARG, std::string("ace_load: cannot open ") + path);
     SaveHeader h;
-    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kSaveMagic, 8) != 0) {
+    std::memset(&h, 0, sizeof(h));
+    bool hdr = std::fread(&h, kHeaderV1, 1, f) == 1;
+    if (hdr && std::memcmp(h.magic, kSaveMagic, 8) == 0)
+        hdr = std::fread(&h.coulomb_rc, sizeof(h.coulomb_rc), 1, f) == 1;
+    else if (hdr)
+        hdr = std::memcmp(h.magic, kSaveMagicV1, 8) == 0;
+    if (!hdr) {
         std::fclose(f);
         return fail(ACE_ERR_INVALID_ARG, "ace_load: not an ACE vector file");
     }
-    bool same = h.precision == plan->prec && h.n_pw_half == plan->npw && h.ecut == plan->ecut;
+    bool same = h.precision == plan->prec && h.n_pw_half == plan->npw && h.ecut == plan->ecut &&
+                h.coulomb_rc == plan->coul_rc;
     for (int d = 0; d < 3; ++d) same = same && h.grid[d] == plan->n[d];
     for (int d = 0; d < 9; ++d) same = same && h.cell[d] == plan->cell[d];
     if (!same || h.n_occ < 1 || h.n_occ > plan->n_occ_max) {
         std::fclose(f);
-        return fail(ACE_ERR_INVALID_ARG, "ace_load: file was saved for another grid, cell, cutoff, precision or size");
+        return fail(ACE_ERR_INVALID_ARG, "ace_load: file was saved for another grid, cell, cutoff, Coulomb cutoff, precision or size");
     }
     const size_t bytes = (size_t)h.n_occ * plan->npw * 2 * plan->esz;
     std::vector<char> buf(bytes);

@@ -455,12 +455,20 @@ __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pa
             const R four_pi_s = R(4.0 * 3.14159265358979323846 * a.kscale);
             const R* g1 = gt + 3 * S.n0;
             const R* g2t = gt + 3 * (S.n0 + S.n1);
-            auto coulomb = [&](int e, const R* gyx, int ez) {
-                const R gx = gyx[0] + gt[3 * (z0 + ez)];
-                const R gy = gyx[1] + gt[3 * (z0 + ez) + 1];
-                const R gz = gyx[2] + gt[3 * (z0 + ez) + 2];
-                const R g2 = gx * gx + gy * gy + gz * gz;
-                const R kv = g2 > R(0) ? four_pi_s / g2 : R(0);
+            // the cut-off interaction reads its factor from the plan's table
+            const R* ktab = a.kern_inline ? reinterpret_cast<const R*>(a.kern) : nullptr;
+            const long long kz = (long long)S.n1 * S.n2;
+            auto coulomb = [&](int e, const R* gyx, int ez, long long kyx) {
+                R kv;
+                if (ktab) {
+                    kv = ktab[(z0 + ez) * kz + kyx];
+                } else {
+                    const R gx = gyx[0] + gt[3 * (z0 + ez)];
+                    const R gy = gyx[1] + gt[3 * (z0 + ez) + 1];
+                    const R gz = gyx[2] + gt[3 * (z0 + ez) + 2];
+                    const R g2 = gx * gx + gy * gy + gz * gz;
+                    kv = g2 > R(0) ? four_pi_s / g2 : R(0);
+                }
                 tile[e] = scale(tile[e], kv);
             };
             if (S.nt() % txy == 0) {
@@ -469,14 +477,15 @@ __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pa
                 const int xp = S.xpos(x0 + ex, y0 + ey);
                 const R gyx[3] = {g1[3 * (y0 + ey)] + g2t[3 * xp], g1[3 * (y0 + ey) + 1] + g2t[3 * xp + 1],
                                   g1[3 * (y0 + ey) + 2] + g2t[3 * xp + 2]};
-                for (int ez = threadIdx.x / txy; ez < S.tz; ez += S.nt() / txy) coulomb(ez * txy + l, gyx, ez);
+                const long long kyx = (long long)(y0 + ey) * S.n2 + x0 + ex;
+                for (int ez = threadIdx.x / txy; ez < S.tz; ez += S.nt() / txy) coulomb(ez * txy + l, gyx, ez, kyx);
             } else {
                 for (int e = threadIdx.x; e < tile_elems; e += S.nt()) {
                     const int ex = e % S.tx, ey = (e / S.tx) % S.ty, ez = e / txy;
                     const int xp = S.xpos(x0 + ex, y0 + ey);
                     const R gyx[3] = {g1[3 * (y0 + ey)] + g2t[3 * xp], g1[3 * (y0 + ey) + 1] + g2t[3 * xp + 1],
                                       g1[3 * (y0 + ey) + 2] + g2t[3 * xp + 2]};
-                    coulomb(e, gyx, ez);
+                    coulomb(e, gyx, ez, (long long)(y0 + ey) * S.n2 + x0 + ex);
                 }
             }
             __syncthreads();

@@ -435,3 +435,77 @@ def test_pair_variants_odd_pair_count(variant):
     assert abs(E - ref["E_x"]) / (3 * 6 / 4) <= TOL["mixed"]["E"]
     assert rel(host(W), ref["W_G"]) <= TOL["mixed"]["W"]
     plan.close()
+
+
+# ---------------------------------------- the Coulomb interaction cut off at R_c
+
+def _check_truncated(s, prec, rc, **plan_kw):
+    n = len(s["psi"])
+    with oracle.coulomb_cutoff(rc):
+        ref = oracle.ace_build(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, prec, coulomb_rc=rc, **plan_kw)
+    xi, E = ace.ace_build(plan, dev(s["psi"], plan), s["alpha"])
+    W, M = ace.ace_last_intermediates(plan, n)
+    tol = TOL[prec]
+    n_atom = 3 * n / 4
+    assert abs(E - ref["E_x"]) / n_atom <= tol["E"] * (1 if prec == "mixed" else abs(ref["E_x"]))
+    assert rel(host(W), ref["W_G"]) <= tol["W"]
+    tr = gen.random_trials(s["cell"], s["ecut"], 4, seed=98)
+    K = host(ace.ace_apply(plan, xi, dev(tr, plan)))
+    assert rel(K, oracle.ace_apply(ref["xi"], tr, ref["miller"])) <= tol["K"]
+    plan.close()
+    return E
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_truncated_coulomb_generic_passes(prec):
+    """16^3 box (runtime-size passes): the Coulomb stage reads the cut-off
+    kernel from the plan's table, in the plan's precision."""
+    s = small_system()
+    E = _check_truncated(s, prec, ace.sphere_radius(s["cell"]))
+    # a different cutoff gives a different answer (the table is used)
+    E2 = _check_truncated(s, prec, 2.0)
+    assert abs(E - E2) > 1e-4
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+def test_truncated_coulomb_every_variant(variant):
+    """32^3 cube, mixed precision: the per-pencil pass's tables (natural and
+    transposed planes) carry the cut-off kernel in every pair-pass variant."""
+    s = gen.config_small()
+    _check_truncated(s, "mixed", ace.sphere_radius(s["cell"]), pair_variant=variant)
+
+
+@pytest.mark.parametrize("prec,kernels", [("fp64", 0), ("mixed", 2)])
+def test_truncated_coulomb_cube_without_pencil_pass(prec, kernels):
+    s = gen.config_small()
+    _check_truncated(s, prec, ace.sphere_radius(s["cell"]), kernels=kernels)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_truncated_coulomb_hfx_exact(prec):
+    s = small_system()
+    rc = ace.sphere_radius(s["cell"])
+    with oracle.coulomb_cutoff(rc):
+        ref = oracle.vx_apply(s["psi"], s["trials"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], len(s["psi"]), prec, coulomb_rc=rc)
+    out = host(ace.hfx_apply_exact(plan, dev(s["psi"], plan), s["alpha"], dev(s["trials"], plan)))
+    assert rel(out, ref) <= TOL[prec]["W"]
+
+
+def test_truncated_coulomb_checkpoint_and_rejections(tmp_path):
+    s = gen.config_small()
+    rc = ace.sphere_radius(s["cell"])
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], 8, "mixed", coulomb_rc=rc)
+    xi, E = ace.ace_build(plan, dev(s["psi"], plan), s["alpha"])
+    path = str(tmp_path / "xi_rc.ace")
+    ace.ace_save(plan, path, xi, s["alpha"], E)
+    same = ace.Plan(s["grid"], s["cell"], s["ecut"], 8, "mixed", coulomb_rc=rc)
+    xi2, _, E2 = ace.ace_load(same, path)
+    assert torch.equal(xi, xi2) and E2 == E
+    bare = ace.Plan(s["grid"], s["cell"], s["ecut"], 8, "mixed")
+    with pytest.raises(ace.AceError):
+        ace.ace_load(bare, path)
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(ace.AceError):
+            ace.Plan(s["grid"], s["cell"], s["ecut"], 8, "mixed", coulomb_rc=bad)
