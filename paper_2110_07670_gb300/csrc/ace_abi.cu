@@ -108,7 +108,7 @@ struct ace_plan {
     float* d_kern = nullptr;   // 4 pi / |G|^2 / N in the tile passes' spectrum layout (zline only)
     float* d_kern_t = nullptr; // the same for transposed planes (n % 16 == 0 cubes)
     double coul_rc = 0;        // Coulomb cutoff radius (0: 4 pi / |G|^2 with G = 0 dropped)
-    void* d_kern_r = nullptr;  // cut-off kernel for the Coulomb stage of the tile passes, R[n0][n1][n2]
+    void* d_kern_r = nullptr;  // K(G) / N for the Coulomb stage of the tile passes, R[n0][n1][n2]
     int variant = 1;           // pair passes: 1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid
     bool hybrid = false;       // variant 4: plane-kernel P1 in the tile layout, then the tile P2 / P3
     float tune_ms[5] = {0, 0, 0, 0, 0};  // autotune: tile x1 stream, tile x2, planes x2, pipeline, hybrid x2
@@ -994,12 +994,13 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     const bool swz = P->s_xy.cube && cube_swizzle(P->n[2]);
     // Coulomb tables K(G) / N (Eq. 3) at every stored position of the spectrum,
     // computed in double: the per-pencil pass always reads one; the Coulomb
-    // stage of the tile passes reads one only for the cut-off interaction (for
-    // the bare 4 pi / |G|^2 it forms the factor from G itself).
+    // stage of the tile passes reads one for the cut-off interaction and in
+    // double precision (one load is cheaper than a double division there); in
+    // single precision it forms 4 pi / |G|^2 from G itself.
     if (opts) P->coul_rc = opts->coulomb_rc;
     P->zline = P->s_xy.cube && P->s_z.cube && zline_group(P->n[0]) > 0;
     if (const char* env = std::getenv("ACE_ZLINE")) P->zline = P->zline && std::atoi(env) != 0;
-    const bool inline_tab = P->coul_rc > 0 && !P->zline;
+    const bool inline_tab = !P->zline && (P->coul_rc > 0 || sizeof(R) == 8);
     if (P->zline || inline_tab) {
         const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
         const bool with_t = P->zline && tplane_supported(n0);

@@ -63,7 +63,7 @@ struct PassArgs {
     const int* freq[3];  // per axis: frequency held at each position after the forward stages
     const void* kern;    // per-pencil Coulomb pass: 4 pi / |G|^2 / N in spectrum layout, [n0][n1][n2] float
     int kern_inline;     // 1: the tile passes' Coulomb stage reads K(G) / N from kern ([n0][n1][n2], type R,
-                         // by x slot) instead of forming 4 pi / |G|^2 (the cut-off interaction)
+                         // by x slot) instead of forming 4 pi / |G|^2 (cut-off interaction; double precision)
 };
 
 struct PassShape {
