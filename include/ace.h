@@ -30,7 +30,8 @@
  *  - Real-space grid grid[3] = (n0, n1, n2) along (a1, a2, a3); each n is a
  *    product of 2, 3, 5 and n_d >= 2 max|Miller_d| + 1.
  *  - Coulomb kernel 4 pi / |G|^2 on every G of the FFT box (folded to
- *    -n/2..n/2-1), G = 0 term dropped.
+ *    -n/2..n/2-1), G = 0 term dropped; or the interaction cut off at a radius
+ *    (ace_opts.coulomb_rc).
  *  - Vectors are complex, interleaved (re, im): complex128 for ACE_FP64 plans,
  *    complex64 for ACE_MIXED plans.  [rows][n_pw_half].
  *
@@ -188,6 +189,36 @@ int ace_build_finish(ace_plan* plan, const void* psi_G, int n_occ, const void* W
  */
 int ace_overlap_screen(ace_plan* plan, const void* psi_G, int n_occ, double rho_cut, int32_t* pair_row_ptr,
                        int32_t* pair_col, int* n_pairs, double* S, void* stream);
+
+/*
+ * SCDM localisation (Section 2.4) with the s'-MTACE pre-selection (Section
+ * 2.5): the orthonormal localised orbitals built from selected columns of the
+ * density matrix Gamma = Psi Psi^*, for the s-MTACE construction.
+ *   1. rho(r) = sum_i psi_i(r)^2 and grad rho = 2 sum_i psi_i grad psi_i on the
+ *      plan's grid (grad psi_i exact for the plane-wave expansion);
+ *   2. preselect != 0: candidate grid points are those with rho > <rho> and
+ *      |grad rho| < <|grad rho|> (averages over all grid points); preselect == 0:
+ *      every grid point;
+ *   3. column-pivoted (rank-revealing) QR of Psi^* restricted to the candidate
+ *      columns: the n_occ pivots C_k, at each step the column of largest
+ *      residual norm (ties to the lowest grid index);
+ *   4. phi_G = O psi_G with O = (V V^T)^{-1/2} V, V[k][i] = psi_i(r_{C_k}): the
+ *      columns Gamma(r, r_{C_k}) orthonormalised symmetrically (Loewdin).
+ * Every step after the real-space orbitals runs in double.
+ *   psi_G        [n_occ][n_pw_half] device, orthonormal, as ace_build (n_occ <= 2048)
+ *   phi_G        [n_occ][n_pw_half] device output, same precision; must not overlap psi_G
+ *   pivots       [n_occ] host output (may be NULL): grid points (i0 n1 + i1) n2 + i2, in pivot order
+ *   n_candidates host output (may be NULL): candidate grid points
+ *   O            [n_occ][n_occ] host output (may be NULL): the orthogonal rotation, row k for pivot k
+ * ACE_ERR_NOT_POSDEF when fewer candidates than orbitals remain, the candidate
+ * columns have rank below n_occ, or the orthonormalisation does not converge.
+ * Uses the plan's real-space buffers (the next ace_build recomputes them).
+ * Synchronises the stream.  Grid points whose rho or |grad rho| lies within
+ * rounding of an average, and pivots whose residual ties within rounding, may
+ * fall either way.
+ */
+int ace_scdm(ace_plan* plan, const void* psi_G, int n_occ, int preselect, void* phi_G, int32_t* pivots,
+             int* n_candidates, double* O, void* stream);
 
 /*
  * Apply the compressed operator (Eq. 5, an inner MTS step):

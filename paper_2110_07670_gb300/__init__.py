@@ -25,7 +25,7 @@ SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_
            "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc",
            "ace_build_batched", "ace_save", "ace_load", "ace_build_pairs", "ace_build_finish",
            "ace_plan_config", "ace_overlap_screen", "ace_build_async", "ace_build_result",
-           "ace_check_timeout_path")
+           "ace_check_timeout_path", "ace_scdm")
 
 _lib = None
 
@@ -86,6 +86,7 @@ def load(build_if_missing=False):
     lib.ace_build_result.argtypes = [P, ctypes.POINTER(f64), P]
     lib.ace_overlap_screen.argtypes = [P, P, i32, f64, P, P, ctypes.POINTER(i32), P, P]
     lib.ace_plan_config.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+    lib.ace_scdm.argtypes = [P, P, i32, i32, P, P, ctypes.POINTER(i32), P, P]
     lib.ace_apply_noalloc.argtypes = [P, i32, P, i32, i32, i32, P, P]
     lib.hfx_apply_exact.argtypes = [P, P, i32, f64, P, i32, P, P]
     lib.ace_last_intermediates.argtypes = [P, P, P, P]
@@ -291,6 +292,29 @@ def ace_build_result(plan, stream=None):
     E = ctypes.c_double(0.0)
     _check(load().ace_build_result(plan.handle, ctypes.byref(E), _stream(stream)))
     return E.value
+
+
+def ace_scdm(plan, psi_G, preselect=True, phi_G=None, stream=None):
+    """SCDM localisation (Section 2.4) with the s'-MTACE pre-selection
+    (Section 2.5, preselect=True): returns (phi_G, pivots, O, n_candidates) --
+    the localised orbitals (same layout and precision as psi_G), the pivot grid
+    points (i0 n1 + i1) n2 + i2, the orthogonal rotation phi = O psi (float64
+    numpy) and how many grid points were candidates."""
+    import torch
+
+    psi_G = plan._vec(psi_G, "psi_G")
+    n = psi_G.shape[0]
+    if phi_G is None:
+        phi_G = torch.empty_like(psi_G)
+    else:
+        phi_G = plan._vec(phi_G, "phi_G")
+    piv = np.zeros(n, dtype=np.int32)
+    O = np.zeros((n, n), dtype=np.float64)
+    nc = ctypes.c_int(0)
+    _check(load().ace_scdm(plan.handle, _ptr(psi_G), n, int(bool(preselect)), _ptr(phi_G),
+                           piv.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nc), O.ctypes.data_as(ctypes.c_void_p),
+                           _stream(stream)))
+    return phi_G, piv, O, nc.value
 
 
 def ace_overlap_screen(plan, psi_G, rho_cut, stream=None):

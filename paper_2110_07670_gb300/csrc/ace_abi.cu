@@ -109,6 +109,18 @@ struct ace_plan {
     float* d_kern_t = nullptr; // the same for transposed planes (n % 16 == 0 cubes)
     double coul_rc = 0;        // Coulomb cutoff radius (0: 4 pi / |G|^2 with G = 0 dropped)
     void* d_kern_r = nullptr;  // K(G) / N for the Coulomb stage of the tile passes, R[n0][n1][n2]
+    struct Scdm {                 // SCDM workspace, grown on first use
+        double* gv = nullptr;     // G components per plane wave [3][npw]
+        char* dpsi = nullptr;     // derivative coefficients [n][npw] complex (plan precision)
+        double* dens = nullptr;   // rho [N], grad rho [3][N], then the stats partials and means
+        int* isel = nullptr;      // block counts, offsets, candidate grid points
+        double* A = nullptr;      // candidate columns [n][m]
+        double* nu = nullptr;     // residual norms [m]
+        char* part = nullptr;     // argmax partials
+        double* mats = nullptr;   // Q, X, T, Y [n][n] each, err
+        int* ipiv = nullptr;      // pivots [n], status
+        size_t c_dpsi = 0, c_dens = 0, c_isel = 0, c_A = 0, c_nu = 0, c_part = 0, c_mats = 0, c_ipiv = 0;
+    } scdm;
     int variant = 1;           // pair passes: 1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid
     bool hybrid = false;       // variant 4: plane-kernel P1 in the tile layout, then the tile P2 / P3
     float tune_ms[5] = {0, 0, 0, 0, 0};  // autotune: tile x1 stream, tile x2, planes x2, pipeline, hybrid x2
@@ -817,6 +829,108 @@ int overlap_impl(ace_plan* P, const void* psi_G, int n, double rho_cut, int32_t*
     return ACE_OK;
 }
 
+// SCDM localisation (Section 2.4) with the s'-MTACE pre-selection (Section
+// 2.5): real-space orbitals, rho and grad rho, the candidate grid points,
+// column-pivoted QR of Psi^* on them, and phi_G = O psi_G with O the polar
+// factor of V[k][i] = psi_i(r_{C_k}) (scdm.cu).  Blocking: the pivot count
+// and the Newton-Schulz convergence are read on the host.
+template <typename R>
+int scdm_impl(ace_plan* P, const void* psi_G, int n, int preselect, void* phi_G, int32_t* pivots, int* n_cand,
+              double* O, cudaStream_t st) {
+    ACE_TRY(check_gamma<R>(P, psi_G, n, st));
+    auto& W = P->scdm;
+    const long long N = P->N;
+    const int npw = P->npw;
+    std::vector<Quad> oq = orbital_quads(n);
+    ACE_TRY(upload_quads(P, oq, st));
+    R* phi = (R*)P->d_phi;
+    ACE_TRY(run_to_real<R>(P, (const cx<R>*)psi_G, P->d_quads, (int)oq.size(), phi, st));
+    long long m = N;
+    const int* sel = nullptr;
+    if (preselect) {
+        if (!W.gv) {
+            std::vector<double> gv((size_t)3 * npw);
+            for (int p = 0; p < npw; ++p)
+                for (int c = 0; c < 3; ++c) {
+                    double g = 0;
+                    for (int ax = 0; ax < 3; ++ax) g += P->miller[3 * p + ax] * P->b[3 * ax + c];
+                    gv[(size_t)c * npw + p] = g;
+                }
+            ACE_TRY(dalloc((void**)&W.gv, gv.size() * sizeof(double)));
+            ACE_CK(cudaMemcpy(W.gv, gv.data(), gv.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        const int ns = scdm_stats_blocks(N), nsel = scdm_select_blocks(N);
+        ACE_TRY(grow(&W.dpsi, &W.c_dpsi, (size_t)n * npw * sizeof(cx<R>)));
+        ACE_TRY(grow(&W.dens, &W.c_dens, (size_t)4 * N + 2 * ns + 2));
+        ACE_TRY(grow(&W.isel, &W.c_isel, (size_t)2 * nsel + 1 + N));
+        double *rho = W.dens, *grad = W.dens + N, *part = W.dens + 4 * N, *means = part + 2 * ns;
+        int *counts = W.isel, *offsets = W.isel + nsel, *cand = W.isel + 2 * nsel + 1;
+        R* dphi = (R*)P->d_acc;
+        cx<R>* dpsi = (cx<R>*)W.dpsi;
+        // grad rho = 2 sum_i psi_i grad psi_i, one Cartesian component at a time
+        for (int d = 0; d < 3; ++d) {
+            ACE_CKL(launch_deriv_coeffs<R>((const cx<R>*)psi_G, n, npw, W.gv + (size_t)d * npw, dpsi, st));
+            ACE_TRY(run_to_real<R>(P, dpsi, P->d_quads, (int)oq.size(), dphi, st));
+            ACE_CKL(launch_orbital_sum<R>(phi, dphi, n, N, grad + d * N, st));
+        }
+        ACE_CKL(launch_orbital_sum<R>(phi, nullptr, n, N, rho, st));
+        ACE_CKL(launch_scdm_stats(rho, grad, N, part, means, st));
+        ACE_CKL(launch_scdm_select(rho, grad, N, means, counts, offsets, cand, st));
+        int count = 0;
+        ACE_CK(cudaMemcpyAsync(&count, offsets + nsel, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ACE_CK(cudaStreamSynchronize(st));
+        if (count < n)
+            return fail(ACE_ERR_NOT_POSDEF, "pre-selection kept " + std::to_string(count) + " grid points for " +
+                                                std::to_string(n) + " orbitals");
+        m = count;
+        sel = cand;
+    }
+    // column-pivoted QR of the candidate columns: n steps, each a pass over A
+    const int qb = scdm_qr_blocks(m);
+    ACE_TRY(grow(&W.A, &W.c_A, (size_t)n * m));
+    ACE_TRY(grow(&W.nu, &W.c_nu, (size_t)m));
+    ACE_TRY(grow(&W.part, &W.c_part, (size_t)qb * scdm_argmax_bytes()));
+    ACE_TRY(grow(&W.mats, &W.c_mats, (size_t)4 * n * n + 2));
+    ACE_TRY(grow(&W.ipiv, &W.c_ipiv, (size_t)2 * n + 1));
+    double *Q = W.mats, *X = Q + (size_t)n * n, *T = X + (size_t)n * n, *Y = T + (size_t)n * n, *err = Y + (size_t)n * n;
+    int *piv = W.ipiv, *status = W.ipiv + n;  // piv: columns of A; grid points after them
+    ACE_CK(cudaMemsetAsync(status, 0, sizeof(int), st));
+    ACE_CKL(launch_gather_columns<R>(phi, n, N, sel, m, W.A, st));
+    ACE_CKL(launch_qr_init(W.A, n, m, W.nu, W.part, st));
+    ACE_CKL(launch_qr_pick(W.part, m, W.A, n, Q, 0, piv, W.nu, err + 1, status, st));
+    for (int k = 1; k < n; ++k) {
+        ACE_CKL(launch_qr_update(W.A, n, m, Q + (size_t)(k - 1) * n, W.nu, W.part, st));
+        ACE_CKL(launch_qr_pick(W.part, m, W.A, n, Q, k, piv, W.nu, err + 1, status, st));
+    }
+    int h_status = 0;
+    ACE_CK(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaStreamSynchronize(st));
+    if (h_status) return fail(ACE_ERR_NOT_POSDEF, "the candidate columns of Psi^* have rank below n_occ");
+    // the polar factor of V by Newton-Schulz steps, until X X^T = I to 1e-10
+    // (the step after that leaves rounding only)
+    ACE_CKL(launch_polar_start(W.A, n, m, piv, X, st));
+    bool converged = false;
+    for (int it = 0; it < 100 && !converged; ++it) {
+        ACE_CKL(launch_newton_schulz_step(X, T, Y, n, err, st));
+        double h_err = 0;
+        ACE_CK(cudaMemcpyAsync(&h_err, err, sizeof(double), cudaMemcpyDeviceToHost, st));
+        ACE_CK(cudaStreamSynchronize(st));
+        converged = h_err < 1e-10;
+    }
+    if (!converged) return fail(ACE_ERR_NOT_POSDEF, "the orthonormalisation of the selected columns did not converge");
+    ACE_CKL(launch_gemm_nn<R>(X, n, n, (const R*)psi_G, 2LL * npw, 1.0, (R*)phi_G, true, st));
+    if (pivots) {
+        int* grid_pts = W.ipiv + n + 1;
+        ACE_CKL(launch_map_pivots(piv, sel, n, grid_pts, st));
+        ACE_CK(cudaMemcpyAsync(pivots, grid_pts, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    if (O) ACE_CK(cudaMemcpyAsync(O, X, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaStreamSynchronize(st));
+    ACE_TRY(check_device_error(P, st));
+    if (n_cand) *n_cand = (int)m;
+    return ACE_OK;
+}
+
 template <typename R>
 int apply_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, void* out, cudaStream_t st) {
     ACE_TRY(grow(&P->d_C, &P->C_cap, (size_t)T * n_occ));
@@ -839,7 +953,9 @@ void free_plan(ace_plan* P) {
     if (P->fork_ev) cudaEventDestroy(P->fork_ev);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
                     P->d_WG, P->d_M, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
-                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_kern_t, P->d_kern_r, P->d_pipe};
+                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_kern_t, P->d_kern_r, P->d_pipe,
+                    P->scdm.gv, P->scdm.dpsi, P->scdm.dens, P->scdm.isel, P->scdm.A, P->scdm.nu,
+                    P->scdm.part, P->scdm.mats, P->scdm.ipiv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -1205,6 +1321,21 @@ int ace_overlap_screen(ace_plan* plan, const void* psi_G, int n_occ, double rho_
     return plan->prec == ACE_FP64
                ? overlap_impl<double>(plan, psi_G, n_occ, rho_cut, pair_row_ptr, pair_col, n_pairs, S, st)
                : overlap_impl<float>(plan, psi_G, n_occ, rho_cut, pair_row_ptr, pair_col, n_pairs, S, st);
+}
+
+int ace_scdm(ace_plan* plan, const void* psi_G, int n_occ, int preselect, void* phi_G, int32_t* pivots,
+             int* n_candidates, double* O, void* stream) {
+    if (!plan || !psi_G || !phi_G) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (n_occ < 1 || n_occ > plan->n_occ_max) return fail(ACE_ERR_INVALID_ARG, "n_occ out of range");
+    if (n_occ > 2048) return fail(ACE_ERR_INVALID_ARG, "ace_scdm: at most 2048 orbitals");
+    const size_t bytes = (size_t)n_occ * plan->npw * 2 * plan->esz;
+    const char *a = (const char*)psi_G, *b = (const char*)phi_G;
+    if (a < b + bytes && b < a + bytes) return fail(ACE_ERR_INVALID_ARG, "ace_scdm: phi_G overlaps psi_G");
+    DeviceGuard g(plan->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->prec == ACE_FP64
+               ? scdm_impl<double>(plan, psi_G, n_occ, preselect, phi_G, pivots, n_candidates, O, st)
+               : scdm_impl<float>(plan, psi_G, n_occ, preselect, phi_G, pivots, n_candidates, O, st);
 }
 
 int ace_build_finish(ace_plan* plan, const void* psi_G, int n_occ, const void* W_G, void* xi, void* stream) {

@@ -194,6 +194,44 @@ template <typename R>
 cudaError_t launch_gemm_nn(const double* A, int m, int k, const R* B, long long ncols, double alpha, R* out,
                            bool fp64_math, cudaStream_t st, bool lower = false);
 
+// ---- SCDM localisation (Sections 2.4-2.5; scdm.cu), every result in double
+// out[i][p] = i gd[p] psi[i][p] (the coefficients of d psi_i / d r_d)
+template <typename R>
+cudaError_t launch_deriv_coeffs(const cx<R>* psi, int n, int npw, const double* gd, cx<R>* out, cudaStream_t st);
+// out[r] = sum_i phi_i(r)^2 (dphi null) or 2 sum_i phi_i(r) dphi_i(r); phi, dphi [n][N]
+template <typename R>
+cudaError_t launch_orbital_sum(const R* phi, const R* dphi, int n, long long N, double* out, cudaStream_t st);
+// means[0] = <rho>, means[1] = <|grad rho|> (grad [3][N]); part: 2 scdm_stats_blocks(N) doubles
+int scdm_stats_blocks(long long N);
+cudaError_t launch_scdm_stats(const double* rho, const double* grad, long long N, double* part, double* means,
+                              cudaStream_t st);
+// sel <- ascending grid points with rho > means[0] and |grad rho| < means[1];
+// counts [scdm_select_blocks(N)], offsets [scdm_select_blocks(N) + 1] (the last: how many)
+int scdm_select_blocks(long long N);
+cudaError_t launch_scdm_select(const double* rho, const double* grad, long long N, const double* means, int* counts,
+                               int* offsets, int* sel, cudaStream_t st);
+// A[i][s] = phi_i(r_s), r_s = sel[s] (sel null: s), A [n][m]
+template <typename R>
+cudaError_t launch_gather_columns(const R* phi, int n, long long N, const int* sel, long long m, double* A,
+                                  cudaStream_t st);
+// column-pivoted QR of A [n][m] by Gram-Schmidt: nu [m] residual norms, part
+// [scdm_qr_blocks(m)] argmax partials of scdm_argmax_bytes() each, Q [n][n]
+// (row k = q_k), piv [n], nu0 one double; status set to 1 on rank deficiency
+// (a best residual norm^2 not above 1e-10 of the largest column norm^2)
+int scdm_qr_blocks(long long m);
+size_t scdm_argmax_bytes();
+cudaError_t launch_qr_init(const double* A, int n, long long m, double* nu, void* part, cudaStream_t st);
+cudaError_t launch_qr_update(const double* A, int n, long long m, const double* qk, double* nu, void* part,
+                             cudaStream_t st);
+cudaError_t launch_qr_pick(const void* part, long long m, const double* A, int n, double* Q, int k, int* piv,
+                           double* nu, double* nu0, int* status, cudaStream_t st);
+// out[k] = sel[piv[k]] (sel null: piv[k]): the pivots' grid points
+cudaError_t launch_map_pivots(const int* piv, const int* sel, int n, int* out, cudaStream_t st);
+// X [n][n] = V / |V|_F, V[k][i] = A[i][piv[k]]; one Newton-Schulz step toward
+// its polar factor (T, Y [n][n] scratch), err[0] = max |X X^T - I| before it
+cudaError_t launch_polar_start(const double* A, int n, long long m, const int* piv, double* X, cudaStream_t st);
+cudaError_t launch_newton_schulz_step(double* X, double* T, double* Y, int n, double* err, cudaStream_t st);
+
 // Cholesky of -M and the inverse of its factor, in double, one thread block.
 // status: 0 ok, 1 not positive definite.
 cudaError_t launch_neg_cholesky_inverse(const double* M, int n, double* L, double* Linv, int* status,
