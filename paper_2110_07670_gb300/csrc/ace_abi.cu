@@ -114,10 +114,10 @@ struct ace_plan {
         char* dpsi = nullptr;     // derivative coefficients [n][npw] complex (plan precision)
         double* dens = nullptr;   // rho [N], grad rho [3][N], then the stats partials and means
         int* isel = nullptr;      // block counts, offsets, candidate grid points
-        double* A = nullptr;      // candidate columns [n][m]
-        double* nu = nullptr;     // residual norms [m]
+        char* A = nullptr;        // candidate columns [n][m], double
+        double* nu = nullptr;     // residual norms [m], then the QR coefficients [n][m]
         char* part = nullptr;     // argmax partials
-        double* mats = nullptr;   // Q, X, T, Y [n][n] each, err
+        double* mats = nullptr;   // Q, X, T, Y [n][n] each, err, nu0, r [n], c [n]
         int* ipiv = nullptr;      // pivots [n], status
         size_t c_dpsi = 0, c_dens = 0, c_isel = 0, c_A = 0, c_nu = 0, c_part = 0, c_mats = 0, c_ipiv = 0;
     } scdm;
@@ -887,38 +887,49 @@ int scdm_impl(ace_plan* P, const void* psi_G, int n, int preselect, void* phi_G,
     }
     // column-pivoted QR of the candidate columns: n steps, each a pass over A
     const int qb = scdm_qr_blocks(m);
-    ACE_TRY(grow(&W.A, &W.c_A, (size_t)n * m));
-    ACE_TRY(grow(&W.nu, &W.c_nu, (size_t)m));
+    ACE_TRY(grow(&W.A, &W.c_A, (size_t)n * m * sizeof(double)));
+    ACE_TRY(grow(&W.nu, &W.c_nu, (size_t)m + (size_t)n * m));
     ACE_TRY(grow(&W.part, &W.c_part, (size_t)qb * scdm_argmax_bytes()));
-    ACE_TRY(grow(&W.mats, &W.c_mats, (size_t)4 * n * n + 2));
+    ACE_TRY(grow(&W.mats, &W.c_mats, (size_t)4 * n * n + 3 * n + 3));
     ACE_TRY(grow(&W.ipiv, &W.c_ipiv, (size_t)2 * n + 1));
+    double* A = (double*)W.A;
     double *Q = W.mats, *X = Q + (size_t)n * n, *T = X + (size_t)n * n, *Y = T + (size_t)n * n, *err = Y + (size_t)n * n;
     int *piv = W.ipiv, *status = W.ipiv + n;  // piv: columns of A; grid points after them
+    double *rdiag = err + 2 + 2 * n, *fro = rdiag + n;  // after err, nu0, r, c; fro right after rdiag
+    const QrWork qw{W.part, W.nu, W.nu + m, Q, err + 2, err + 2 + n, err + 1, rdiag, piv, status};
     ACE_CK(cudaMemsetAsync(status, 0, sizeof(int), st));
-    ACE_CKL(launch_gather_columns<R>(phi, n, N, sel, m, W.A, st));
-    ACE_CKL(launch_qr_init(W.A, n, m, W.nu, W.part, st));
-    ACE_CKL(launch_qr_pick(W.part, m, W.A, n, Q, 0, piv, W.nu, err + 1, status, st));
-    for (int k = 1; k < n; ++k) {
-        ACE_CKL(launch_qr_update(W.A, n, m, Q + (size_t)(k - 1) * n, W.nu, W.part, st));
-        ACE_CKL(launch_qr_pick(W.part, m, W.A, n, Q, k, piv, W.nu, err + 1, status, st));
-    }
+    ACE_CKL(launch_gather_columns<R>(phi, n, N, sel, m, A, st));
+    ACE_CKL(launch_qr_init<double>(A, n, m, W.nu, W.part, st));
+    for (int k = 0; k < n; ++k) ACE_CKL(launch_qr_step<double>(A, n, m, k, qw, st));
     int h_status = 0;
     ACE_CK(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     ACE_CK(cudaStreamSynchronize(st));
     if (h_status) return fail(ACE_ERR_NOT_POSDEF, "the candidate columns of Psi^* have rank below n_occ");
-    // the polar factor of V by Newton-Schulz steps, until X X^T = I to 1e-10
-    // (the step after that leaves rounding only)
-    ACE_CKL(launch_polar_start(W.A, n, m, piv, X, st));
+    // the polar factor of V by scaled Newton-Schulz steps (Chen & Chow): X0 =
+    // V / |V|_F has its singular values in (0, 1]; l estimates the smallest,
+    // from above, by min_k R[k][k] / |V|_F (an over-estimate only makes a
+    // step less aggressive), and follows its image under each step.  Until
+    // X X^T = I to 1e-10; the step after that leaves rounding only.
+    ACE_CKL(launch_polar_start<double>(A, n, m, piv, X, fro, st));
+    std::vector<double> hd((size_t)n + 1);
+    ACE_CK(cudaMemcpyAsync(hd.data(), rdiag, ((size_t)n + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaStreamSynchronize(st));
+    double l = *std::min_element(hd.begin(), hd.begin() + n) / hd[n];
+    if (!(l > 0) || l > 1) l = 1;
     bool converged = false;
     for (int it = 0; it < 100 && !converged; ++it) {
-        ACE_CKL(launch_newton_schulz_step(X, T, Y, n, err, st));
+        const double alpha = std::sqrt(3.0 / (1.0 + l + l * l));
+        ACE_CKL(launch_newton_schulz_step(X, T, Y, n, alpha, err, st));
+        l = std::min(1.0, 0.5 * alpha * l * (3.0 - alpha * alpha * l * l));
         double h_err = 0;
         ACE_CK(cudaMemcpyAsync(&h_err, err, sizeof(double), cudaMemcpyDeviceToHost, st));
         ACE_CK(cudaStreamSynchronize(st));
         converged = h_err < 1e-10;
     }
     if (!converged) return fail(ACE_ERR_NOT_POSDEF, "the orthonormalisation of the selected columns did not converge");
-    ACE_CKL(launch_gemm_nn<R>(X, n, n, (const R*)psi_G, 2LL * npw, 1.0, (R*)phi_G, true, st));
+    // phi_G = O psi_G: double arithmetic for double plans; single precision
+    // with compensated slice sums otherwise (as the ACE apply)
+    ACE_CKL(launch_gemm_nn<R>(X, n, n, (const R*)psi_G, 2LL * npw, 1.0, (R*)phi_G, sizeof(R) == 8, st));
     if (pivots) {
         int* grid_pts = W.ipiv + n + 1;
         ACE_CKL(launch_map_pivots(piv, sel, n, grid_pts, st));

@@ -210,27 +210,40 @@ cudaError_t launch_scdm_stats(const double* rho, const double* grad, long long N
 int scdm_select_blocks(long long N);
 cudaError_t launch_scdm_select(const double* rho, const double* grad, long long N, const double* means, int* counts,
                                int* offsets, int* sel, cudaStream_t st);
-// A[i][s] = phi_i(r_s), r_s = sel[s] (sel null: s), A [n][m]
+// A[i][s] = phi_i(r_s) in double, r_s = sel[s] (sel null: s), A [n][m]
 template <typename R>
 cudaError_t launch_gather_columns(const R* phi, int n, long long N, const int* sel, long long m, double* A,
                                   cudaStream_t st);
-// column-pivoted QR of A [n][m] by Gram-Schmidt: nu [m] residual norms, part
-// [scdm_qr_blocks(m)] argmax partials of scdm_argmax_bytes() each, Q [n][n]
-// (row k = q_k), piv [n], nu0 one double; status set to 1 on rank deficiency
-// (a best residual norm^2 not above 1e-10 of the largest column norm^2)
+// Column-pivoted QR of A [n][m] by Gram-Schmidt applied twice, all products in
+// double: launch_qr_init, then launch_qr_step for k = 0 .. n-1 (step k picks
+// pivot k and, below n - 1, updates the residual norms).  part:
+// scdm_qr_blocks(m) argmax partials of scdm_argmax_bytes() each; nu [m]
+// residual norms; R [n][m] coefficients q_l . a_j; Q [n][n] (row k = q_k);
+// r, c [n] scratch; piv [n] columns of A; nu0 one double; status set to 1 on
+// rank deficiency (a best residual norm^2 not above 1e-10 of the largest
+// column norm^2).
 int scdm_qr_blocks(long long m);
 size_t scdm_argmax_bytes();
-cudaError_t launch_qr_init(const double* A, int n, long long m, double* nu, void* part, cudaStream_t st);
-cudaError_t launch_qr_update(const double* A, int n, long long m, const double* qk, double* nu, void* part,
-                             cudaStream_t st);
-cudaError_t launch_qr_pick(const void* part, long long m, const double* A, int n, double* Q, int k, int* piv,
-                           double* nu, double* nu0, int* status, cudaStream_t st);
+struct QrWork {
+    void* part;
+    double *nu, *R, *Q, *r, *c, *nu0, *rdiag;  // rdiag [n]: R[k][k] = |r_k|
+    int *piv, *status;
+};
+template <typename T>
+cudaError_t launch_qr_init(const T* A, int n, long long m, double* nu, void* part, cudaStream_t st);
+template <typename T>
+cudaError_t launch_qr_step(const T* A, int n, long long m, int k, QrWork w, cudaStream_t st);
 // out[k] = sel[piv[k]] (sel null: piv[k]): the pivots' grid points
 cudaError_t launch_map_pivots(const int* piv, const int* sel, int n, int* out, cudaStream_t st);
-// X [n][n] = V / |V|_F, V[k][i] = A[i][piv[k]]; one Newton-Schulz step toward
-// its polar factor (T, Y [n][n] scratch), err[0] = max |X X^T - I| before it
-cudaError_t launch_polar_start(const double* A, int n, long long m, const int* piv, double* X, cudaStream_t st);
-cudaError_t launch_newton_schulz_step(double* X, double* T, double* Y, int n, double* err, cudaStream_t st);
+// X [n][n] = V / |V|_F, V[k][i] = A[i][piv[k]], fro = |V|_F; one Newton-Schulz
+// step toward its polar factor with the scaling alpha (Chen & Chow, SIAM J.
+// Matrix Anal. Appl. 35 (2014)), T, Y [n][n] scratch, err[0] = max |X X^T - I|
+// before it
+template <typename T>
+cudaError_t launch_polar_start(const T* A, int n, long long m, const int* piv, double* X, double* fro,
+                               cudaStream_t st);
+cudaError_t launch_newton_schulz_step(double* X, double* T, double* Y, int n, double alpha, double* err,
+                                      cudaStream_t st);
 
 // Cholesky of -M and the inverse of its factor, in double, one thread block.
 // status: 0 ok, 1 not positive definite.

@@ -6,8 +6,8 @@
 //     plane-wave expansion); every sum over orbitals in double
 //   candidates: rho > <rho> and |grad rho| < <|grad rho|>, ascending grid index
 //   pivots: column-pivoted QR of Psi^* on the candidate columns, as Gram-Schmidt
-//     with re-orthogonalisation: at step k the column of largest residual norm
-//     (ties to the lowest index), residual norms downdated by (q_k . a_j)^2
+//     applied twice: at step k the column of largest residual norm (ties to
+//     the lowest index), residual norms downdated by (q_k . a_j)^2
 //   Phi = (V V^T)^{-1/2} V Psi, V[k][i] = psi_i(r_{C_k}): the polar factor of V
 //     by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2 from V / |V|_F
 // All of it in double; the orbitals' real-space values come in the plan's
@@ -97,17 +97,17 @@ template <typename R>
 __global__ void orbital_sum_kernel(const R* __restrict__ phi, const R* __restrict__ dphi, int n, long long N,
                                    double* __restrict__ out) {
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
+        // single precision: the products of each 8 orbitals summed in float,
+        // those sums in double; double precision: everything in double
+        const R* b = dphi ? dphi : phi;
         double s = 0;
-        if (dphi) {
-            for (int i = 0; i < n; ++i) s += (double)phi[i * N + r] * (double)dphi[i * N + r];
-            out[r] = 2.0 * s;
-        } else {
-            for (int i = 0; i < n; ++i) {
-                const double v = (double)phi[i * N + r];
-                s += v * v;
-            }
-            out[r] = s;
+        for (int i0 = 0; i0 < n; i0 += 8) {
+            R f = R(0);
+            const int i1 = i0 + 8 < n ? i0 + 8 : n;
+            for (int i = i0; i < i1; ++i) f += phi[i * N + r] * b[i * N + r];
+            s += (double)f;
         }
+        out[r] = dphi ? 2.0 * s : s;
     }
 }
 
@@ -201,7 +201,9 @@ __global__ void select_scatter_kernel(const double* __restrict__ rho, const doub
     if (f) sel[offsets[blockIdx.x] + before + __popc(bal & ((1u << l) - 1u))] = (int)r;
 }
 
-// A[i][s] = phi_i(r_s) in double, r_s = sel[s] (sel == nullptr: r_s = s)
+// A[i][s] = phi_i(r_s) in double, r_s = sel[s] (sel == nullptr: r_s = s):
+// converted once here, since a conversion in the QR passes would cost as much
+// of the double-precision pipe as the products themselves
 template <typename R>
 __global__ void gather_columns_kernel(const R* __restrict__ phi, long long N, const int* __restrict__ sel,
                                       long long m, double* __restrict__ A) {
@@ -211,100 +213,180 @@ __global__ void gather_columns_kernel(const R* __restrict__ phi, long long N, co
 }
 
 // ------------------------------------------------------ column-pivoted QR
+// Step k: (1) the pivot p_k, the column of largest residual norm nu; (2) its
+// residual r = a_p - sum_{l<k} R[l][p] q_l with the coefficients R[l][j] =
+// q_l . a_j stored by the earlier updates, then once more against q_0..q_{k-1}
+// (classical Gram-Schmidt, twice); (3) q_k = r / |r|, R[k][j] = q_k . a_j and
+// nu_j -= R[k][j]^2 for every column not chosen yet (nu < 0 marks chosen ones).
+
+// r[i] = base - (the 8 partial sums of row i), the 8 partials held by the
+// threads i % 32 of the block's 8 warps (blockDim 256)
+__device__ __forceinline__ void rows_reduce8(double part, double base, double* r, int i, int n) {
+    __shared__ double red[8][33];
+    red[threadIdx.x >> 5][threadIdx.x & 31] = part;
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0 && i < n) {
+        double s = 0;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) s += red[g][threadIdx.x];
+        r[i] = base - s;
+    }
+}
 
 // nu[j] = |a_j|^2 and the block's largest
-__global__ void qr_init_kernel(const double* __restrict__ A, int n, long long m, double* __restrict__ nu,
+template <typename T>
+__global__ void qr_init_kernel(const T* __restrict__ A, int n, long long m, double* __restrict__ nu,
                                ArgMax* __restrict__ part) {
     ArgMax best{-1.0, -1};
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < m; j += (long long)gridDim.x * blockDim.x) {
-        double s = 0;
-        for (int i = 0; i < n; ++i) {
-            const double v = A[i * m + j];
-            s += v * v;
+        double s[4] = {0, 0, 0, 0};
+        int i = 0;
+        for (; i + 4 <= n; i += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double v = (double)A[(i + u) * m + j];
+                s[u] += v * v;
+            }
+        for (; i < n; ++i) {
+            const double v = (double)A[i * m + j];
+            s[0] += v * v;
         }
-        nu[j] = s;
-        best = better(best, ArgMax{s, j});
+        const double t = (s[0] + s[1]) + (s[2] + s[3]);
+        nu[j] = t;
+        best = better(best, ArgMax{t, j});
     }
     best = block_argmax(best);
     if (threadIdx.x == 0) part[blockIdx.x] = best;
 }
 
-// nu[j] -= (q_k . a_j)^2 for the columns not chosen yet (nu < 0 marks chosen
-// ones), and the block's largest
-__global__ void qr_update_kernel(const double* __restrict__ A, int n, long long m, const double* __restrict__ qk,
-                                 double* __restrict__ nu, ArgMax* __restrict__ part) {
-    extern __shared__ double q[];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) q[i] = qk[i];
-    __syncthreads();
-    ArgMax best{-1.0, -1};
-    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < m; j += (long long)gridDim.x * blockDim.x) {
-        double v = nu[j];
-        if (v < 0) continue;
-        double d = 0;
-        for (int i = 0; i < n; ++i) d += q[i] * A[i * m + j];
-        v -= d * d;
-        if (v < 0) v = 0;
-        nu[j] = v;
-        best = better(best, ArgMax{v, j});
-    }
-    best = block_argmax(best);
-    if (threadIdx.x == 0) part[blockIdx.x] = best;
-}
-
-// One block: the pivot of step k from the block partials; q_k = the
-// normalised residual of its column against q_0..q_{k-1} (two Gram-Schmidt
-// passes).  status = 1 when the largest residual norm^2 is not above 1e-10
-// times the largest column norm^2 (kept in *nu0 at step 0): the candidate
-// columns do not span n_occ dimensions beyond rounding.
-__global__ void qr_pick_kernel(const ArgMax* __restrict__ part, int nparts, const double* __restrict__ A, int n,
-                               long long m, double* __restrict__ Q, int k, int* __restrict__ piv,
-                               double* __restrict__ nu, double* __restrict__ nu0, int* __restrict__ status) {
-    extern __shared__ double sh[];
-    double* r = sh;      // n
-    double* c = sh + n;  // k coefficients
+// (1) and the first half of (2), rows [256 blockIdx.x, +256) of r.  Every
+// block reduces the partials (the same result); block 0 records the pivot.
+// status = 1 when the largest residual norm^2 is not above 1e-10 times the
+// largest column norm^2 (nu0, recorded at step 0): the candidate columns do
+// not span n_occ dimensions beyond rounding; r is then left zero.
+template <typename T>
+__global__ void qr_resid_kernel(const ArgMax* __restrict__ part, int nparts, const T* __restrict__ A, int n,
+                                long long m, const double* __restrict__ Rrows, const double* __restrict__ Q, int k,
+                                int* __restrict__ piv, double* __restrict__ nu, double* __restrict__ nu0,
+                                int* __restrict__ status, double* __restrict__ r) {
+    extern __shared__ double rp[];  // R[l][p], l < k
     __shared__ long long s_p;
-    __shared__ double s_norm;
     ArgMax best{-1.0, -1};
     for (int b = threadIdx.x; b < nparts; b += blockDim.x) best = better(best, part[b]);
     best = block_argmax(best);
     if (threadIdx.x == 0) {
-        if (k == 0) *nu0 = best.v;
-        const bool ok = best.j >= 0 && best.v > 1e-10 * *nu0 && best.v == best.v;
+        const double ref = k == 0 ? best.v : *nu0;
+        const bool ok = best.j >= 0 && best.v > 1e-10 * ref && best.v == best.v;
         s_p = ok ? best.j : -1;
-        if (!ok) *status = 1;
-        if (ok) {
-            piv[k] = (int)best.j;
-            nu[best.j] = -1.0;
+        if (blockIdx.x == 0) {
+            if (k == 0) *nu0 = best.v;
+            if (ok) {
+                piv[k] = (int)best.j;
+                nu[best.j] = -1.0;
+            } else {
+                *status = 1;
+            }
         }
     }
     __syncthreads();
-    if (s_p < 0) return;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] = A[i * m + s_p];
-    __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int l = threadIdx.x; l < k; l += blockDim.x) {
-            double s = 0;
-            for (int i = 0; i < n; ++i) s += Q[(long long)l * n + i] * r[i];
-            c[l] = s;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            double s = r[i];
-            for (int l = 0; l < k; ++l) s -= c[l] * Q[(long long)l * n + i];
-            r[i] = s;
-        }
-        __syncthreads();
+    const long long p = s_p;
+    // 32 rows per block, the k terms of each split over 8 threads
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31), g = threadIdx.x >> 5;
+    if (p < 0) {
+        if (g == 0 && i < n) r[i] = 0.0;
+        return;
     }
+    for (int l = threadIdx.x; l < k; l += blockDim.x) rp[l] = Rrows[l * m + p];
+    __syncthreads();
     double s = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += r[i] * r[i];
-    s = block_sum(s);
+    if (i < n)
+        for (int l = g; l < k; l += 8) s += rp[l] * Q[(long long)l * n + i];
+    rows_reduce8(s, i < n ? (double)A[i * m + p] : 0.0, r, i, n);
+}
+
+// second Gram-Schmidt pass, part 1: c_l = q_l . r, one warp per l
+__global__ void qr_dots_kernel(const double* __restrict__ Q, int n, int k, const double* __restrict__ r,
+                               double* __restrict__ c) {
+    const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (l >= k) return;
+    double s = 0;
+    for (int i = lane; i < n; i += 32) s += Q[(long long)l * n + i] * r[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) c[l] = s;
+}
+
+// part 2: r_i -= sum_l c_l q_l[i]
+__global__ void qr_apply_kernel(const double* __restrict__ Q, int n, int k, const double* __restrict__ c,
+                                double* __restrict__ r) {
+    extern __shared__ double cs[];
+    for (int l = threadIdx.x; l < k; l += blockDim.x) cs[l] = c[l];
+    __syncthreads();
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31), g = threadIdx.x >> 5;
+    double s = 0;
+    if (i < n)
+        for (int l = g; l < k; l += 8) s += cs[l] * Q[(long long)l * n + i];
+    rows_reduce8(s, i < n ? r[i] : 0.0, r, i, n);
+}
+
+// (3): every block normalises r itself; block 0 stores q_k and |r| = R[k][k]
+template <typename T>
+__global__ void qr_update_kernel(const T* __restrict__ A, int n, long long m, const double* __restrict__ r, int k,
+                                 double* __restrict__ Q, double* __restrict__ Rrows, double* __restrict__ nu,
+                                 double* __restrict__ rdiag, ArgMax* __restrict__ part) {
+    extern __shared__ double q[];
+    __shared__ double s_inv;
+    double ss = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = r[i];
+        q[i] = v;
+        ss += v * v;
+    }
+    ss = block_sum(ss);
     if (threadIdx.x == 0) {
-        s_norm = sqrt(s);
-        if (!(s > 0)) *status = 1;
+        s_inv = ss > 0 ? 1.0 / sqrt(ss) : 0.0;
+        if (blockIdx.x == 0) rdiag[k] = sqrt(ss);  // R[k][k]
     }
     __syncthreads();
-    if (!(s_norm > 0)) return;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) Q[(long long)k * n + i] = r[i] / s_norm;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        q[i] *= s_inv;
+        if (blockIdx.x == 0) Q[(long long)k * n + i] = q[i];
+    }
+    __syncthreads();
+    // tiles of 64 columns; warp w takes columns (w & 1) * 32 + lane of the
+    // tile and the row quarter w >> 1, the quarters summed in shared memory
+    __shared__ double red[4][64];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = w >> 1, cl = (w & 1) * 32 + lane;
+    const int rq = (n + 3) / 4, i0 = g * rq, i1 = i0 + rq < n ? i0 + rq : n;
+    ArgMax best{-1.0, -1};
+    double* Rk = Rrows + k * m;
+    const long long ntiles = (m + 63) / 64;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long j = t * 64 + cl;
+        double dd[4] = {0, 0, 0, 0};
+        if (j < m) {
+            int i = i0;
+            for (; i + 4 <= i1; i += 4)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) dd[u] += q[i + u] * (double)A[(i + u) * m + j];
+            for (; i < i1; ++i) dd[0] += q[i] * (double)A[i * m + j];
+        }
+        red[g][cl] = (dd[0] + dd[1]) + (dd[2] + dd[3]);
+        __syncthreads();
+        if (g == 0 && j < m) {
+            double v = nu[j];
+            if (v >= 0) {
+                const double d = (red[0][cl] + red[1][cl]) + (red[2][cl] + red[3][cl]);
+                Rk[j] = d;
+                v -= d * d;
+                if (v < 0) v = 0;
+                nu[j] = v;
+                best = better(best, ArgMax{v, j});
+            }
+        }
+        __syncthreads();
+    }
+    best = block_argmax(best);
+    if (threadIdx.x == 0) part[blockIdx.x] = best;
 }
 
 // grid point of each pivot column: out[k] = sel[piv[k]] (sel null: piv[k])
@@ -316,26 +398,31 @@ __global__ void map_pivots_kernel(const int* __restrict__ piv, const int* __rest
 
 // ------------------------------------------------------ polar factor
 
-// X[k][i] = A[i][piv[k]] / |V|_F (one block)
-__global__ void polar_start_kernel(const double* __restrict__ A, int n, long long m, const int* __restrict__ piv,
-                                   double* __restrict__ X) {
+// X[k][i] = A[i][piv[k]] / |V|_F, fro = |V|_F (one block)
+template <typename T>
+__global__ void polar_start_kernel(const T* __restrict__ A, int n, long long m, const int* __restrict__ piv,
+                                   double* __restrict__ X, double* __restrict__ fro) {
     __shared__ double s_inv;
     double s = 0;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int k = e / n, i = e - k * n;
-        const double v = A[(long long)i * m + piv[k]];
+        const double v = (double)A[(long long)i * m + piv[k]];
         X[e] = v;
         s += v * v;
     }
     s = block_sum(s);
-    if (threadIdx.x == 0) s_inv = 1.0 / sqrt(s);
+    if (threadIdx.x == 0) {
+        s_inv = 1.0 / sqrt(s);
+        *fro = sqrt(s);
+    }
     __syncthreads();
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) X[e] *= s_inv;
 }
 
-// C = A op(B), n x n, op(B) = B^T when trans_b; 16 x 16 tiles
+// C = A op(B), n x n, op(B) = B^T when trans_b; 16 x 16 tiles.  err != null:
+// also *err = max(*err, max |C - I|) (non-negative doubles order as their bits)
 __global__ void dgemm_small_kernel(const double* __restrict__ A, const double* __restrict__ B, int n, int trans_b,
-                                   double* __restrict__ C) {
+                                   double* __restrict__ C, double* __restrict__ err) {
     __shared__ double As[16][17], Bs[16][17];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
@@ -351,30 +438,23 @@ __global__ void dgemm_small_kernel(const double* __restrict__ A, const double* _
         for (int k = 0; k < 16; ++k) s += As[ty][k] * Bs[k][tx];
         __syncthreads();
     }
-    if (row < n && col < n) C[(long long)row * n + col] = s;
-}
-
-// err[0] = max |T - I| (one block)
-__global__ void orth_error_kernel(const double* __restrict__ T, int n, double* __restrict__ err) {
-    __shared__ double s[kThreads];
     double e = 0;
-    for (int k = threadIdx.x; k < n * n; k += blockDim.x) {
-        const int i = k / n, j = k - i * n;
-        e = fmax(e, fabs(T[k] - (i == j ? 1.0 : 0.0)));
+    if (row < n && col < n) {
+        C[(long long)row * n + col] = s;
+        e = fabs(s - (row == col ? 1.0 : 0.0));
     }
-    s[threadIdx.x] = e;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) s[threadIdx.x] = fmax(s[threadIdx.x], s[threadIdx.x + o]);
-        __syncthreads();
+    if (err) {
+        for (int o = 16; o > 0; o >>= 1) e = fmax(e, __shfl_down_sync(0xffffffffu, e, o));
+        if ((threadIdx.x & 31) == 0)
+            atomicMax(reinterpret_cast<unsigned long long*>(err), (unsigned long long)__double_as_longlong(e));
     }
-    if (threadIdx.x == 0) err[0] = s[0];
 }
 
-// X <- 1.5 X - 0.5 Y
-__global__ void ns_combine_kernel(double* __restrict__ X, const double* __restrict__ Y, long long total) {
+// X <- a X + b Y
+__global__ void ns_combine_kernel(double* __restrict__ X, const double* __restrict__ Y, long long total, double a,
+                                  double b) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
-        X[e] = 1.5 * X[e] - 0.5 * Y[e];
+        X[e] = a * X[e] + b * Y[e];
 }
 
 int grid_for(long long items) {
@@ -426,28 +506,31 @@ cudaError_t launch_gather_columns(const R* phi, int n, long long N, const int* s
     return cudaGetLastError();
 }
 
+// blocks of the column passes: one per 64-column tile, at most 8 per SM of 152
 int scdm_qr_blocks(long long m) {
-    const long long b = (m + kThreads - 1) / kThreads;
-    return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b));  // 8 blocks of 256 per SM at most
+    const long long b = (m + 63) / 64;
+    return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
 }
 
 size_t scdm_argmax_bytes() { return sizeof(ArgMax); }
 
-cudaError_t launch_qr_init(const double* A, int n, long long m, double* nu, void* part, cudaStream_t st) {
-    qr_init_kernel<<<scdm_qr_blocks(m), kThreads, 0, st>>>(A, n, m, nu, (ArgMax*)part);
+template <typename T>
+cudaError_t launch_qr_init(const T* A, int n, long long m, double* nu, void* part, cudaStream_t st) {
+    qr_init_kernel<T><<<scdm_qr_blocks(m), kThreads, 0, st>>>(A, n, m, nu, (ArgMax*)part);
     return cudaGetLastError();
 }
 
-cudaError_t launch_qr_update(const double* A, int n, long long m, const double* qk, double* nu, void* part,
-                             cudaStream_t st) {
-    qr_update_kernel<<<scdm_qr_blocks(m), kThreads, n * sizeof(double), st>>>(A, n, m, qk, nu, (ArgMax*)part);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_qr_pick(const void* part, long long m, const double* A, int n, double* Q, int k, int* piv,
-                           double* nu, double* nu0, int* status, cudaStream_t st) {
-    qr_pick_kernel<<<1, kThreads, (size_t)(n + k + 1) * sizeof(double), st>>>(
-        (const ArgMax*)part, scdm_qr_blocks(m), A, n, m, Q, k, piv, nu, nu0, status);
+template <typename T>
+cudaError_t launch_qr_step(const T* A, int n, long long m, int k, QrWork w, cudaStream_t st) {
+    const int rb = (n + 31) / 32;
+    qr_resid_kernel<T><<<rb, kThreads, (size_t)(k + 1) * sizeof(double), st>>>(
+        (const ArgMax*)w.part, scdm_qr_blocks(m), A, n, m, w.R, w.Q, k, w.piv, w.nu, w.nu0, w.status, w.r);
+    if (k > 0) {
+        qr_dots_kernel<<<(k + 7) / 8, kThreads, 0, st>>>(w.Q, n, k, w.r, w.c);
+        qr_apply_kernel<<<rb, kThreads, (size_t)k * sizeof(double), st>>>(w.Q, n, k, w.c, w.r);
+    }
+    qr_update_kernel<T><<<scdm_qr_blocks(m), kThreads, (size_t)n * sizeof(double), st>>>(
+        A, n, m, w.r, k, w.Q, w.R, w.nu, w.rdiag, (ArgMax*)w.part);
     return cudaGetLastError();
 }
 
@@ -456,20 +539,24 @@ cudaError_t launch_map_pivots(const int* piv, const int* sel, int n, int* out, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_polar_start(const double* A, int n, long long m, const int* piv, double* X, cudaStream_t st) {
-    polar_start_kernel<<<1, kThreads, 0, st>>>(A, n, m, piv, X);
+template <typename T>
+cudaError_t launch_polar_start(const T* A, int n, long long m, const int* piv, double* X, double* fro,
+                               cudaStream_t st) {
+    polar_start_kernel<T><<<1, kThreads, 0, st>>>(A, n, m, piv, X, fro);
     return cudaGetLastError();
 }
 
-// One Newton-Schulz step X <- X (3 I - X^T X) / 2 written as 1.5 X - 0.5 (X X^T) X
-// (the same map for the polar factor of a square X); err[0] = max |X X^T - I|
-// before the step.
-cudaError_t launch_newton_schulz_step(double* X, double* T, double* Y, int n, double* err, cudaStream_t st) {
+// One scaled Newton-Schulz step X <- (alpha X) (3 I - (alpha X)^T (alpha X)) / 2,
+// written as 1.5 alpha X - 0.5 alpha^3 (X X^T) X (the same map for a square
+// X); err[0] = max |X X^T - I| before it.
+cudaError_t launch_newton_schulz_step(double* X, double* T, double* Y, int n, double alpha, double* err,
+                                      cudaStream_t st) {
     dim3 g((n + 15) / 16, (n + 15) / 16);
-    dgemm_small_kernel<<<g, 256, 0, st>>>(X, X, n, 1, T);
-    orth_error_kernel<<<1, kThreads, 0, st>>>(T, n, err);
-    dgemm_small_kernel<<<g, 256, 0, st>>>(T, X, n, 0, Y);
-    ns_combine_kernel<<<grid_for((long long)n * n), kThreads, 0, st>>>(X, Y, (long long)n * n);
+    cudaMemsetAsync(err, 0, sizeof(double), st);
+    dgemm_small_kernel<<<g, 256, 0, st>>>(X, X, n, 1, T, err);
+    dgemm_small_kernel<<<g, 256, 0, st>>>(T, X, n, 0, Y, nullptr);
+    ns_combine_kernel<<<grid_for((long long)n * n), kThreads, 0, st>>>(X, Y, (long long)n * n, 1.5 * alpha,
+                                                                       -0.5 * alpha * alpha * alpha);
     return cudaGetLastError();
 }
 
@@ -482,5 +569,13 @@ template cudaError_t launch_gather_columns<float>(const float*, int, long long, 
                                                   cudaStream_t);
 template cudaError_t launch_gather_columns<double>(const double*, int, long long, const int*, long long, double*,
                                                    cudaStream_t);
+template cudaError_t launch_qr_init<float>(const float*, int, long long, double*, void*, cudaStream_t);
+template cudaError_t launch_qr_init<double>(const double*, int, long long, double*, void*, cudaStream_t);
+template cudaError_t launch_qr_step<float>(const float*, int, long long, int, QrWork, cudaStream_t);
+template cudaError_t launch_qr_step<double>(const double*, int, long long, int, QrWork, cudaStream_t);
+template cudaError_t launch_polar_start<float>(const float*, int, long long, const int*, double*, double*,
+                                               cudaStream_t);
+template cudaError_t launch_polar_start<double>(const double*, int, long long, const int*, double*, double*,
+                                                cudaStream_t);
 
 }  // namespace ace
