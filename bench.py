@@ -395,6 +395,34 @@ def run_ours(args):
         s_mtace["mts_inner_apply_ms"] = min(ts_)
         s_mtace["mts_exact_over_inner"] = ms_per_step / min(ts_)
         del Kp
+        # s'-MTACE (Sections 2.4-2.5): SCDM localisation with the density /
+        # gradient pre-selection, then the overlap screen and the screened
+        # build on the localised orbitals -- the whole outer step
+        phi = torch.empty_like(psi)
+        ace.ace_scdm(plan, psi, phi_G=phi)
+        sc = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, piv, _, ncand = ace.ace_scdm(plan, psi, phi_G=phi)  # synchronous call: host wall time
+            sc.append((time.perf_counter() - t0) * 1e3)
+        pairs_l, _ = ace.ace_overlap_screen(plan, phi, rho_cut)
+        xs = torch.empty_like(psi)
+        ace.ace_build(plan, phi, cfg["alpha"], pairs=pairs_l, xi=xs)
+        sb = []
+        for _ in range(2):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, E_l = ace.ace_build(plan, phi, cfg["alpha"], pairs=pairs_l, xi=xs)
+            b.record()
+            torch.cuda.synchronize()
+            sb.append(a.elapsed_time(b))
+        s_mtace["s_prime"] = {"scdm_ms": min(sc), "candidate_points": ncand, "grid_points": int(np.prod(cfg["grid"])),
+                              "pairs_kept": int(pairs_l[0][-1]), "screened_build_ms": min(sb),
+                              "outer_step_ms": min(sc) + ov_ms + min(sb), "E_x": E_l,
+                              "dE_x_per_atom_vs_all_pairs": abs(E_l - E_mixed) / cfg["n_atom"]}
+        del xs, phi
 
     # ---- the same step replayed from a CUDA graph (build + apply captured once),
     # and on the small 8-orbital / 32^3 case, where launches dominate
@@ -546,6 +574,28 @@ def profile_overlap(n_occ, reps=3):
     print(json.dumps({"profile_overlap": n_occ, "pairs_kept": int(pairs[0][-1]), "ms": ms}))
 
 
+def profile_scdm(which, reps=2):
+    """SCDM localisation with the s'-MTACE pre-selection (Sections 2.4-2.5) on
+    the 128 water-box orbitals on 96^3 ("water32") or the 512 localised
+    orbitals on 160^3 ("localized"): the kernels the SCDM launch lists under
+    profiles/ cover (the first call allocates, the last is the one to read)."""
+    import torch
+
+    import gen
+    import paper_2110_07670_gb300 as ace
+    cfg = gen.config_water32() if which == "water32" else gen.config_localized()
+    n = len(cfg["psi"])
+    plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, "mixed", pair_variant=1)
+    d = torch.from_numpy(cfg["psi"].astype(np.complex64)).cuda()
+    phi = torch.empty_like(d)
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, piv, _, ncand = ace.ace_scdm(plan, d, phi_G=phi)
+        ms = (time.perf_counter() - t0) * 1e3
+    print(json.dumps({"profile_scdm": which, "n_occ": n, "grid": list(cfg["grid"]), "candidates": ncand, "ms": ms}))
+
+
 def profile_apply(T, reps=3):
     """ACE applies on T random trials with 256 random ACE vectors in the
     120^3 / 23.5-bohr / 80 Ry basis (78398 plane waves): the tensor-core Gram
@@ -590,12 +640,17 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0, help="run one small build with this many orbitals")
     ap.add_argument("--profile-apply", type=int, default=0, help="run ACE applies on this many trial vectors")
     ap.add_argument("--profile-overlap", type=int, default=0, help="run the overlap screen on this many orbitals")
+    ap.add_argument("--profile-scdm", default=None, choices=["water32", "localized"],
+                    help="run SCDM localisation on this workload")
     ap.add_argument("--pair-variant", type=int, default=None,
                     help="pair-pass kernels (1-4); default: autotuned, and 1 for --profile-case")
     ap.add_argument("--pair-streams", type=int, default=1, help="pair streams of --profile-case")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args.profile_case, pair_variant=args.pair_variant or 1, pair_streams=args.pair_streams)
+        return
+    if args.profile_scdm:
+        profile_scdm(args.profile_scdm)
         return
     if args.profile_overlap:
         profile_overlap(args.profile_overlap)

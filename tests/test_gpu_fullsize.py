@@ -176,3 +176,32 @@ def test_overlap_screen_water32_grid():
     pairs, S = ace.ace_overlap_screen(plan, torch.from_numpy(psi.astype(np.complex64)).cuda(), 2.5e-2)
     assert np.abs(S - S_ref).max() <= 2e-5
     plan.close()
+
+
+def test_scdm_water32_full_size():
+    """SCDM with the s' pre-selection on the 128 water-box orbitals, 96^3:
+    the rotation is orthogonal, the localised orbitals are orthonormal and
+    span the occupied space, the pivots are distinct grid points, and the
+    unscreened exchange energy is unchanged (E_x is invariant under the
+    rotation)."""
+    global _WATER32
+    if _WATER32 is None:
+        _WATER32 = gen.config_water32()
+    cfg = _WATER32
+    n = len(cfg["psi"])
+    plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, "mixed")
+    psi = dev(cfg["psi"], plan)
+    phi, piv, O, nc = ace.ace_scdm(plan, psi)
+    N = int(np.prod(cfg["grid"]))
+    assert n <= nc < N and len(set(piv.tolist())) == n and piv.min() >= 0 and piv.max() < N
+    assert np.abs(O @ O.T - np.eye(n)).max() < 1e-12
+    m = oracle.half_sphere(cfg["cell"], cfg["ecut"])
+    P = host(phi)
+    assert np.abs(oracle.gamma_gram(P, P, m) - np.eye(n)).max() < 1e-5
+    S = oracle.gamma_gram(cfg["psi"], P, m)
+    assert np.abs(S @ S.T - np.eye(n)).max() < 1e-5
+    assert np.abs(P - O @ cfg["psi"]).max() < 1e-5 * np.abs(P).max()
+    _, E_psi = ace.ace_build(plan, psi, cfg["alpha"])
+    _, E_phi = ace.ace_build(plan, phi, cfg["alpha"])
+    assert abs(E_phi - E_psi) / cfg["n_atom"] <= 1e-6
+    plan.close()
