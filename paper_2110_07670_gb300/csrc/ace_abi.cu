@@ -598,6 +598,17 @@ int check_gamma(ace_plan* P, const void* psi, int n, cudaStream_t st) {
 // The quads go through the plan's pinned staging buffer (a captured copy
 // reads it when the graph runs).  Outside capture, the previous upload from it
 // is waited for before it is rewritten.
+// The quads of a call that is never captured (exact exchange, overlap screen,
+// SCDM): copied from pageable memory (the copy has taken the data when it
+// returns), leaving the pinned staging buffer, which a captured build's
+// replays read, to the builds.
+int upload_quads_eager(ace_plan* P, const std::vector<Quad>& q, cudaStream_t st) {
+    if (g_capture) return fail(ACE_ERR_INVALID_ARG, "this call cannot be captured");
+    ACE_TRY(grow(&P->d_quads, &P->quads_cap, q.size()));
+    ACE_CK(cudaMemcpyAsync(P->d_quads, q.data(), q.size() * sizeof(Quad), cudaMemcpyHostToDevice, st));
+    return ACE_OK;
+}
+
 int upload_quads(ace_plan* P, const std::vector<Quad>& q, cudaStream_t st) {
     ACE_TRY(grow(&P->d_quads, &P->quads_cap, q.size()));
     if (!P->quads_ev) ACE_CK(cudaEventCreateWithFlags(&P->quads_ev, cudaEventDisableTiming));
@@ -748,7 +759,7 @@ int hfx_impl(ace_plan* P, const void* psi_occ, int n_occ, double alpha, const vo
         }
     pack_pairs(pa, pb, q);
     const int no = (int)oq.size(), nt = (int)tq.size(), np = (int)q.size() - no - nt;
-    ACE_TRY(upload_quads(P, q, st));
+    ACE_TRY(upload_quads_eager(P, q, st));
     size_t tcap_elems = P->t_cap;
     void* tphi = P->d_tphi;
     if ((size_t)T * P->N > tcap_elems) {
@@ -782,7 +793,7 @@ int overlap_impl(ace_plan* P, const void* psi_G, int n, double rho_cut, int32_t*
                  double* S_out, cudaStream_t st) {
     ACE_TRY(check_gamma<R>(P, psi_G, n, st));
     std::vector<Quad> oq = orbital_quads(n);
-    ACE_TRY(upload_quads(P, oq, st));
+    ACE_TRY(upload_quads_eager(P, oq, st));
     R* phi = (R*)P->d_phi;
     ACE_TRY(run_to_real<R>(P, (const cx<R>*)psi_G, P->d_quads, (int)oq.size(), phi, st));
     const long long K = P->N;
@@ -842,7 +853,7 @@ int scdm_impl(ace_plan* P, const void* psi_G, int n, int preselect, void* phi_G,
     const long long N = P->N;
     const int npw = P->npw;
     std::vector<Quad> oq = orbital_quads(n);
-    ACE_TRY(upload_quads(P, oq, st));
+    ACE_TRY(upload_quads_eager(P, oq, st));
     R* phi = (R*)P->d_phi;
     ACE_TRY(run_to_real<R>(P, (const cx<R>*)psi_G, P->d_quads, (int)oq.size(), phi, st));
     long long m = N;

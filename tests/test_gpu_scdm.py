@@ -151,3 +151,31 @@ def test_scdm_rejections():
     dup = dev(np.concatenate([s["psi"][:4], s["psi"][:4]]), plan)
     with pytest.raises(ace.AceError):
         ace.ace_scdm(plan, dup, preselect=False)  # rank 4 < 8
+
+
+def test_graph_replay_unaffected_by_scdm_overlap_and_exact_exchange():
+    """A captured build replays the pair list of its capture even after SCDM,
+    the overlap screen and the exact exchange ran eagerly on the plan with an
+    odd orbital count (their quads differ from the build's)."""
+    s = gen.config_small()
+    n = len(s["psi"])
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "mixed")
+    psi = dev(s["psi"], plan)
+    xi = torch.empty_like(psi)
+    ace.ace_build_async(plan, psi, s["alpha"], xi=xi)
+    ace.ace_build_result(plan)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ace.ace_build_async(plan, psi, s["alpha"], xi=xi)
+    g.replay()
+    E0 = ace.ace_build_result(plan)
+    five = dev(s["psi"][:5], plan)
+    ace.ace_scdm(plan, five)
+    ace.ace_overlap_screen(plan, five, 0.1)
+    ace.hfx_apply_exact(plan, five, s["alpha"], dev(gen.random_trials(s["cell"], s["ecut"], 3, seed=8), plan))
+    g.replay()
+    assert abs(ace.ace_build_result(plan) - E0) <= 1e-10 * abs(E0)
+    ref = oracle.ace_build(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
+    assert abs(E0 - ref["E_x"]) / s["n_atom"] <= 1e-6
+    del g
+    plan.close()
