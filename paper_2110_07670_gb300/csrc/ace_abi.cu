@@ -114,7 +114,7 @@ struct ace_plan {
         char* dpsi = nullptr;     // derivative coefficients [n][npw] complex (plan precision)
         double* dens = nullptr;   // rho [N], grad rho [3][N], then the stats partials and means
         int* isel = nullptr;      // block counts, offsets, candidate grid points
-        char* A = nullptr;        // candidate columns [n][m], double
+        char* A = nullptr;        // candidate columns [n][m] (plan precision)
         double* nu = nullptr;     // residual norms [m], then the QR coefficients [n][m]
         char* part = nullptr;     // argmax partials
         double* mats = nullptr;   // Q, X, T, Y [n][n] each, err, nu0, r [n], c [n]
@@ -898,20 +898,20 @@ int scdm_impl(ace_plan* P, const void* psi_G, int n, int preselect, void* phi_G,
     }
     // column-pivoted QR of the candidate columns: n steps, each a pass over A
     const int qb = scdm_qr_blocks(m);
-    ACE_TRY(grow(&W.A, &W.c_A, (size_t)n * m * sizeof(double)));
+    ACE_TRY(grow(&W.A, &W.c_A, (size_t)n * m * sizeof(R)));
     ACE_TRY(grow(&W.nu, &W.c_nu, (size_t)m + (size_t)n * m));
     ACE_TRY(grow(&W.part, &W.c_part, (size_t)qb * scdm_argmax_bytes()));
     ACE_TRY(grow(&W.mats, &W.c_mats, (size_t)4 * n * n + 3 * n + 3));
     ACE_TRY(grow(&W.ipiv, &W.c_ipiv, (size_t)2 * n + 1));
-    double* A = (double*)W.A;
+    R* A = (R*)W.A;
     double *Q = W.mats, *X = Q + (size_t)n * n, *T = X + (size_t)n * n, *Y = T + (size_t)n * n, *err = Y + (size_t)n * n;
     int *piv = W.ipiv, *status = W.ipiv + n;  // piv: columns of A; grid points after them
     double *rdiag = err + 2 + 2 * n, *fro = rdiag + n;  // after err, nu0, r, c; fro right after rdiag
     const QrWork qw{W.part, W.nu, W.nu + m, Q, err + 2, err + 2 + n, err + 1, rdiag, piv, status};
     ACE_CK(cudaMemsetAsync(status, 0, sizeof(int), st));
     ACE_CKL(launch_gather_columns<R>(phi, n, N, sel, m, A, st));
-    ACE_CKL(launch_qr_init<double>(A, n, m, W.nu, W.part, st));
-    for (int k = 0; k < n; ++k) ACE_CKL(launch_qr_step<double>(A, n, m, k, qw, st));
+    ACE_CKL(launch_qr_init<R>(A, n, m, W.nu, W.part, st));
+    for (int k = 0; k < n; ++k) ACE_CKL(launch_qr_step<R>(A, n, m, k, qw, st));
     int h_status = 0;
     ACE_CK(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     ACE_CK(cudaStreamSynchronize(st));
@@ -921,7 +921,7 @@ int scdm_impl(ace_plan* P, const void* psi_G, int n, int preselect, void* phi_G,
     // from above, by min_k R[k][k] / |V|_F (an over-estimate only makes a
     // step less aggressive), and follows its image under each step.  Until
     // X X^T = I to 1e-10; the step after that leaves rounding only.
-    ACE_CKL(launch_polar_start<double>(A, n, m, piv, X, fro, st));
+    ACE_CKL(launch_polar_start<R>(A, n, m, piv, X, fro, st));
     std::vector<double> hd((size_t)n + 1);
     ACE_CK(cudaMemcpyAsync(hd.data(), rdiag, ((size_t)n + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
     ACE_CK(cudaStreamSynchronize(st));

@@ -210,9 +210,9 @@ cudaError_t launch_scdm_stats(const double* rho, const double* grad, long long N
 int scdm_select_blocks(long long N);
 cudaError_t launch_scdm_select(const double* rho, const double* grad, long long N, const double* means, int* counts,
                                int* offsets, int* sel, cudaStream_t st);
-// A[i][s] = phi_i(r_s) in double, r_s = sel[s] (sel null: s), A [n][m]
+// A[i][s] = phi_i(r_s), r_s = sel[s] (sel null: s), A [n][m] in the orbitals' precision
 template <typename R>
-cudaError_t launch_gather_columns(const R* phi, int n, long long N, const int* sel, long long m, double* A,
+cudaError_t launch_gather_columns(const R* phi, int n, long long N, const int* sel, long long m, R* A,
                                   cudaStream_t st);
 // Column-pivoted QR of A [n][m] by Gram-Schmidt applied twice, all products in
 // double: launch_qr_init, then launch_qr_step for k = 0 .. n-1 (step k picks

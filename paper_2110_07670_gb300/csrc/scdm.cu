@@ -201,15 +201,16 @@ __global__ void select_scatter_kernel(const double* __restrict__ rho, const doub
     if (f) sel[offsets[blockIdx.x] + before + __popc(bal & ((1u << l) - 1u))] = (int)r;
 }
 
-// A[i][s] = phi_i(r_s) in double, r_s = sel[s] (sel == nullptr: r_s = s):
-// converted once here, since a conversion in the QR passes would cost as much
-// of the double-precision pipe as the products themselves
+// A[i][s] = phi_i(r_s), r_s = sel[s] (sel == nullptr: r_s = s), in the
+// orbitals' precision (the QR update reads single-precision values through
+// float-float arithmetic; a float -> double conversion per product would cost
+// the double-precision pipe as much as the product)
 template <typename R>
 __global__ void gather_columns_kernel(const R* __restrict__ phi, long long N, const int* __restrict__ sel,
-                                      long long m, double* __restrict__ A) {
+                                      long long m, R* __restrict__ A) {
     const int i = blockIdx.y;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < m; s += (long long)gridDim.x * blockDim.x)
-        A[i * m + s] = (double)phi[i * N + (sel ? sel[s] : s)];
+        A[i * m + s] = phi[i * N + (sel ? sel[s] : s)];
 }
 
 // ------------------------------------------------------ column-pivoted QR
@@ -328,12 +329,33 @@ __global__ void qr_apply_kernel(const double* __restrict__ Q, int n, int k, cons
     rows_reduce8(s, i < n ? r[i] : 0.0, r, i, n);
 }
 
-// (3): every block normalises r itself; block 0 stores q_k and |r| = R[k][k]
+// Dot product of q (double, split as qh + ql in float) with a column of
+// single-precision values, in float-float arithmetic on the FP32 pipes: each
+// qh a exactly as a product and its error (fmaf), ql a rounded, the running
+// sum kept as an unevaluated pair (TwoSum); relative accuracy about 2^-48 of
+// sum |q_i a_i|, against 2^-53 in double at a fraction of the cost on GB300.
+// (The _rn intrinsics keep the rounded steps from being contracted into
+// fused multiply-adds, which would break the error-free transformations.)
+__device__ __forceinline__ void ff_dot_acc(float qh, float ql, float a, float& sh, float& sl) {
+    const float p = __fmul_rn(qh, a);
+    float e = fmaf(qh, a, -p);  // qh a - p, exactly
+    e = fmaf(ql, a, e);
+    const float s = __fadd_rn(sh, p), bb = __fsub_rn(s, sh);
+    const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));  // sh + p - s, exactly
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+    sh = s;
+}
+
+// (3): every block normalises r itself; block 0 stores q_k and |r| = R[k][k].
+// Double candidate columns: the dots in double; single-precision ones (exact
+// in float): in float-float (ff_dot_acc).
 template <typename T>
 __global__ void qr_update_kernel(const T* __restrict__ A, int n, long long m, const double* __restrict__ r, int k,
                                  double* __restrict__ Q, double* __restrict__ Rrows, double* __restrict__ nu,
                                  double* __restrict__ rdiag, ArgMax* __restrict__ part) {
     extern __shared__ double q[];
+    float* qh = reinterpret_cast<float*>(q + n);  // float-float split of q (single precision A)
+    float* ql = qh + n;
     __shared__ double s_inv;
     double ss = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -350,6 +372,10 @@ __global__ void qr_update_kernel(const T* __restrict__ A, int n, long long m, co
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         q[i] *= s_inv;
         if (blockIdx.x == 0) Q[(long long)k * n + i] = q[i];
+        if constexpr (sizeof(T) == 4) {
+            qh[i] = (float)q[i];
+            ql[i] = (float)(q[i] - (double)qh[i]);
+        }
     }
     __syncthreads();
     // tiles of 64 columns; warp w takes columns (w & 1) * 32 + lane of the
@@ -362,15 +388,28 @@ __global__ void qr_update_kernel(const T* __restrict__ A, int n, long long m, co
     const long long ntiles = (m + 63) / 64;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const long long j = t * 64 + cl;
-        double dd[4] = {0, 0, 0, 0};
+        double part_sum = 0;
         if (j < m) {
-            int i = i0;
-            for (; i + 4 <= i1; i += 4)
+            if constexpr (sizeof(T) == 4) {
+                float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
+                int i = i0;
+                for (; i + 2 <= i1; i += 2) {
+                    ff_dot_acc(qh[i], ql[i], (float)A[i * m + j], sh[0], sl[0]);
+                    ff_dot_acc(qh[i + 1], ql[i + 1], (float)A[(i + 1) * m + j], sh[1], sl[1]);
+                }
+                if (i < i1) ff_dot_acc(qh[i], ql[i], (float)A[i * m + j], sh[0], sl[0]);
+                part_sum = ((double)sh[0] + (double)sl[0]) + ((double)sh[1] + (double)sl[1]);
+            } else {
+                double dd[4] = {0, 0, 0, 0};
+                int i = i0;
+                for (; i + 4 <= i1; i += 4)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) dd[u] += q[i + u] * (double)A[(i + u) * m + j];
-            for (; i < i1; ++i) dd[0] += q[i] * (double)A[i * m + j];
+                    for (int u = 0; u < 4; ++u) dd[u] += q[i + u] * (double)A[(i + u) * m + j];
+                for (; i < i1; ++i) dd[0] += q[i] * (double)A[i * m + j];
+                part_sum = (dd[0] + dd[1]) + (dd[2] + dd[3]);
+            }
         }
-        red[g][cl] = (dd[0] + dd[1]) + (dd[2] + dd[3]);
+        red[g][cl] = part_sum;
         __syncthreads();
         if (g == 0 && j < m) {
             double v = nu[j];
@@ -499,7 +538,7 @@ cudaError_t launch_scdm_select(const double* rho, const double* grad, long long 
 }
 
 template <typename R>
-cudaError_t launch_gather_columns(const R* phi, int n, long long N, const int* sel, long long m, double* A,
+cudaError_t launch_gather_columns(const R* phi, int n, long long N, const int* sel, long long m, R* A,
                                   cudaStream_t st) {
     dim3 grid((unsigned)std::min<long long>((m + kThreads - 1) / kThreads, 1024), (unsigned)n);
     gather_columns_kernel<R><<<grid, kThreads, 0, st>>>(phi, N, sel, m, A);
@@ -529,7 +568,7 @@ cudaError_t launch_qr_step(const T* A, int n, long long m, int k, QrWork w, cuda
         qr_dots_kernel<<<(k + 7) / 8, kThreads, 0, st>>>(w.Q, n, k, w.r, w.c);
         qr_apply_kernel<<<rb, kThreads, (size_t)k * sizeof(double), st>>>(w.Q, n, k, w.c, w.r);
     }
-    qr_update_kernel<T><<<scdm_qr_blocks(m), kThreads, (size_t)n * sizeof(double), st>>>(
+    qr_update_kernel<T><<<scdm_qr_blocks(m), kThreads, (size_t)n * (sizeof(double) + 2 * sizeof(float)), st>>>(
         A, n, m, w.r, k, w.Q, w.R, w.nu, w.rdiag, (ArgMax*)w.part);
     return cudaGetLastError();
 }
@@ -565,7 +604,7 @@ template cudaError_t launch_deriv_coeffs<double>(const cx<double>*, int, int, co
                                                  cudaStream_t);
 template cudaError_t launch_orbital_sum<float>(const float*, const float*, int, long long, double*, cudaStream_t);
 template cudaError_t launch_orbital_sum<double>(const double*, const double*, int, long long, double*, cudaStream_t);
-template cudaError_t launch_gather_columns<float>(const float*, int, long long, const int*, long long, double*,
+template cudaError_t launch_gather_columns<float>(const float*, int, long long, const int*, long long, float*,
                                                   cudaStream_t);
 template cudaError_t launch_gather_columns<double>(const double*, int, long long, const int*, long long, double*,
                                                    cudaStream_t);
