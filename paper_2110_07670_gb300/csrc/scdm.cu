@@ -234,6 +234,22 @@ __device__ __forceinline__ void rows_reduce8(double part, double base, double* r
     }
 }
 
+// sum over l = g, g + 8, ... < k of c[l] Q[l][i], four loads in flight
+__device__ __forceinline__ double strided_dot8(const double* c, const double* __restrict__ Q, int n, int i, int g,
+                                               int k) {
+    double s[4] = {0, 0, 0, 0};
+    int l = g;
+    for (; l + 24 < k; l += 32) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = Q[(long long)(l + 8 * u) * n + i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] += c[l + 8 * u] * v[u];
+    }
+    for (; l < k; l += 8) s[0] += c[l] * Q[(long long)l * n + i];
+    return (s[0] + s[1]) + (s[2] + s[3]);
+}
+
 // nu[j] = |a_j|^2 and the block's largest
 template <typename T>
 __global__ void qr_init_kernel(const T* __restrict__ A, int n, long long m, double* __restrict__ nu,
@@ -299,10 +315,7 @@ __global__ void qr_resid_kernel(const ArgMax* __restrict__ part, int nparts, con
     }
     for (int l = threadIdx.x; l < k; l += blockDim.x) rp[l] = Rrows[l * m + p];
     __syncthreads();
-    double s = 0;
-    if (i < n)
-        for (int l = g; l < k; l += 8) s += rp[l] * Q[(long long)l * n + i];
-    rows_reduce8(s, i < n ? (double)A[i * m + p] : 0.0, r, i, n);
+    rows_reduce8(i < n ? strided_dot8(rp, Q, n, i, g, k) : 0.0, i < n ? (double)A[i * m + p] : 0.0, r, i, n);
 }
 
 // second Gram-Schmidt pass, part 1: c_l = q_l . r, one warp per l
@@ -310,10 +323,15 @@ __global__ void qr_dots_kernel(const double* __restrict__ Q, int n, int k, const
                                double* __restrict__ c) {
     const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (l >= k) return;
-    double s = 0;
-    for (int i = lane; i < n; i += 32) s += Q[(long long)l * n + i] * r[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) c[l] = s;
+    double s[4] = {0, 0, 0, 0};
+    int i = lane;
+    for (; i + 96 < n; i += 128)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] += Q[(long long)l * n + i + 32 * u] * r[i + 32 * u];
+    for (; i < n; i += 32) s[0] += Q[(long long)l * n + i] * r[i];
+    double t = (s[0] + s[1]) + (s[2] + s[3]);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) c[l] = t;
 }
 
 // part 2: r_i -= sum_l c_l q_l[i]
@@ -323,10 +341,7 @@ __global__ void qr_apply_kernel(const double* __restrict__ Q, int n, int k, cons
     for (int l = threadIdx.x; l < k; l += blockDim.x) cs[l] = c[l];
     __syncthreads();
     const int i = blockIdx.x * 32 + (threadIdx.x & 31), g = threadIdx.x >> 5;
-    double s = 0;
-    if (i < n)
-        for (int l = g; l < k; l += 8) s += cs[l] * Q[(long long)l * n + i];
-    rows_reduce8(s, i < n ? r[i] : 0.0, r, i, n);
+    rows_reduce8(i < n ? strided_dot8(cs, Q, n, i, g, k) : 0.0, i < n ? r[i] : 0.0, r, i, n);
 }
 
 // Dot product of q (double, split as qh + ql in float) with a column of
@@ -390,21 +405,29 @@ __global__ void qr_update_kernel(const T* __restrict__ A, int n, long long m, co
         const long long j = t * 64 + cl;
         double part_sum = 0;
         if (j < m) {
+            // eight loads in flight per thread before their products
             if constexpr (sizeof(T) == 4) {
                 float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
                 int i = i0;
-                for (; i + 2 <= i1; i += 2) {
-                    ff_dot_acc(qh[i], ql[i], (float)A[i * m + j], sh[0], sl[0]);
-                    ff_dot_acc(qh[i + 1], ql[i + 1], (float)A[(i + 1) * m + j], sh[1], sl[1]);
+                for (; i + 8 <= i1; i += 8) {
+                    float v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = (float)A[(i + u) * m + j];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) ff_dot_acc(qh[i + u], ql[i + u], v[u], sh[u & 1], sl[u & 1]);
                 }
-                if (i < i1) ff_dot_acc(qh[i], ql[i], (float)A[i * m + j], sh[0], sl[0]);
+                for (; i < i1; ++i) ff_dot_acc(qh[i], ql[i], (float)A[i * m + j], sh[0], sl[0]);
                 part_sum = ((double)sh[0] + (double)sl[0]) + ((double)sh[1] + (double)sl[1]);
             } else {
                 double dd[4] = {0, 0, 0, 0};
                 int i = i0;
-                for (; i + 4 <= i1; i += 4)
+                for (; i + 8 <= i1; i += 8) {
+                    double v[8];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) dd[u] += q[i + u] * (double)A[(i + u) * m + j];
+                    for (int u = 0; u < 8; ++u) v[u] = (double)A[(i + u) * m + j];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) dd[u & 3] += q[i + u] * v[u];
+                }
                 for (; i < i1; ++i) dd[0] += q[i] * (double)A[i * m + j];
                 part_sum = (dd[0] + dd[1]) + (dd[2] + dd[3]);
             }
