@@ -11,7 +11,11 @@ forces here, the exchange energy plays the role of the force:
     dE(k)      = E_exact(k) - E_ACE(k)               (the slow correction)
 
 K_0 equals alpha V_X on span(Phi_0), so dE(0) = 0, and dE grows with the
-orbitals' drift.  Every step runs through the library's C ABI.
+orbitals' drift.  With rho_cut set, the outer step is the s'-MTACE one
+(Sections 2.4-2.5): SCDM localisation of Phi_0 with the density / gradient
+pre-selection, the overlap screen S_ij >= rho_cut on the localised orbitals,
+and K_0 built from the screened pairs only; dE(0) is then the screening
+error.  Every step runs through the library's C ABI.
 """
 import time
 
@@ -26,11 +30,12 @@ def gamma_energy(psi, Kpsi):
     return float(2.0 * np.real(np.sum(np.conj(psi) * Kpsi)) - np.real(np.sum(np.conj(psi[:, 0]) * Kpsi[:, 0])))
 
 
-def run(plan, phi0, alpha, orbitals_at, n_inner, every=1):
+def run(plan, phi0, alpha, orbitals_at, n_inner, every=1, rho_cut=None):
     """Outer build on phi0, then inner steps k = 1..n_inner on orbitals_at(k)
     (host arrays [n_occ][n_pw_half], Gamma-symmetric, orthonormal).  Returns a
     list of per-step records: k, E_ACE, and every `every` steps E_exact and dE,
-    with the device time of each part."""
+    with the device time of each part.  rho_cut: build K_0 the s'-MTACE way
+    (record 0 then also carries the SCDM pivots and the kept pair list)."""
     import torch
 
     import paper_2110_07670_gb300 as ace
@@ -38,9 +43,21 @@ def run(plan, phi0, alpha, orbitals_at, n_inner, every=1):
     dt = np.complex64 if plan.prec == ace.ACE_MIXED else np.complex128
     d0 = torch.from_numpy(np.ascontiguousarray(phi0.astype(dt))).cuda()
     t0 = time.perf_counter()
-    xi, E0 = ace.ace_build(plan, d0, alpha)
-    torch.cuda.synchronize()
-    out = [{"k": 0, "E_ACE": E0, "E_exact": E0, "dE": 0.0, "build_s": time.perf_counter() - t0}]
+    if rho_cut is None:
+        xi, E0 = ace.ace_build(plan, d0, alpha)
+        torch.cuda.synchronize()
+        out = [{"k": 0, "E_ACE": E0, "E_exact": E0, "dE": 0.0, "build_s": time.perf_counter() - t0}]
+    else:
+        loc, piv, _, _ = ace.ace_scdm(plan, d0)
+        pairs, _ = ace.ace_overlap_screen(plan, loc, rho_cut)
+        xi, _ = ace.ace_build(plan, loc, alpha, pairs=pairs)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        E0 = gamma_energy(phi0, ace.ace_apply(plan, xi, d0).cpu().numpy().astype(np.complex128))
+        _, E_ex = ace.ace_build(plan, d0, alpha, xi=torch.empty_like(d0))
+        torch.cuda.synchronize()
+        out = [{"k": 0, "E_ACE": E0, "E_exact": E_ex, "dE": E_ex - E0, "build_s": t_build, "pivots": piv,
+                "pairs": pairs}]
     W = torch.empty_like(d0)
     for k in range(1, n_inner + 1):
         phik = orbitals_at(k)

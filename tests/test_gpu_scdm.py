@@ -179,3 +179,33 @@ def test_graph_replay_unaffected_by_scdm_overlap_and_exact_exchange():
     assert abs(E0 - ref["E_x"]) / s["n_atom"] <= 1e-6
     del g
     plan.close()
+
+
+def test_s_prime_mts_harness_matches_oracle():
+    """The MTS loop with s'-MTACE outer steps (FP64): SCDM, the overlap screen
+    and the screened build on Phi_0, then inner steps on drifting orbitals --
+    pivots, the kept pairs and every step's energies against the oracle."""
+    from paper_2110_07670_gb300 import mts
+    s = gen.config_small()
+    n = len(s["psi"])
+    D = gen.random_orbitals(s["cell"], s["ecut"], n, seed=33)
+    at = lambda k: mts.drifted_orbitals(s["psi"], D, 0.02, k)
+    loc = oscdm.scdm(s["psi"], s["cell"], s["grid"], s["ecut"])
+    S = oracle.overlap(loc["phi_G"], s["cell"], s["grid"], s["ecut"])
+    cut = float(np.median(S[np.triu_indices(n, 1)]))
+    assert np.abs(S - cut).min() > 1e-9 * cut  # no pair within rounding of the cut
+    pairs = oracle.screened_pairs(S, cut)
+    ref = oracle.ace_build(loc["phi_G"], s["cell"], s["grid"], s["ecut"], s["alpha"], pairs=pairs)
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "fp64")
+    rec = mts.run(plan, s["psi"], s["alpha"], at, n_inner=2, every=1, rho_cut=cut)
+    plan.close()
+    assert np.array_equal(rec[0]["pivots"], loc["pivots"])
+    assert all(np.array_equal(a, b) for a, b in zip(rec[0]["pairs"], pairs))
+    for r in rec:
+        phik = at(r["k"]) if r["k"] else s["psi"]
+        E_ace = mts.gamma_energy(phik, oracle.ace_apply(ref["xi"], phik, ref["miller"]))
+        E_ex = oracle.exchange(phik, s["cell"], s["grid"], s["ecut"], s["alpha"])[1]
+        assert abs(r["E_ACE"] - E_ace) <= 1e-10 * abs(E_ex)
+        assert abs(r["E_exact"] - E_ex) <= 1e-10 * abs(E_ex)
+        assert abs(r["dE"] - (E_ex - E_ace)) <= 2e-10 * abs(E_ex)
+    assert abs(rec[0]["dE"]) > 1e-6  # the screening error
