@@ -152,3 +152,19 @@ def test_scdm_keeps_exchange_energy(small):
     _, E0 = oracle.exchange(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
     _, E1 = oracle.exchange(r["phi_G"], s["cell"], s["grid"], s["ecut"], s["alpha"])
     assert abs(E0 - E1) < 1e-12 * abs(E0)
+
+
+def test_scdm_without_preselection_matches_lapack_and_polar():
+    """Every grid point a candidate: the pivots are LAPACK's pivoted-QR pivots
+    of the n x N matrix of orbital values, and O is the orthogonal polar factor
+    of V (scipy.linalg.polar: V = O P, and also (V V^T)^{1/2} O)."""
+    s = gen.config_small()
+    psi = s["psi"][:5]
+    r = oscdm.scdm(psi, s["cell"], s["grid"], s["ecut"], use_preselect=False)
+    A = oracle.to_real(psi, s["cell"], s["grid"], s["ecut"]).reshape(len(psi), -1)
+    _, _, perm = scipy.linalg.qr(A, pivoting=True, mode="economic")
+    assert np.array_equal(r["pivots"], perm[:len(psi)])
+    V = A[:, r["pivots"]].T
+    U, _ = scipy.linalg.polar(V)
+    assert np.abs(r["O"] - U).max() < 1e-12
+    assert np.abs(r["phi_G"] - U @ psi).max() < 1e-12
