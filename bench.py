@@ -19,6 +19,7 @@ clocks sampled during the timed region.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -336,6 +337,19 @@ def run_ours(args):
                 "algorithmic_bytes_per_build": pipe_bytes, "pair_wall_ms_per_build": pair_wall,
                 "share_of_step": pair_wall / max(stats["total_ms"] / args.steps, 1e-9),
                 "per_pass_alone": per_pass}
+    # ALU view of the same passes (the FFT/pair path is near the FP32 ridge,
+    # about 6 flops per algorithmic byte): the FFT flops of every packed
+    # transform -- a forward and an inverse 3D complex FFT of N points, 5 N
+    # log2 N flops each, the usual count -- over the pair wall time, against
+    # the FP32 peak of SMs x 128 lanes x 2 flops x the highest SM clock seen
+    fft_flops = 2 * 5.0 * N * math.log2(N) * (stats["pair_transforms"] / args.steps)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    alu_tflops = fft_flops / (pair_wall / 1e3) / 1e12 if pair_wall > 0 else 0.0
+    roofline["alu"] = {"flops_per_build": fft_flops, "achieved_tflops": alu_tflops, "peak_tflops_fp32": fp32_peak,
+                       "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
+                       "frac": alu_tflops / fp32_peak if fp32_peak > 0 else 0.0}
     # the dominant kernel live: its launches' CUDA-event durations on the
     # stream that ran them, in the timed steps (with two streams each launch
     # shares the GPU with the other stream's passes)
