@@ -62,6 +62,8 @@ def _load():
             fn.restype = ctypes.c_int if name != "orc_fft3d" else None
         lib.orc_set_coulomb_cutoff.argtypes = [f64]
         lib.orc_set_coulomb_cutoff.restype = None
+        lib.orc_set_coulomb_g0.argtypes = [f64]
+        lib.orc_set_coulomb_g0.restype = None
         _lib = lib
     return _lib
 
@@ -128,6 +130,52 @@ class coulomb_cutoff:
     def __exit__(self, *exc):
         _load().orc_set_coulomb_cutoff(ctypes.c_double(0.0))
         return False
+
+
+class coulomb_g0:
+    """Context in which the bare kernel 4 pi / |G|^2 keeps the value k0 at
+    G = 0 instead of dropping it (k0 = auxiliary_function_k0(cell): the
+    Gygi-Baldereschi correction)."""
+
+    def __init__(self, k0):
+        self.k0 = float(k0)
+
+    def __enter__(self):
+        _load().orc_set_coulomb_g0(ctypes.c_double(self.k0))
+        return self
+
+    def __exit__(self, *exc):
+        _load().orc_set_coulomb_g0(ctypes.c_double(0.0))
+        return False
+
+
+def auxiliary_function_k0(cell, alpha=None):
+    """K(0) = 4 pi chi of the auxiliary-function treatment of the G = 0
+    divergence for Gamma-only sampling (Gygi & Baldereschi, Phys. Rev. B 34,
+    4405 (1986)), with F(q) = exp(-alpha q^2) / q^2:
+        chi = Omega / (2 pi)^3 int F d^3q - [sum_{G != 0} F(G) + lim_{q->0} (F(q) - 1/q^2)]
+            = Omega / (2 pi)^3 * 2 pi^(3/2) / sqrt(alpha) - sum_{G != 0} F(G) + alpha,
+    the sum over the whole reciprocal lattice (Gaussian-damped); the G = 0
+    value of F's regular part (-alpha) belongs to the lattice sum, and with it
+    chi does not depend on alpha while the real-space images of F are below
+    double-precision resolution.  alpha defaults to (L_min / 12)^2 (L_min:
+    the shortest lattice vector).  For a cubic cell 4 pi chi / L^3 is the
+    Madelung term xi_M / L that dropping G = 0 leaves in a localised charge's
+    self-energy."""
+    a = np.asarray(cell, dtype=np.float64).reshape(3, 3)
+    omega = abs(np.linalg.det(a))
+    b = 2.0 * np.pi * np.linalg.inv(a).T
+    if alpha is None:
+        alpha = (np.linalg.norm(a, axis=1).min() / 12.0) ** 2
+    gmax = np.sqrt(50.0 / alpha)  # exp(-alpha G^2) < 2e-22 beyond
+    lim = [int(np.ceil(gmax * np.linalg.norm(a[i]) / (2 * np.pi))) + 1 for i in range(3)]
+    h, k, l = np.meshgrid(*[np.arange(-m, m + 1) for m in lim], indexing="ij")
+    G = np.stack([h.ravel(), k.ravel(), l.ravel()], 1) @ b
+    g2 = (G * G).sum(1)
+    g2 = g2[g2 > 0]
+    lattice = float(np.sum(np.exp(-alpha * g2) / g2))
+    integral = omega / (2 * np.pi) ** 3 * 2.0 * np.pi ** 1.5 / np.sqrt(alpha)
+    return 4.0 * np.pi * (integral - lattice + alpha)
 
 
 def sphere_radius(cell):

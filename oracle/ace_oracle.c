@@ -28,7 +28,9 @@
  * Alternative G=0 treatment (orc_set_coulomb_cutoff): the Coulomb interaction
  * cut off at r = R_c (Spencer & Alavi, Phys. Rev. B 77, 193110 (2008)), whose
  * Fourier transform is K(G) = 4 pi (1 - cos(|G| R_c)) / |G|^2 and
- * K(0) = 2 pi R_c^2.
+ * K(0) = 2 pi R_c^2; or (orc_set_coulomb_g0) the bare kernel with a given
+ * value in place of the dropped G = 0 term (the auxiliary-function
+ * correction of Gygi & Baldereschi, computed by the Python side).
  *
  * Parity of every function here is pinned by tests against things other than
  * this file: a brute-force DFT, closed-form Coulomb energies (plane waves and
@@ -214,6 +216,11 @@ static double coulomb_rc = 0.0;
 
 void orc_set_coulomb_cutoff(double rc) { coulomb_rc = rc > 0.0 ? rc : 0.0; }
 
+/* K(0) of the bare kernel (0: the G = 0 term dropped). */
+static double coulomb_k0 = 0.0;
+
+void orc_set_coulomb_g0(double k0) { coulomb_k0 = k0; }
+
 /* Coulomb kernel for box entry (i0,i1,i2): 4 pi / |G|^2 with G = 0 dropped,
  * or, with a cutoff R_c, the transform of 1/r restricted to r < R_c. */
 static double coulomb(const grid_t *g, int i0, int i1, int i2)
@@ -224,7 +231,7 @@ static double coulomb(const grid_t *g, int i0, int i1, int i2)
     if (coulomb_rc > 0.0)
         return g2 == 0.0 ? 2.0 * M_PI * coulomb_rc * coulomb_rc
                          : 4.0 * M_PI * (1.0 - cos(sqrt(g2) * coulomb_rc)) / g2;
-    return g2 == 0.0 ? 0.0 : 4.0 * M_PI / g2;
+    return g2 == 0.0 ? coulomb_k0 : 4.0 * M_PI / g2;
 }
 
 /* psi(r) on the grid from half-sphere coefficients: full sphere via c(-G) = c(G)^*. */

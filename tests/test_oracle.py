@@ -257,6 +257,60 @@ def test_truncated_exchange_invariants():
     assert abs(ref["E_x"] - ref0["E_x"]) > 1e-6
 
 
+# --------------------- auxiliary-function G = 0 term (Gygi-Baldereschi)
+
+@pytest.mark.parametrize("L", [20.0, 13.0])
+def test_auxiliary_function_k0_is_the_madelung_term(L):
+    """For a cubic cell K(0) / Omega = xi_M / L, the simple-cubic Madelung
+    constant xi_M = 2.83729747948 (independent of the cell size)."""
+    k0 = oracle.auxiliary_function_k0(gen.cubic_cell(L))
+    assert abs(k0 / L ** 2 - 2.83729747948) < 1e-10
+
+
+def test_auxiliary_function_k0_independent_of_alpha():
+    cell = np.array([[9.0, 0.0, 0.0], [1.5, 10.0, 0.0], [0.3, 0.7, 11.0]])
+    k = [oracle.auxiliary_function_k0(cell, alpha=a) for a in (None, 0.3, 0.6)]
+    assert max(k) - min(k) < 1e-12 * abs(k[0])
+
+
+@pytest.mark.parametrize("sigma,L,n", [(1.0, 20.0, 96), (0.8, 14.0, 64)])
+def test_gaussian_self_energy_with_auxiliary_g0(sigma, L, n):
+    """With K(0) = 4 pi chi the Madelung term of the dropped-G = 0 self-energy
+    cancels: e = sqrt(2/pi)/sigma + 2 pi sigma^2 / L^3."""
+    ecut = 80.0
+    cell = gen.cubic_cell(L)
+    m = oracle.half_sphere(cell, ecut)
+    c = gen.gaussian_sum_coefficients(cell, m, [np.array([3.0, 4.0, 5.0])], [sigma], [1.0])
+    with oracle.coulomb_g0(oracle.auxiliary_function_k0(cell)):
+        e = oracle.pair_energy(c, c, cell, (n, n, n), ecut)
+    assert abs(e - (np.sqrt(2 / np.pi) / sigma + 2 * np.pi * sigma ** 2 / L ** 3)) < 1e-10
+    # and the context restores the dropped term
+    e0 = oracle.pair_energy(c, c, cell, (n, n, n), ecut)
+    assert abs(e0 - (np.sqrt(2 / np.pi) / sigma - 2.83729747948 / L + 2 * np.pi * sigma ** 2 / L ** 3)) < 1e-10
+
+
+def test_auxiliary_g0_exchange_invariants():
+    cell = gen.cubic_cell(7.0)
+    ecut, grid, alpha = 14.0, (16, 16, 16), 0.25
+    psi = gen.random_orbitals(cell, ecut, 5, seed=11)
+    trials = gen.random_trials(cell, ecut, 3, seed=12)
+    m = oracle.half_sphere(cell, ecut)
+    with oracle.coulomb_g0(oracle.auxiliary_function_k0(cell)):
+        V = oracle.vx_apply(psi, trials, cell, grid, ecut, alpha)
+        ref = oracle.ace_build(psi, cell, grid, ecut, alpha)
+        Kphi = oracle.ace_apply(ref["xi"], psi, m)
+    A = oracle.gamma_gram(trials, V, m)
+    assert np.abs(A - A.T).max() < 1e-13 * np.abs(A).max()
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).max() < 1e-14
+    assert abs(ref["E_x"] - np.trace(ref["M"])) < 1e-13 * abs(ref["E_x"])
+    assert np.abs(Kphi - ref["W_G"]).max() < 1e-12 * np.abs(ref["W_G"]).max()
+    # each orbital's own pair density has mean 1 / Omega: the G = 0 term adds
+    # -alpha K(0) / Omega per orbital to E_x
+    E0 = oracle.ace_build(psi, cell, grid, ecut, alpha)["E_x"]
+    k0 = oracle.auxiliary_function_k0(cell)
+    assert abs((ref["E_x"] - E0) - (-alpha * k0 / 7.0 ** 3 * 5)) < 1e-12 * abs(E0)
+
+
 # ------------------------------------------------------------ invariants
 
 @pytest.fixture(scope="module")
