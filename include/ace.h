@@ -31,7 +31,8 @@
  *    product of 2, 3, 5 and n_d >= 2 max|Miller_d| + 1.
  *  - Coulomb kernel 4 pi / |G|^2 on every G of the FFT box (folded to
  *    -n/2..n/2-1), G = 0 term dropped; or the interaction cut off at a radius
- *    (ace_opts.coulomb_rc).
+ *    (ace_opts.coulomb_rc), or the G = 0 term from the auxiliary-function
+ *    correction (ace_opts.coulomb_g0).
  *  - Vectors are complex, interleaved (re, im): complex128 for ACE_FP64 plans,
  *    complex64 for ACE_MIXED plans.  [rows][n_pw_half].
  *
@@ -91,6 +92,14 @@ typedef struct {
                           usual choice is R_c = (3 Omega / 4 pi)^(1/3).  Negative or
                           non-finite: ACE_ERR_INVALID_ARG.  Applies to every build and to
                           hfx_apply_exact of the plan. */
+    int coulomb_g0;    /* with coulomb_rc = 0: 1 = keep the bare kernel's G = 0 term as
+                          K(0) = 4 pi chi, the auxiliary-function correction for Gamma-only
+                          sampling (Gygi & Baldereschi, Phys. Rev. B 34, 4405 (1986)),
+                          chi = Omega / (2 pi)^3 int F d^3q - sum_{G != 0} F(G) + alpha for
+                          F(q) = exp(-alpha q^2) / q^2 over the whole reciprocal lattice
+                          (independent of alpha; for a cubic cell K(0) / Omega = xi_M / L,
+                          the Madelung term); 0 = drop it.  1 with coulomb_rc > 0, or any
+                          other value: ACE_ERR_INVALID_ARG. */
 } ace_opts;
 
 /*

@@ -44,7 +44,7 @@ class _System(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("pair_batch", ctypes.c_int), ("kernels", ctypes.c_int), ("pair_streams", ctypes.c_int),
-                ("pair_variant", ctypes.c_int), ("coulomb_rc", ctypes.c_double)]
+                ("pair_variant", ctypes.c_int), ("coulomb_rc", ctypes.c_double), ("coulomb_g0", ctypes.c_int)]
 
 
 STAT_FIELDS = ("orbitals_ms", "pair_fwd_ms", "pair_coulomb_ms", "pair_inv_ms", "w_to_g_ms", "gram_ms", "factor_ms",
@@ -130,17 +130,19 @@ class Plan:
     the largest occupied set, and the precision ("mixed" or "fp64").
     coulomb_rc = 0 solves Eq. 3 with 4 pi / |G|^2 and the G = 0 term dropped;
     coulomb_rc > 0 uses the interaction 1/r cut off at that radius (bohr;
-    sphere_radius(cell) is the usual choice)."""
+    sphere_radius(cell) is the usual choice); coulomb_g0=True keeps the bare
+    kernel's G = 0 term as the auxiliary-function (Gygi-Baldereschi) value."""
 
     def __init__(self, grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0, kernels=0, pair_streams=0,
-                 pair_variant=0, coulomb_rc=0.0):
+                 pair_variant=0, coulomb_rc=0.0, coulomb_g0=False):
         lib = load()
         self.precision = precision
         self.prec = ACE_MIXED if precision == "mixed" else ACE_FP64
         g = np.ascontiguousarray(np.asarray(grid, dtype=np.int32).reshape(3))
         c = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(9))
         h = ctypes.c_void_p()
-        opts = _Opts(int(pair_batch), int(kernels), int(pair_streams), int(pair_variant), float(coulomb_rc))
+        opts = _Opts(int(pair_batch), int(kernels), int(pair_streams), int(pair_variant), float(coulomb_rc),
+                     int(bool(coulomb_g0)))
         _check(lib.ace_plan_create(ctypes.byref(h), g.ctypes.data_as(ctypes.c_void_p),
                                    c.ctypes.data_as(ctypes.c_void_p), float(ecut), int(n_occ_max), self.prec,
                                    ctypes.byref(opts)))
@@ -148,6 +150,7 @@ class Plan:
         self.grid = tuple(int(x) for x in g)
         self.n_occ_max = int(n_occ_max)
         self.coulomb_rc = float(coulomb_rc)
+        self.coulomb_g0 = bool(coulomb_g0)
         n = ctypes.c_int(0)
         _check(lib.ace_gvec(h, ctypes.byref(n), None))
         self.n_pw_half = n.value
@@ -187,13 +190,15 @@ class Plan:
 
 
 def ace_plan_create(grid, cell, ecut, n_occ_max, precision="mixed", pair_batch=0, kernels=0, pair_streams=0,
-                    pair_variant=0, coulomb_rc=0.0):
+                    pair_variant=0, coulomb_rc=0.0, coulomb_g0=False):
     """kernels: 0 fastest available, 1 CUDA-core Gram products, 2 also generic FFT passes;
     pair_streams: 0 automatic, 1 every pair pass in order on the call's stream;
     pair_variant: 0 automatic (timed at creation), 1 tile passes, 2 transposed planes,
     3 persistent pipeline, 4 hybrid (plane-kernel forward pass, tile passes after it);
-    coulomb_rc: 0 bare Coulomb with G = 0 dropped, > 0 the interaction cut off at that radius."""
-    return Plan(grid, cell, ecut, n_occ_max, precision, pair_batch, kernels, pair_streams, pair_variant, coulomb_rc)
+    coulomb_rc: 0 bare Coulomb with G = 0 dropped, > 0 the interaction cut off at that radius;
+    coulomb_g0: keep the bare kernel's G = 0 term as the auxiliary-function value."""
+    return Plan(grid, cell, ecut, n_occ_max, precision, pair_batch, kernels, pair_streams, pair_variant, coulomb_rc,
+                coulomb_g0)
 
 
 def sphere_radius(cell):

@@ -108,6 +108,8 @@ struct ace_plan {
     float* d_kern = nullptr;   // 4 pi / |G|^2 / N in the tile passes' spectrum layout (zline only)
     float* d_kern_t = nullptr; // the same for transposed planes (n % 16 == 0 cubes)
     double coul_rc = 0;        // Coulomb cutoff radius (0: 4 pi / |G|^2 with G = 0 dropped)
+    int coul_g0 = 0;           // 1: the bare kernel keeps K(0) = 4 pi chi (auxiliary function)
+    double coul_k0 = 0;        // that K(0)
     void* d_kern_r = nullptr;  // K(G) / N for the Coulomb stage of the tile passes, R[n0][n1][n2]
     struct Scdm {                 // SCDM workspace, grown on first use
         double* gv = nullptr;     // G components per plane wave [3][npw]
@@ -1094,6 +1096,41 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     return rc;
 }
 
+// K(0) = 4 pi chi of the auxiliary-function treatment of the G = 0 term for
+// Gamma-only sampling (Gygi & Baldereschi), F(q) = exp(-a q^2) / q^2:
+//   chi = Omega / (2 pi)^3 int F d^3q - [sum_{G != 0} F(G) - a]
+// (the bracket's -a: F's regular part F - 1/q^2 at q = 0, the G = 0 member
+// of the lattice sum).  With a = (L_min / 12)^2 the real-space images of F are
+// below double resolution and chi does not depend on a; the sum runs over
+// every reciprocal lattice vector with a G^2 <= 50.
+double auxiliary_function_k0(const double cell[9], const double b[9], double omega) {
+    double lmin = 1e300;
+    for (int i = 0; i < 3; ++i)
+        lmin = std::min(lmin, std::sqrt(cell[3 * i] * cell[3 * i] + cell[3 * i + 1] * cell[3 * i + 1] +
+                                        cell[3 * i + 2] * cell[3 * i + 2]));
+    const double a = (lmin / 12.0) * (lmin / 12.0), g2max = 50.0 / a;
+    int lim[3];
+    for (int i = 0; i < 3; ++i) {
+        const double len = std::sqrt(cell[3 * i] * cell[3 * i] + cell[3 * i + 1] * cell[3 * i + 1] +
+                                     cell[3 * i + 2] * cell[3 * i + 2]);
+        lim[i] = (int)std::ceil(std::sqrt(g2max) * len / (2 * M_PI)) + 1;
+    }
+    double lattice = 0;
+    for (int h = -lim[0]; h <= lim[0]; ++h)
+        for (int k = -lim[1]; k <= lim[1]; ++k)
+            for (int l = -lim[2]; l <= lim[2]; ++l) {
+                if (h == 0 && k == 0 && l == 0) continue;
+                double g2 = 0;
+                for (int c = 0; c < 3; ++c) {
+                    const double g = h * b[c] + k * b[3 + c] + l * b[6 + c];
+                    g2 += g * g;
+                }
+                lattice += std::exp(-a * g2) / g2;
+            }
+    const double integral = omega / std::pow(2 * M_PI, 3) * 2.0 * std::pow(M_PI, 1.5) / std::sqrt(a);
+    return 4 * M_PI * (integral - (lattice - a));
+}
+
 template <typename R>
 int create_impl(ace_plan* P, const ace_opts* opts) {
     P->esz = sizeof(R);
@@ -1135,10 +1172,14 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     // stage of the tile passes reads one for the cut-off interaction and in
     // double precision (one load is cheaper than a double division there); in
     // single precision it forms 4 pi / |G|^2 from G itself.
-    if (opts) P->coul_rc = opts->coulomb_rc;
+    if (opts) {
+        P->coul_rc = opts->coulomb_rc;
+        P->coul_g0 = opts->coulomb_g0;
+        if (P->coul_g0) P->coul_k0 = auxiliary_function_k0(P->cell, P->b, P->omega);
+    }
     P->zline = P->s_xy.cube && P->s_z.cube && zline_group(P->n[0]) > 0;
     if (const char* env = std::getenv("ACE_ZLINE")) P->zline = P->zline && std::atoi(env) != 0;
-    const bool inline_tab = !P->zline && (P->coul_rc > 0 || sizeof(R) == 8);
+    const bool inline_tab = !P->zline && (P->coul_rc > 0 || P->coul_g0 || sizeof(R) == 8);
     if (P->zline || inline_tab) {
         const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
         const bool with_t = P->zline && tplane_supported(n0);
@@ -1161,7 +1202,7 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
         auto k = [&](double q2) {
             if (rc > 0) return (q2 > 0 ? 4 * M_PI * (1 - std::cos(std::sqrt(q2) * rc)) / q2 : 2 * M_PI * rc * rc) /
                                (double)P->N;
-            return q2 > 0 ? 4 * M_PI / (q2 * (double)P->N) : 0.0;
+            return q2 > 0 ? 4 * M_PI / (q2 * (double)P->N) : P->coul_k0 / (double)P->N;
         };
         for (int z = 0; z < n0; ++z)
             for (int y = 0; y < n1; ++y)
@@ -1244,6 +1285,8 @@ int ace_plan_create(ace_plan** plan, const int grid[3], const double cell[9], do
         if (grid[d] < 1 || grid[d] > 4096) return fail(ACE_ERR_INVALID_ARG, "grid extent out of range");
     if (opts && !(std::isfinite(opts->coulomb_rc) && opts->coulomb_rc >= 0))
         return fail(ACE_ERR_INVALID_ARG, "coulomb_rc must be finite and >= 0");
+    if (opts && (opts->coulomb_g0 < 0 || opts->coulomb_g0 > 1 || (opts->coulomb_g0 && opts->coulomb_rc > 0)))
+        return fail(ACE_ERR_INVALID_ARG, "coulomb_g0 must be 0 or 1, and 0 with coulomb_rc > 0");
     ace_plan* P = new ace_plan();
     cudaGetDevice(&P->dev);
     P->prec = precision;
@@ -1461,15 +1504,18 @@ int ace_build_batched(ace_system* sys, int n_sys, void* stream) {
 }
 
 namespace {
-// Version 2 appends the Coulomb cutoff; version 1 files (no cutoff field)
-// were written with the bare kernel and load as coulomb_rc = 0.
-const char kSaveMagic[8] = {'A', 'C', 'E', 'X', 'I', '0', '0', '2'};
+// Version 3 appends the Coulomb cutoff and the G = 0 choice; version 1 files
+// (neither field) were written with the bare kernel, G = 0 dropped, and load
+// as such; version 2 files carry the cutoff only.
+const char kSaveMagic[8] = {'A', 'C', 'E', 'X', 'I', '0', '0', '3'};
+const char kSaveMagicV2[8] = {'A', 'C', 'E', 'X', 'I', '0', '0', '2'};
 const char kSaveMagicV1[8] = {'A', 'C', 'E', 'X', 'I', '0', '0', '1'};
 struct SaveHeader {
     char magic[8];
     int32_t precision, grid[3], n_occ, n_pw_half;
     double cell[9], ecut, alpha, E_x;
     double coulomb_rc;
+    int64_t coulomb_g0;
 };
 constexpr size_t kHeaderV1 = offsetof(SaveHeader, coulomb_rc);
 }  // namespace
@@ -1495,6 +1541,7 @@ int ace_save(const char* path, const ace_plan* plan, const void* xi, int n_occ, 
     h.alpha = alpha;
     h.E_x = E_x;
     h.coulomb_rc = plan->coul_rc;
+    h.coulomb_g0 = plan->coul_g0;
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(ACE_ERR_INVALID_ARG, std::string("ace_save: cannot open ") + path);
     const bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 && std::fwrite(buf.data(), 1, bytes, f) == bytes;
@@ -1510,6 +1557,9 @@ int ace_load(const char* path, const ace_plan* plan, void* xi, int* n_occ, doubl
     std::memset(&h, 0, sizeof(h));
     bool hdr = std::fread(&h, kHeaderV1, 1, f) == 1;
     if (hdr && std::memcmp(h.magic, kSaveMagic, 8) == 0)
+        hdr = std::fread(&h.coulomb_rc, sizeof(h.coulomb_rc), 1, f) == 1 &&
+              std::fread(&h.coulomb_g0, sizeof(h.coulomb_g0), 1, f) == 1;
+    else if (hdr && std::memcmp(h.magic, kSaveMagicV2, 8) == 0)
         hdr = std::fread(&h.coulomb_rc, sizeof(h.coulomb_rc), 1, f) == 1;
     else if (hdr)
         hdr = std::memcmp(h.magic, kSaveMagicV1, 8) == 0;
@@ -1518,7 +1568,7 @@ int ace_load(const char* path, const ace_plan* plan, void* xi, int* n_occ, doubl
         return fail(ACE_ERR_INVALID_ARG, "ace_load: not an ACE vector file");
     }
     bool same = h.precision == plan->prec && h.n_pw_half == plan->npw && h.ecut == plan->ecut &&
-                h.coulomb_rc == plan->coul_rc;
+                h.coulomb_rc == plan->coul_rc && h.coulomb_g0 == plan->coul_g0;
     for (int d = 0; d < 3; ++d) same = same && h.grid[d] == plan->n[d];
     for (int d = 0; d < 9; ++d) same = same && h.cell[d] == plan->cell[d];
     if (!same || h.n_occ < 1 || h.n_occ > plan->n_occ_max) {

@@ -440,10 +440,14 @@ def test_pair_variants_odd_pair_count(variant):
 # ---------------------------------------- the Coulomb interaction cut off at R_c
 
 def _check_truncated(s, prec, rc, **plan_kw):
+    return _check_coulomb(s, prec, oracle.coulomb_cutoff(rc), coulomb_rc=rc, **plan_kw)
+
+
+def _check_coulomb(s, prec, ctx, **plan_kw):
     n = len(s["psi"])
-    with oracle.coulomb_cutoff(rc):
+    with ctx:
         ref = oracle.ace_build(s["psi"], s["cell"], s["grid"], s["ecut"], s["alpha"])
-    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, prec, coulomb_rc=rc, **plan_kw)
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, prec, **plan_kw)
     xi, E = ace.ace_build(plan, dev(s["psi"], plan), s["alpha"])
     W, M = ace.ace_last_intermediates(plan, n)
     tol = TOL[prec]
@@ -509,3 +513,36 @@ def test_truncated_coulomb_checkpoint_and_rejections(tmp_path):
     for bad in (-1.0, float("nan"), float("inf")):
         with pytest.raises(ace.AceError):
             ace.Plan(s["grid"], s["cell"], s["ecut"], 8, "mixed", coulomb_rc=bad)
+
+
+# ------------------------- the auxiliary-function G = 0 term (Gygi-Baldereschi)
+
+@pytest.mark.parametrize("prec,kw", [("mixed", dict(pair_variant=1)), ("mixed", dict(pair_variant=2)),
+                                     ("mixed", dict(pair_variant=3)), ("mixed", dict(pair_variant=4)),
+                                     ("mixed", dict(kernels=2)), ("fp64", {})])
+def test_auxiliary_g0_every_path(prec, kw):
+    """K(0) = 4 pi chi computed by the library against the oracle's own
+    computation of it, through every Coulomb-table path (32^3 cube)."""
+    s = gen.config_small()
+    E = _check_coulomb(s, prec, oracle.coulomb_g0(oracle.auxiliary_function_k0(s["cell"])), coulomb_g0=True, **kw)
+    # the G = 0 term shifts E_x by -alpha n K(0) / Omega from the dropped-term value
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], 8, prec)
+    _, E0 = ace.ace_build(plan, dev(s["psi"], plan), s["alpha"])
+    k0 = oracle.auxiliary_function_k0(s["cell"])
+    assert abs((E - E0) - (-s["alpha"] * 8 * k0 / 1000.0)) <= (1e-6 * s["n_atom"] if prec == "mixed" else 1e-9)
+
+
+def test_auxiliary_g0_generic_box_and_rejections(tmp_path):
+    s = small_system()
+    _check_coulomb(s, "mixed", oracle.coulomb_g0(oracle.auxiliary_function_k0(s["cell"])), coulomb_g0=True)
+    with pytest.raises(ace.AceError):
+        ace.Plan(s["grid"], s["cell"], s["ecut"], 5, "mixed", coulomb_g0=True, coulomb_rc=3.0)
+    c = gen.config_small()
+    plan = ace.Plan(c["grid"], c["cell"], c["ecut"], 8, "mixed", coulomb_g0=True)
+    xi, E = ace.ace_build(plan, dev(c["psi"], plan), c["alpha"])
+    path = str(tmp_path / "xi_g0.ace")
+    ace.ace_save(plan, path, xi, c["alpha"], E)
+    xi2, _, _ = ace.ace_load(ace.Plan(c["grid"], c["cell"], c["ecut"], 8, "mixed", coulomb_g0=True), path)
+    assert torch.equal(xi, xi2)
+    with pytest.raises(ace.AceError):
+        ace.ace_load(ace.Plan(c["grid"], c["cell"], c["ecut"], 8, "mixed"), path)
