@@ -438,6 +438,43 @@ def run_ours(args):
                               "dE_x_per_atom_vs_all_pairs": abs(E_l - E_mixed) / cfg["n_atom"]}
         del xs, phi
 
+    # ---- 16 independent systems of uneven size (n_occ 32..256, 48^3..120^3
+    # grids): the eager batched call, and all 16 builds captured as one CUDA
+    # graph (each on its own forked stream) and replayed
+    batched = None
+    if world == 1:
+        import gen
+
+        systems = gen.batched_systems()
+        bplans = [ace.Plan(s_["grid"], s_["cell"], s_["ecut"], len(s_["psi"]), "mixed") for s_ in systems]
+        bpsi = [torch.from_numpy(s_["psi"].astype(np.complex64)).cuda() for s_ in systems]
+        bsys = [dict(plan=p_, psi_G=x_, alpha=s_["alpha"]) for p_, x_, s_ in zip(bplans, bpsi, systems)]
+        n_pairs_b = sum(len(s_["psi"]) * (len(s_["psi"]) + 1) // 2 for s_ in systems)
+        ace.ace_build_batched(bsys)
+        te = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ace.ace_build_batched(bsys)  # synchronous call: host wall time
+            te.append((time.perf_counter() - t0) * 1e3)
+        bg = ace.BatchedBuildGraph(bsys)
+        bg.replay()
+        tg = []
+        for _ in range(3):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            bg.launch()
+            b.record()
+            torch.cuda.synchronize()
+            tg.append(a.elapsed_time(b))
+        batched = {"systems": len(systems), "pairs": n_pairs_b, "eager_ms": min(te), "graph_ms": min(tg),
+                   "pairs_per_s_graph": n_pairs_b / (min(tg) / 1e3)}
+        del bg
+        for p_ in bplans:
+            p_.close()
+        del bpsi, bsys
+
     # ---- the same step replayed from a CUDA graph (build + apply captured once),
     # and on the small 8-orbital / 32^3 case, where launches dominate
     graph = None
@@ -549,7 +586,7 @@ def run_ours(args):
                        "pair_kernels": kcfg},
             "ace_builds_per_s": builds, "E_x": E_mixed, "fp64_gpu": fp64,
             "phases_ms_per_step": {k: v / args.steps for k, v in stats.items() if k.endswith("_ms")},
-            "s_mtace": s_mtace, "cuda_graph": graph,
+            "s_mtace": s_mtace, "cuda_graph": graph, "batched_16_systems": batched,
             "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clocks}
     print(json.dumps(line), flush=True)

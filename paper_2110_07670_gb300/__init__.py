@@ -446,6 +446,46 @@ def ace_build_batched(systems, stream=None):
     return [(outs[k], arr[k].E_x) for k in range(len(systems))]
 
 
+class BatchedBuildGraph:
+    """Several independent systems (each with its own plan) built by one CUDA
+    graph launch: every system's ace_build_async captured on its own stream,
+    forked from and joined back into the capturing stream, after one run of
+    the same calls outside capture (allocations, attributes).  replay() runs
+    all the builds and returns their E_x; each system's xi is filled in place.
+    systems: list of dicts with plan, psi_G (captured by address: copy new
+    orbitals into it before a replay), alpha and optionally pairs."""
+
+    def __init__(self, systems):
+        import torch
+        self.systems = systems
+        self.xi = [torch.empty_like(s["psi_G"]) for s in systems]
+        for s, xi in zip(systems, self.xi):
+            ace_build_async(s["plan"], s["psi_G"], s["alpha"], pairs=s.get("pairs"), xi=xi)
+        for s in systems:
+            ace_build_result(s["plan"])
+        self.streams = [torch.cuda.Stream() for _ in systems]
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            main = torch.cuda.current_stream()
+            for s, xi, side in zip(systems, self.xi, self.streams):
+                side.wait_stream(main)
+                with torch.cuda.stream(side):
+                    ace_build_async(s["plan"], s["psi_G"], s["alpha"], pairs=s.get("pairs"), xi=xi, stream=side)
+            for side in self.streams:
+                main.wait_stream(side)
+
+    def launch(self):
+        """Replay the graph without waiting for it."""
+        self.graph.replay()
+
+    def replay(self):
+        """Replay and return every system's E_x (waits for the graph)."""
+        import torch
+        self.graph.replay()
+        torch.cuda.current_stream().synchronize()
+        return [ace_build_result(s["plan"]) for s in self.systems]
+
+
 def ace_save(plan, path, xi, alpha, E_x, stream=None):
     plan._vec(xi, "xi")
     _check(load().ace_save(os.fsencode(path), plan.handle, _ptr(xi), xi.shape[0], float(alpha), float(E_x),

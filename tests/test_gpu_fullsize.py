@@ -150,6 +150,32 @@ def test_batched_sixteen_uneven_systems():
         p.close()
 
 
+def test_batched_sixteen_systems_one_graph():
+    """The 16 uneven systems captured as one CUDA graph (each build on its own
+    forked stream): a replay gives the eager batched call's E_x and xi, and a
+    replay after new orbitals are copied into a captured input builds from
+    them."""
+    systems = gen.batched_systems()
+    plans = [ace.Plan(s["grid"], s["cell"], s["ecut"], len(s["psi"]), "mixed") for s in systems]
+    psis = [dev(s["psi"], p) for s, p in zip(systems, plans)]
+    eager = ace.ace_build_batched([dict(plan=p, psi_G=x, alpha=s["alpha"]) for p, x, s in zip(plans, psis, systems)])
+    g = ace.BatchedBuildGraph([dict(plan=p, psi_G=x, alpha=s["alpha"]) for p, x, s in zip(plans, psis, systems)])
+    Es = g.replay()
+    for k, s in enumerate(systems):
+        assert abs(Es[k] - eager[k][1]) / s["n_atom"] <= 1e-9
+        assert rel(host(g.xi[k]), host(eager[k][0])) <= 1e-6
+    s0 = systems[0]
+    psi2 = gen.random_orbitals(s0["cell"], s0["ecut"], len(s0["psi"]), seed=77)
+    psis[0].copy_(dev(psi2, plans[0]))
+    Es2 = g.replay()
+    _, E_ref = ace.ace_build(plans[0], dev(psi2, plans[0]), s0["alpha"])
+    assert abs(Es2[0] - E_ref) / s0["n_atom"] <= 1e-9
+    assert all(abs(Es2[k] - Es[k]) <= 1e-12 * abs(Es[k]) for k in range(1, len(systems)))
+    del g
+    for p in plans:
+        p.close()
+
+
 def test_save_load_roundtrip():
     cfg = gen.config_small()
     plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], 8, "mixed")
