@@ -899,7 +899,7 @@ int scdm_impl(ace_plan* P, const void* psi_G, int n, int preselect, void* phi_G,
         sel = cand;
     }
     // column-pivoted QR of the candidate columns: n steps, each a pass over A
-    const int qb = scdm_qr_blocks(m);
+    const int qb = scdm_qr_blocks(m, n, (int)sizeof(R));
     ACE_TRY(grow(&W.A, &W.c_A, (size_t)n * m * sizeof(R)));
     ACE_TRY(grow(&W.nu, &W.c_nu, (size_t)m + (size_t)n * m));
     ACE_TRY(grow(&W.part, &W.c_part, (size_t)qb * scdm_argmax_bytes()));

@@ -222,7 +222,7 @@ cudaError_t launch_gather_columns(const R* phi, int n, long long N, const int* s
 // r, c [n] scratch; piv [n] columns of A; nu0 one double; status set to 1 on
 // rank deficiency (a best residual norm^2 not above 1e-10 of the largest
 // column norm^2).
-int scdm_qr_blocks(long long m);
+int scdm_qr_blocks(long long m, int n, int esz);  // esz: bytes of an element of A
 size_t scdm_argmax_bytes();
 struct QrWork {
     void* part;

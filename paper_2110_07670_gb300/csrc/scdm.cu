@@ -393,16 +393,17 @@ __global__ void qr_update_kernel(const T* __restrict__ A, int n, long long m, co
         }
     }
     __syncthreads();
-    // tiles of 64 columns; warp w takes columns (w & 1) * 32 + lane of the
-    // tile and the row quarter w >> 1, the quarters summed in shared memory
-    __shared__ double red[4][64];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = w >> 1, cl = (w & 1) * 32 + lane;
-    const int rq = (n + 3) / 4, i0 = g * rq, i1 = i0 + rq < n ? i0 + rq : n;
+    // tiles of 32 columns over one resident wave of blocks; warp g takes the
+    // tile's columns (one per lane) over the row group g of 8, the groups
+    // summed in shared memory
+    __shared__ double red[8][32];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, cl = lane;
+    const int rq = (n + 7) / 8, i0 = g * rq, i1 = i0 + rq < n ? i0 + rq : n;
     ArgMax best{-1.0, -1};
     double* Rk = Rrows + k * m;
-    const long long ntiles = (m + 63) / 64;
+    const long long ntiles = (m + 31) / 32;
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const long long j = t * 64 + cl;
+        const long long j = t * 32 + cl;
         double part_sum = 0;
         if (j < m) {
             // eight loads in flight per thread before their products
@@ -437,7 +438,8 @@ __global__ void qr_update_kernel(const T* __restrict__ A, int n, long long m, co
         if (g == 0 && j < m) {
             double v = nu[j];
             if (v >= 0) {
-                const double d = (red[0][cl] + red[1][cl]) + (red[2][cl] + red[3][cl]);
+                const double d = ((red[0][cl] + red[1][cl]) + (red[2][cl] + red[3][cl])) +
+                                 ((red[4][cl] + red[5][cl]) + (red[6][cl] + red[7][cl]));
                 Rk[j] = d;
                 v -= d * d;
                 if (v < 0) v = 0;
@@ -568,30 +570,43 @@ cudaError_t launch_gather_columns(const R* phi, int n, long long N, const int* s
     return cudaGetLastError();
 }
 
-// blocks of the column passes: one per 64-column tile, at most 8 per SM of 152
-int scdm_qr_blocks(long long m) {
-    const long long b = (m + 63) / 64;
-    return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
+size_t qr_update_smem(int n) { return (size_t)n * (sizeof(double) + 2 * sizeof(float)); }
+
+// blocks of the column passes: one per 32-column tile, at most one resident
+// wave of the update kernel (its occupancy for this n times the SM count)
+int scdm_qr_blocks(long long m, int n, int esz) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const cudaError_t e =
+        esz == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, qr_update_kernel<float>, kThreads, qr_update_smem(n))
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, qr_update_kernel<double>, kThreads, qr_update_smem(n));
+    if (e != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        per = 1;
+    }
+    const long long tiles = (m + 31) / 32, wave = (long long)std::max(sms, 1) * per;
+    return (int)std::max(1LL, std::min(tiles, wave));
 }
 
 size_t scdm_argmax_bytes() { return sizeof(ArgMax); }
 
 template <typename T>
 cudaError_t launch_qr_init(const T* A, int n, long long m, double* nu, void* part, cudaStream_t st) {
-    qr_init_kernel<T><<<scdm_qr_blocks(m), kThreads, 0, st>>>(A, n, m, nu, (ArgMax*)part);
+    qr_init_kernel<T><<<scdm_qr_blocks(m, n, sizeof(T)), kThreads, 0, st>>>(A, n, m, nu, (ArgMax*)part);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_qr_step(const T* A, int n, long long m, int k, QrWork w, cudaStream_t st) {
-    const int rb = (n + 31) / 32;
+    const int rb = (n + 31) / 32, qb = scdm_qr_blocks(m, n, sizeof(T));
     qr_resid_kernel<T><<<rb, kThreads, (size_t)(k + 1) * sizeof(double), st>>>(
-        (const ArgMax*)w.part, scdm_qr_blocks(m), A, n, m, w.R, w.Q, k, w.piv, w.nu, w.nu0, w.status, w.r);
+        (const ArgMax*)w.part, qb, A, n, m, w.R, w.Q, k, w.piv, w.nu, w.nu0, w.status, w.r);
     if (k > 0) {
         qr_dots_kernel<<<(k + 7) / 8, kThreads, 0, st>>>(w.Q, n, k, w.r, w.c);
         qr_apply_kernel<<<rb, kThreads, (size_t)k * sizeof(double), st>>>(w.Q, n, k, w.c, w.r);
     }
-    qr_update_kernel<T><<<scdm_qr_blocks(m), kThreads, (size_t)n * (sizeof(double) + 2 * sizeof(float)), st>>>(
+    qr_update_kernel<T><<<qb, kThreads, qr_update_smem(n), st>>>(
         A, n, m, w.r, k, w.Q, w.R, w.nu, w.rdiag, (ArgMax*)w.part);
     return cudaGetLastError();
 }
