@@ -209,3 +209,14 @@ def test_s_prime_mts_harness_matches_oracle():
         assert abs(r["E_exact"] - E_ex) <= 1e-10 * abs(E_ex)
         assert abs(r["dE"] - (E_ex - E_ace)) <= 2e-10 * abs(E_ex)
     assert abs(rec[0]["dE"]) > 1e-6  # the screening error
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_scdm_few_orbitals(prec, n):
+    """1 to 3 orbitals (empty row groups in the column pass, no second
+    Gram-Schmidt pass at step 0, a 1 x 1 rotation)."""
+    s = gen.config_small()
+    piv, ref = _check_scdm(dict(s, psi=s["psi"][:n]), prec, True)
+    if prec == "fp64":
+        assert np.array_equal(piv, ref["pivots"])

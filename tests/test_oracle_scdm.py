@@ -168,3 +168,16 @@ def test_scdm_without_preselection_matches_lapack_and_polar():
     U, _ = scipy.linalg.polar(V)
     assert np.abs(r["O"] - U).max() < 1e-12
     assert np.abs(r["phi_G"] - U @ psi).max() < 1e-12
+
+
+def test_scdm_single_orbital():
+    """One orbital: the pivot is the candidate where psi^2 is largest and the
+    localised orbital is psi itself, with the sign of psi there."""
+    s = gen.config_small()
+    psi = s["psi"][:1]
+    r = oscdm.scdm(psi, s["cell"], s["grid"], s["ecut"])
+    phi = oracle.to_real(psi, s["cell"], s["grid"], s["ecut"]).reshape(-1)
+    c = r["candidates"]
+    p = c[np.argmax(phi[c] ** 2)]
+    assert r["pivots"][0] == p
+    assert np.abs(r["phi_G"] - np.sign(phi[p]) * psi).max() < 1e-14
