@@ -213,7 +213,10 @@ int ace_overlap_screen(ace_plan* plan, const void* psi_G, int n_occ, double rho_
  *      residual norm (ties to the lowest grid index);
  *   4. phi_G = O psi_G with O = (V V^T)^{-1/2} V, V[k][i] = psi_i(r_{C_k}): the
  *      columns Gamma(r, r_{C_k}) orthonormalised symmetrically (Loewdin).
- * Every step after the real-space orbitals runs in double.
+ * Every step after the real-space orbitals runs in double, except that for
+ * ACE_MIXED plans the QR's column pass forms q . a (a the single-precision
+ * orbital values, exact in float) in float-float arithmetic, about 2^-48 of
+ * sum |q_i a_i|, and phi_G = O psi_G is formed in float with compensated sums.
  *   psi_G        [n_occ][n_pw_half] device, orthonormal, as ace_build (n_occ <= 2048)
  *   phi_G        [n_occ][n_pw_half] device output, same precision; must not overlap psi_G
  *   pivots       [n_occ] host output (may be NULL): grid points (i0 n1 + i1) n2 + i2, in pivot order
