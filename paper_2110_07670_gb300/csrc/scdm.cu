@@ -234,17 +234,17 @@ __device__ __forceinline__ void rows_reduce8(double part, double base, double* r
     }
 }
 
-// sum over l = g, g + 8, ... < k of c[l] Q[l][i], four loads in flight
+// sum over l = g, g + 8, ... < k of c[l] Q[l][i], eight loads in flight
 __device__ __forceinline__ double strided_dot8(const double* c, const double* __restrict__ Q, int n, int i, int g,
                                                int k) {
     double s[4] = {0, 0, 0, 0};
     int l = g;
-    for (; l + 24 < k; l += 32) {
-        double v[4];
+    for (; l + 56 < k; l += 64) {
+        double v[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = Q[(long long)(l + 8 * u) * n + i];
+        for (int u = 0; u < 8; ++u) v[u] = Q[(long long)(l + 8 * u) * n + i];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s[u] += c[l + 8 * u] * v[u];
+        for (int u = 0; u < 8; ++u) s[u & 3] += c[l + 8 * u] * v[u];
     }
     for (; l < k; l += 8) s[0] += c[l] * Q[(long long)l * n + i];
     return (s[0] + s[1]) + (s[2] + s[3]);
