@@ -232,6 +232,9 @@ def test_truncated_gaussian_self_energy(sigma, L, n, rc):
         e = oracle.pair_energy(c, c, cell, (n, n, n), ecut)
     expect = np.sqrt(2 / np.pi) / sigma * (1 - np.exp(-rc ** 2 / (2 * sigma ** 2)))
     assert abs(e - expect) < 1e-10
+    if (sigma, L) == (1.0, 20.0):
+        golden = dict((k, float(v)) for k, v in _golden("closed_forms.txt"))
+        assert abs(e - golden["gaussian_sigma1_L20_cutoff_sphere"]) < 1e-10
 
 
 def test_truncated_exchange_invariants():
@@ -284,6 +287,9 @@ def test_gaussian_self_energy_with_auxiliary_g0(sigma, L, n):
     with oracle.coulomb_g0(oracle.auxiliary_function_k0(cell)):
         e = oracle.pair_energy(c, c, cell, (n, n, n), ecut)
     assert abs(e - (np.sqrt(2 / np.pi) / sigma + 2 * np.pi * sigma ** 2 / L ** 3)) < 1e-10
+    if (sigma, L) == (1.0, 20.0):
+        golden = dict((k, float(v)) for k, v in _golden("closed_forms.txt"))
+        assert abs(e - golden["gaussian_sigma1_L20_auxiliary_g0"]) < 1e-10
     # and the context restores the dropped term
     e0 = oracle.pair_energy(c, c, cell, (n, n, n), ecut)
     assert abs(e0 - (np.sqrt(2 / np.pi) / sigma - 2.83729747948 / L + 2 * np.pi * sigma ** 2 / L ** 3)) < 1e-10
