@@ -9,9 +9,10 @@
 //     applied twice: at step k the column of largest residual norm (ties to
 //     the lowest index), residual norms downdated by (q_k . a_j)^2
 //   Phi = (V V^T)^{-1/2} V Psi, V[k][i] = psi_i(r_{C_k}): the polar factor of V
-//     by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2 from V / |V|_F
-// All of it in double; the orbitals' real-space values come in the plan's
-// precision.
+//     by scaled Newton-Schulz steps X <- X (3 I - X^T X) / 2 from V / |V|_F
+// Sums and decisions in double; the orbitals' real-space values come in the
+// plan's precision, and for single precision the QR's column pass forms its
+// products in float-float arithmetic (about 2^-48 relative) on the FP32 pipes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
