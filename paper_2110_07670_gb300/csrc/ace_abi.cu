@@ -148,6 +148,8 @@ struct ace_plan {
     void* d_spec = nullptr;
     void* d_WG = nullptr;
     double* d_M = nullptr;
+    double* d_S = nullptr;     // the overlap screen's S (the last build's M stays in d_M)
+    size_t S_cap = 0;
     double* d_L = nullptr;
     double* d_Linv = nullptr;
     double* d_E = nullptr;
@@ -796,6 +798,7 @@ int overlap_impl(ace_plan* P, const void* psi_G, int n, double rho_cut, int32_t*
     ACE_TRY(check_gamma<R>(P, psi_G, n, st));
     std::vector<Quad> oq = orbital_quads(n);
     ACE_TRY(upload_quads_eager(P, oq, st));
+    ACE_TRY(grow(&P->d_S, &P->S_cap, (size_t)n * n));
     R* phi = (R*)P->d_phi;
     ACE_TRY(run_to_real<R>(P, (const cx<R>*)psi_G, P->d_quads, (int)oq.size(), phi, st));
     const long long K = P->N;
@@ -813,7 +816,7 @@ int overlap_impl(ace_plan* P, const void* psi_G, int n, double rho_cut, int32_t*
             ACE_TRY(grow(&P->d_part, &P->part_cap, ((size_t)nchunk * n * n + 1) / 2));
             float* part = reinterpret_cast<float*>(P->d_part);
             ACE_CKL(launch_overlap_partial_umma((const float*)phi, n, K, kc, part, P->d_err, st));
-            ACE_CKL(launch_overlap_finish<float>(part, nchunk, n, scale, P->d_M, st));
+            ACE_CKL(launch_overlap_finish<float>(part, nchunk, n, scale, P->d_S, st));
             done = true;
         }
     }
@@ -823,11 +826,11 @@ int overlap_impl(ace_plan* P, const void* psi_G, int n, double rho_cut, int32_t*
         nchunk = (int)std::min<long long>(nchunk, std::max<long long>(1, K / 256));
         ACE_TRY(grow(&P->d_part, &P->part_cap, (size_t)nchunk * n * n));
         ACE_CKL(launch_overlap_partial<R>(phi, n, K, nchunk, P->d_part, st));
-        ACE_CKL(launch_overlap_finish<double>(P->d_part, nchunk, n, scale, P->d_M, st));
+        ACE_CKL(launch_overlap_finish<double>(P->d_part, nchunk, n, scale, P->d_S, st));
     }
     mark(P, PH_IDLE, st);
     std::vector<double> S((size_t)n * n);
-    ACE_CK(cudaMemcpyAsync(S.data(), P->d_M, S.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaMemcpyAsync(S.data(), P->d_S, S.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     ACE_CK(cudaStreamSynchronize(st));
     ACE_TRY(check_device_error(P, st));
     int q = 0;
@@ -976,7 +979,7 @@ void free_plan(ace_plan* P) {
     for (auto e : P->aux_ev) cudaEventDestroy(e);
     if (P->fork_ev) cudaEventDestroy(P->fork_ev);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
-                    P->d_WG, P->d_M, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
+                    P->d_WG, P->d_M, P->d_S, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
                     P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_kern_t, P->d_kern_r, P->d_pipe,
                     P->scdm.gv, P->scdm.dpsi, P->scdm.dens, P->scdm.isel, P->scdm.A, P->scdm.nu,
                     P->scdm.part, P->scdm.mats, P->scdm.ipiv};

@@ -546,3 +546,17 @@ def test_auxiliary_g0_generic_box_and_rejections(tmp_path):
     assert torch.equal(xi, xi2)
     with pytest.raises(ace.AceError):
         ace.ace_load(ace.Plan(c["grid"], c["cell"], c["ecut"], 8, "mixed"), path)
+
+
+def test_last_intermediates_survive_the_overlap_screen():
+    """The overlap screen keeps its S apart from the last build's M and W."""
+    s = gen.config_small()
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], 8, "mixed")
+    psi = dev(s["psi"], plan)
+    ace.ace_build(plan, psi, s["alpha"])
+    W0, M0 = ace.ace_last_intermediates(plan, 8)
+    W0 = W0.clone()
+    ace.ace_overlap_screen(plan, psi, 0.1)
+    W1, M1 = ace.ace_last_intermediates(plan, 8)
+    assert np.array_equal(M0, M1) and torch.equal(W0, W1)
+    plan.close()
