@@ -22,7 +22,8 @@ every step below is written out plainly in numpy, in the paper's order:
 
 Readings (also in the design notes): one electron per orbital in rho (a
 constant factor changes neither comparison); |grad rho| is the Euclidean norm;
-the Loewdin orthonormalisation of the selected columns.
+the Loewdin orthonormalisation of the selected columns; a best residual
+norm^2 at or below 1e-10 of the largest column norm^2 is rank deficiency.
 """
 import numpy as np
 
@@ -57,14 +58,18 @@ def preselect(rho, grad):
 
 def qrcp_pivots(A, k):
     """First k pivot columns of Householder QR with column pivoting of A
-    (rows x columns), each step taking the column of largest trailing norm."""
+    (rows x columns), each step taking the column of largest trailing norm.
+    Rank deficient (ValueError) when that norm^2 is not above 1e-10 times the
+    largest column norm^2 of A: fewer than k independent columns beyond
+    rounding."""
     R = np.array(A, dtype=np.float64)
     nr, nc = R.shape
     perm = np.arange(nc)
+    ref = float((R * R).sum(0).max())
     for s in range(k):
         norms = (R[s:, s:] ** 2).sum(0)
         j = s + int(np.argmax(norms))  # argmax returns the first of equal maxima
-        if norms[j - s] <= 0.0:
+        if not norms[j - s] > 1e-10 * ref:
             raise ValueError("rank deficient: fewer than %d independent columns" % k)
         R[:, [s, j]] = R[:, [j, s]]
         perm[[s, j]] = perm[[j, s]]
