@@ -74,3 +74,46 @@ def test_rank_threshold_is_the_same_on_both_sides():
     with pytest.raises(ValueError):
         oscdm.qrcp_pivots(A, 12)
     assert np.array_equal(gs_pivots(A, 4), oscdm.qrcp_pivots(A, 4))
+
+
+def scaled_newton_schulz(V, l0, tol=1e-10, max_it=100):
+    """The library's polar iteration, restated: X0 = V / |V|_F, then
+    X <- 1.5 a X - 0.5 a^3 (X X^T) X with a = sqrt(3 / (1 + l + l^2)) and
+    l <- min(1, 0.5 a l (3 - a^2 l^2)), until max |X X^T - I| < tol was seen
+    before a step (that step included)."""
+    X = V / np.linalg.norm(V)
+    l = l0
+    for it in range(max_it):
+        a = np.sqrt(3.0 / (1.0 + l + l * l))
+        T = X @ X.T
+        err = np.abs(T - np.eye(len(V))).max()
+        X = 1.5 * a * X - 0.5 * a ** 3 * (T @ X)
+        l = min(1.0, 0.5 * a * l * (3.0 - a * a * l * l))
+        if err < tol:
+            return X, it + 1
+    raise RuntimeError("no convergence")
+
+
+@pytest.mark.parametrize("cond,seed", [(10.0, 1), (1e4, 2), (1e7, 3)])
+def test_scaled_newton_schulz_gives_the_polar_factor(cond, seed):
+    """V = U diag(s) W^T with singular values spread over `cond`; the start
+    estimate l0 = min_k R_kk / |V|_F from the pivoted QR of V^T (as the
+    library takes it from its own QR) over-estimates sigma_min: the iteration
+    still converges to scipy's polar factor, in few steps."""
+    import scipy.linalg
+    rng = np.random.default_rng(seed)
+    n = 24
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    W, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = np.geomspace(1.0, 1.0 / cond, n)
+    V = (U * s) @ W.T
+    _, Rq, _ = scipy.linalg.qr(V.T, pivoting=True)
+    l0 = np.abs(np.diag(Rq)).min() / np.linalg.norm(V)
+    assert l0 >= s.min() / np.linalg.norm(V) * 0.999  # an over-estimate (or equal)
+    X, its = scaled_newton_schulz(V, l0)
+    P, _ = scipy.linalg.polar(V)
+    assert np.abs(X - P).max() < 1e-14 * max(cond, 10.0)  # the polar factor's own conditioning
+    assert its <= 10 + int(np.ceil(np.log(cond) / np.log(2.5)))
+    # the plain iteration (l0 = 1: no scaling) needs more steps
+    _, its_plain = scaled_newton_schulz(V, 1.0)
+    assert its_plain >= its
