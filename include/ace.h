@@ -241,16 +241,30 @@ int ace_scdm(ace_plan* plan, const void* psi_G, int n_occ, int preselect, void* 
 int ace_apply(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T, void* Kpsi, void* stream);
 
 /*
+ * The fast energy of an inner MTS step (Section 2.3, Eq. 6-7, with the
+ * operator of Eq. 5): E = sum_t <psi_t| K psi_t> = -sum_{t,k} <xi_k|psi_t>^2,
+ * from the Gram C = xi^T psi of the apply (no K psi is formed), reduced in
+ * FP64 on the device; only E comes back to the host.
+ *   xi [n_occ][n_pw_half], psi [T][n_pw_half]: device; E: host output.
+ * Synchronises the stream; cannot be captured in a CUDA graph.
+ */
+int ace_apply_energy(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T, double* E, void* stream);
+
+/*
  * ace_apply for callers that cannot allocate device memory (the paper has no
  * counterpart; this is a deployment variant of the Eq. 5 apply above).
  * Callers in an inner loop that must not stall on cudaMalloc / cudaFree
  * (both synchronise the device), or whose device memory belongs to another
- * allocator, get the same result as ace_apply without a plan and without any
+ * allocator, get the operator of ace_apply without a plan and without any
  * allocation: the working memory is a fixed 8 MiB __device__ array inside the
  * library, held on every device that loads the library until the process
- * exits.
+ * exits.  For ACE_MIXED it forms xi^T psi on CUDA cores (float products
+ * summed in double over short slices) where ace_apply uses the tensor cores,
+ * and -xi C with compensated float sums, so it agrees with ace_apply within
+ * the parity tolerance (1e-6 of the largest |K psi|), not bit for bit.
  *   xi [n_occ][n_pw_half], psi [T][n_pw_half], Kpsi [T][n_pw_half]: device,
- *   complex128 for precision ACE_FP64, complex64 for ACE_MIXED.
+ *   all on the current device, complex128 for precision ACE_FP64, complex64
+ *   for ACE_MIXED.
  * Limit: T * n_occ <= 524288, else ACE_ERR_INVALID_ARG and nothing runs.
  * The first call on a device looks up the array's device address (once per
  * device); make that first call before any stream capture.  All calls share

@@ -25,7 +25,7 @@ SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_
            "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc",
            "ace_build_batched", "ace_save", "ace_load", "ace_build_pairs", "ace_build_finish",
            "ace_plan_config", "ace_overlap_screen", "ace_build_async", "ace_build_result",
-           "ace_check_timeout_path", "ace_scdm")
+           "ace_check_timeout_path", "ace_scdm", "ace_apply_energy")
 
 _lib = None
 
@@ -79,6 +79,7 @@ def load(build_if_missing=False):
     lib.ace_gvec.argtypes = [P, ctypes.POINTER(i32), P]
     lib.ace_build.argtypes = [P, P, i32, f64, P, P, P, ctypes.POINTER(f64), P]
     lib.ace_apply.argtypes = [P, P, i32, P, i32, P, P]
+    lib.ace_apply_energy.argtypes = [P, P, i32, P, i32, ctypes.POINTER(f64), P]
     lib.ace_build_pairs.argtypes = [P, P, i32, f64, P, P, P, ctypes.POINTER(f64), P]
     lib.ace_build_finish.argtypes = [P, P, i32, P, P, P]
     lib.ace_build_async.argtypes = [P, P, i32, f64, P, P, P, P]
@@ -365,6 +366,17 @@ def ace_apply(plan, xi, psi, out=None, stream=None):
     return out
 
 
+def ace_apply_energy(plan, xi, psi, stream=None):
+    """sum_t <psi_t|K psi_t> = -sum_{t,k} <xi_k|psi_t>^2 (the fast energy of an
+    inner MTS step), reduced on the device; returns a float."""
+    plan._vec(xi, "xi")
+    plan._vec(psi, "psi")
+    E = ctypes.c_double(0.0)
+    _check(load().ace_apply_energy(plan.handle, _ptr(xi), xi.shape[0], _ptr(psi), psi.shape[0], ctypes.byref(E),
+                                   _stream(stream)))
+    return E.value
+
+
 def hfx_apply_exact(plan, psi_occ, alpha, psi, out=None, stream=None):
     """alpha V_X psi with the exact exchange operator of the occupied set."""
     import torch
@@ -408,12 +420,19 @@ def ace_apply_noalloc(xi, psi, out, stream=None):
     """K psi = -xi (xi^T psi) without a plan and without device allocation in
     the library (for callers that must not allocate).  xi, psi and out are
     caller-owned contiguous CUDA tensors: complex64 (mixed) or complex128
-    (fp64) of shape [rows][n_pw_half]; T * n_occ <= 524288."""
+    (fp64) of shape [rows][n_pw_half], all on the current CUDA device;
+    T * n_occ <= 524288.  Raises ValueError before the library is called
+    when a tensor has another dtype, layout or device."""
     import torch
+    if xi.dtype not in (torch.complex64, torch.complex128):
+        raise ValueError("ace_apply_noalloc: xi must be complex64 (mixed) or complex128 (fp64)")
     prec = ACE_MIXED if xi.dtype == torch.complex64 else ACE_FP64
     for t in (xi, psi, out):
         if not t.is_cuda or not t.is_contiguous() or t.dim() != 2 or t.dtype != xi.dtype or t.shape[1] != xi.shape[1]:
             raise ValueError("ace_apply_noalloc: contiguous CUDA complex tensors of one dtype and width")
+    here = torch.device("cuda", torch.cuda.current_device())
+    if any(t.device != here for t in (xi, psi, out)):
+        raise ValueError(f"ace_apply_noalloc: xi, psi and out must be on the current device {here}")
     if out.shape != psi.shape:
         raise ValueError("ace_apply_noalloc: out must have the shape of psi")
     _check(load().ace_apply_noalloc(_ptr(xi), xi.shape[0], _ptr(psi), psi.shape[0], xi.shape[1], prec, _ptr(out),

@@ -128,6 +128,8 @@ struct ace_plan {
     float tune_ms[5] = {0, 0, 0, 0, 0};  // autotune: tile x1 stream, tile x2, planes x2, pipeline, hybrid x2
     bool tplane = false;       // pair passes with transposed spectrum planes (plane.cuh; needs zline)
     int pair_tile = 0;         // pairs ordered in pair_tile x pair_tile orbital blocks (0: row by row; env ACE_PAIR_TILE)
+    int row_block = 4;         // pairs packed column-shared in blocks of this many rows (pack_pairs_blocked;
+                               // < 2: consecutive pairs of the row-ordered list; env ACE_ROW_BLOCK)
     int pair_streams = 2;      // concurrent streams of pair sub-batches
     int pair_sub = 0;          // transforms per sub-batch (0: batch / pair_streams; env ACE_PAIR_SUB)
     bool fused = false;        // the pair passes as one persistent kernel (pipeline.cuh)
@@ -575,6 +577,59 @@ void pack_pairs(const std::vector<int>& pa, const std::vector<int>& pb, std::vec
     }
 }
 
+// Pack the pairs (i, j), i <= j, two per transform in blocks of rb rows.
+// Within a block the columns go in ascending order, and the block's rows that
+// list column j are paired up, (i1, j) with (i2, j), as the quad
+// (j, i1, j, i2): the column orbital is shared by both pairs, so a transform
+// reads one fresh function and makes one merged update of the fresh
+// accumulator W_j, while the functions and accumulators of the block's rb rows
+// are touched by every transform of the block and stay in L2 as the columns
+// stream through.  Pairs left unpaired in their column are packed two at a
+// time, in row order, after their block.  Every listed pair appears exactly
+// once, so the sums of Eq. 2 and 4 are unchanged; only their order differs.
+void pack_pairs_blocked(int n, const std::vector<int>& pa, const std::vector<int>& pb, int rb, std::vector<Quad>& q) {
+    if (rb < 2) {
+        pack_pairs(pa, pb, q);
+        return;
+    }
+    std::vector<std::vector<int>> rows(n);  // columns listed in each row
+    for (size_t p = 0; p < pa.size(); ++p) rows[pa[p]].push_back(pb[p]);
+    std::vector<std::pair<int, int>> cr;  // (column, row) of one block
+    std::vector<int> la, lb;              // unpaired pairs of one block
+    for (int r0 = 0; r0 < n; r0 += rb) {
+        const int r1 = std::min(n, r0 + rb);
+        cr.clear();
+        la.clear();
+        lb.clear();
+        for (int i = r0; i < r1; ++i)
+            for (int j : rows[i]) cr.push_back({j, i});
+        std::sort(cr.begin(), cr.end());
+        for (size_t s = 0; s < cr.size();) {
+            size_t e = s;
+            while (e < cr.size() && cr[e].first == cr[s].first) ++e;
+            const int j = cr[s].first;
+            size_t k = s;
+            for (; k + 1 < e; k += 2) q.push_back(Quad{j, cr[k].second, j, cr[k + 1].second});
+            if (k < e) {
+                la.push_back(cr[k].second);
+                lb.push_back(j);
+            }
+            s = e;
+        }
+        std::vector<size_t> idx(la.size());
+        for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return la[x] < la[y]; });
+        for (size_t k = 0; k < idx.size(); k += 2) {
+            Quad x{la[idx[k]], lb[idx[k]], -1, -1};
+            if (k + 1 < idx.size()) {
+                x.c = la[idx[k + 1]];
+                x.d = lb[idx[k + 1]];
+            }
+            q.push_back(x);
+        }
+    }
+}
+
 // A bounded device-side wait that gave up leaves a flag; report and clear it.
 int check_device_error(ace_plan* P, cudaStream_t st) {
     int err = 0;
@@ -660,10 +715,14 @@ int pairs_enqueue(ace_plan* P, const void* psi_G, int n_occ, double alpha, const
                 pb.push_back(j);
             }
     }
-    if (P->pair_tile > 0) tile_pairs(pa, pb, P->pair_tile);
     std::vector<Quad> oq = orbital_quads(n_occ), q = oq;
     const int n_orb_t = (int)oq.size();
-    pack_pairs(pa, pb, q);
+    if (P->pair_tile > 0) {
+        tile_pairs(pa, pb, P->pair_tile);
+        pack_pairs(pa, pb, q);
+    } else {
+        pack_pairs_blocked(n_occ, pa, pb, P->row_block, q);
+    }
     const int n_pair_t = (int)q.size() - n_orb_t;
     ACE_TRY(upload_quads(P, q, st));
     const Quad* d_oq = P->d_quads;
@@ -968,6 +1027,22 @@ int apply_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, v
     return ACE_OK;
 }
 
+// sum_t <psi_t|K psi_t> = -sum_{t,k} C_tk^2 with C = xi^T psi (the fast
+// energy of an inner MTS step): the apply's Gram, reduced on the device.
+template <typename R>
+int apply_energy_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, double* E, cudaStream_t st) {
+    ACE_TRY(grow(&P->d_C, &P->C_cap, (size_t)T * n_occ));
+    ACE_TRY(gram<R>(P, (const cx<R>*)psi, T, (const cx<R>*)xi, n_occ, P->d_C, st));
+    mark(P, PH_ENERGY, st);
+    ACE_CKL(launch_sumsq(P->d_C, (long long)T * n_occ, -1.0, P->d_E, st));
+    mark(P, PH_IDLE, st);
+    ACE_CK(cudaMemcpyAsync(&P->h_res->E, P->d_E, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ACE_CK(cudaStreamSynchronize(st));
+    ACE_TRY(check_device_error(P, st));
+    *E = P->h_res->E;
+    return ACE_OK;
+}
+
 void free_plan(ace_plan* P) {
     if (P->h_res) cudaFreeHost(P->h_res);
     if (P->quads_ev) cudaEventSynchronize(P->quads_ev);
@@ -1032,17 +1107,18 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
         set_variant(P, 1, fixed_streams ? fixed_streams : 2);
         return ACE_OK;
     }
-    // timing pairs: the first transforms of every pair i <= j of n_occ_max rows
+    // timing pairs: the first transforms of every pair i <= j of n_occ_max
+    // rows, packed as a build packs them
     const int n = P->n_occ_max;
     std::vector<int> pa, pb;
-    const int want = 2 * std::min(4 * P->batch, std::max(1, n * (n + 1) / 4));
-    for (int i = 0; i < n && (int)pa.size() < want; ++i)
-        for (int j = i; j < n && (int)pa.size() < want; ++j) {
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) {
             pa.push_back(i);
             pb.push_back(j);
         }
     std::vector<Quad> q;
-    pack_pairs(pa, pb, q);
+    pack_pairs_blocked(n, pa, pb, P->row_block, q);
+    q.resize(std::min(q.size(), (size_t)std::min(4 * P->batch, std::max(1, n * (n + 1) / 4))));
     const int K = (int)q.size();
     cudaStream_t ts = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1165,6 +1241,7 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     P->tensor_gram = !(opts && opts->kernels >= 1) && sizeof(R) == 4;
     if (const char* env = std::getenv("ACE_LOOKAHEAD")) P->lookahead = std::max(0, std::atoi(env));
     if (const char* env = std::getenv("ACE_PAIR_TILE")) P->pair_tile = std::max(0, std::atoi(env));
+    if (const char* env = std::getenv("ACE_ROW_BLOCK")) P->row_block = std::max(0, std::atoi(env));
     if (opts && opts->pair_streams > 0) P->pair_streams = opts->pair_streams;
     if (const char* env = std::getenv("ACE_PAIR_SUB")) P->pair_sub = std::max(0, std::atoi(env));
     ACE_TRY(setup_shapes<R>(P));
@@ -1426,6 +1503,18 @@ int ace_apply(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T,
                                           : apply_impl<float>(plan, xi, n_occ, psi, T, Kpsi, st);
     g_capture = false;
     return rc;
+}
+
+int ace_apply_energy(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T, double* E, void* stream) {
+    if (!plan || !xi || !E || (T > 0 && !psi)) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (n_occ < 1 || T < 0) return fail(ACE_ERR_INVALID_ARG, "n_occ must be >= 1 and T >= 0");
+    *E = 0.0;
+    if (T == 0) return ACE_OK;
+    DeviceGuard g(plan->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (capturing(st)) return fail(ACE_ERR_INVALID_ARG, "ace_apply_energy returns a host value and cannot be captured");
+    return plan->prec == ACE_FP64 ? apply_energy_impl<double>(plan, xi, n_occ, psi, T, E, st)
+                                  : apply_energy_impl<float>(plan, xi, n_occ, psi, T, E, st);
 }
 
 int hfx_apply_exact(ace_plan* plan, const void* psi_occ, int n_occ, double alpha, const void* psi, int T,

@@ -255,6 +255,9 @@ cudaError_t launch_neg_cholesky_inverse(const double* M, int n, double* L, doubl
 cudaError_t launch_energy_reduce(const double* e_part, const Quad* quads, int ntrans, int ntiles, double coef,
                                  double* E, cudaStream_t st);
 
+// out[0] = coef * sum_k x[k]^2 (one block, fixed order)
+cudaError_t launch_sumsq(const double* x, long long n, double coef, double* out, cudaStream_t st);
+
 // One block waiting up to limit_ms on a barrier nothing completes; sets *err.
 cudaError_t launch_wait_for_nothing(int* err, int limit_ms, cudaStream_t st);
 

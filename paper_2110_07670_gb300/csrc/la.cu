@@ -335,6 +335,23 @@ __global__ void energy_final_kernel(const double* __restrict__ part, int nb, dou
     if (threadIdx.x == 0) *E = coef * s;
 }
 
+// out = coef * sum_k x[k]^2 in one block, a fixed order (the fast MTS energy
+// sum_t <psi_t|K psi_t> = -sum_{t,k} C_tk^2 from the apply's Gram C).
+__global__ void __launch_bounds__(1024) sumsq_kernel(const double* __restrict__ x, long long n, double coef,
+                                                     double* __restrict__ out) {
+    __shared__ double ws[32];
+    double s = 0.0;
+    for (long long k = threadIdx.x; k < n; k += blockDim.x) s += x[k] * x[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        *out = coef * t;
+    }
+}
+
 // -M = L L^T and L^-1 with both in shared memory (n^2 doubles, n <= 160):
 // right-looking Cholesky in place, L copied out, then L^-1 in the same
 // buffer, one column per thread, reading L back through L1.
@@ -485,6 +502,11 @@ cudaError_t launch_neg_cholesky_inverse(const double* M, int n, double* L, doubl
     } else {
         neg_cholesky_inverse_kernel<<<1, 1024, 0, st>>>(M, n, L, Linv, status);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(const double* x, long long n, double coef, double* out, cudaStream_t st) {
+    sumsq_kernel<<<1, 1024, 0, st>>>(x, n, coef, out);
     return cudaGetLastError();
 }
 

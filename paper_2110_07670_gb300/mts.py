@@ -6,7 +6,7 @@ the difference to the exact exchange -- the slow part of the split, which the
 paper evaluates every n steps -- is computed only there.  With no ions or
 forces here, the exchange energy plays the role of the force:
 
-    E_ACE(k)   = sum_i <phi_k,i | K_0 phi_k,i>      (fast: one ACE apply)
+    E_ACE(k)   = sum_i <phi_k,i | K_0 phi_k,i>      (fast: the apply's Gram, -sum C^2)
     E_exact(k) = E_x[Phi_k]                          (slow: a full build on Phi_k)
     dE(k)      = E_exact(k) - E_ACE(k)               (the slow correction)
 
@@ -20,14 +20,6 @@ error.  Every step runs through the library's C ABI.
 import time
 
 import numpy as np
-
-
-def gamma_energy(psi, Kpsi):
-    """sum_i <psi_i | Kpsi_i> with the Gamma-point inner product
-    2 Re sum_half a^* b - a(0) b(0) (host numpy arrays [rows][n_pw_half])."""
-    psi = np.asarray(psi)
-    Kpsi = np.asarray(Kpsi)
-    return float(2.0 * np.real(np.sum(np.conj(psi) * Kpsi)) - np.real(np.sum(np.conj(psi[:, 0]) * Kpsi[:, 0])))
 
 
 def run(plan, phi0, alpha, orbitals_at, n_inner, every=1, rho_cut=None):
@@ -53,7 +45,7 @@ def run(plan, phi0, alpha, orbitals_at, n_inner, every=1, rho_cut=None):
         xi, _ = ace.ace_build(plan, loc, alpha, pairs=pairs)
         torch.cuda.synchronize()
         t_build = time.perf_counter() - t0
-        E0 = gamma_energy(phi0, ace.ace_apply(plan, xi, d0).cpu().numpy().astype(np.complex128))
+        E0 = ace.ace_apply_energy(plan, xi, d0)
         _, E_ex = ace.ace_build(plan, d0, alpha, xi=torch.empty_like(d0))
         torch.cuda.synchronize()
         out = [{"k": 0, "E_ACE": E0, "E_exact": E_ex, "dE": E_ex - E0, "build_s": t_build, "pivots": piv,
@@ -63,10 +55,8 @@ def run(plan, phi0, alpha, orbitals_at, n_inner, every=1, rho_cut=None):
         phik = orbitals_at(k)
         dk = torch.from_numpy(np.ascontiguousarray(phik.astype(dt))).cuda()
         t0 = time.perf_counter()
-        Kp = ace.ace_apply(plan, xi, dk)
-        torch.cuda.synchronize()
-        rec = {"k": k, "apply_s": time.perf_counter() - t0,
-               "E_ACE": gamma_energy(phik, Kp.cpu().numpy().astype(np.complex128))}
+        E_ace = ace.ace_apply_energy(plan, xi, dk)
+        rec = {"k": k, "apply_s": time.perf_counter() - t0, "E_ACE": E_ace}
         if k % every == 0:
             t0 = time.perf_counter()
             _, Ek = ace.ace_build(plan, dk, alpha, xi=W)

@@ -44,3 +44,36 @@ def test_apply_noalloc_rejects_oversize():
     with pytest.raises(ace.AceError) as e:
         ace.ace_apply_noalloc(xi, psi, out)
     assert e.value.code == -1 and "exceeds" in str(e.value)
+
+
+def _gamma_random(rng, rows, npw, dtype):
+    a = (rng.standard_normal((rows, npw)) + 1j * rng.standard_normal((rows, npw))) / np.sqrt(npw)
+    a[:, 0] = a[:, 0].real
+    return _dev(a, dtype)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_apply_noalloc_at_the_size_limit(prec):
+    """T * n_occ exactly at the limit (512 ACE vectors, 1024 trials): C and the
+    Gram partials then just fit in the fixed array; the result must match the
+    plan-based apply, and one more trial must be rejected before any work."""
+    from paper_2110_07670_gb300 import build
+    build.build_library()
+    cfg = gen.config_small()
+    dt = np.complex64 if prec == "mixed" else np.complex128
+    plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], 8, prec)
+    rng = np.random.default_rng(11)
+    xi = _gamma_random(rng, 512, plan.n_pw_half, dt)
+    tr = _gamma_random(rng, 1024, plan.n_pw_half, dt)
+    assert xi.shape[0] * tr.shape[0] == 524288
+    ref = ace.ace_apply(plan, xi, tr).cpu().numpy()
+    out = torch.full_like(tr, float("nan"))
+    ace.ace_apply_noalloc(xi, tr, out)
+    got = out.cpu().numpy()
+    assert np.isfinite(got).all()
+    assert np.abs(got - ref).max() <= TOL[prec] * np.abs(ref).max()
+    over = _gamma_random(rng, 1025, plan.n_pw_half, dt)
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_apply_noalloc(xi, over, torch.empty_like(over))
+    assert e.value.code == -1 and "exceeds" in str(e.value)
+    plan.close()
