@@ -35,7 +35,9 @@ sys.path.insert(0, ROOT)
 METRIC = "pair Poisson solves/sec + ACE builds/sec, mixed vs FP64 GPU at |dE_x|<=1e-6 Ha/atom"
 WORKLOAD = "water32: 128 occupied real orbitals, 96^3 grid, cubic 18.6 bohr, 80 Ry, 8256 pairs, alpha 0.25"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
 L2_BYTES = 129 * 1024 * 1024
+ALG_BYTES_PER_PAIR_PER_POINT = 16  # FP32: four complex (8-byte) transfers per packed transform of two pairs
 
 
 def peaks():
@@ -102,6 +104,113 @@ def workload(seed_trials=77):
     cfg = gen.config_water32()
     trials = gen.random_trials(cfg["cell"], cfg["ecut"], cfg["psi"].shape[0], seed_trials)
     return cfg, trials
+
+
+def golden(key):
+    """The FP64 oracle's stored results for a full-size workload
+    (tests/golden/fullsize_<key>.npz, written by make_fullsize_oracle.py from
+    the oracle alone), or None when not stored."""
+    path = os.path.join(GOLDEN_DIR, f"fullsize_{key}.npz")
+    if not os.path.exists(path):
+        return None
+    with np.load(path) as z:
+        d = {k: z[k] for k in z.files}
+    d["E_x"] = float(d["E_x"])
+    return d
+
+
+def parity_vs_oracle(ace, plan, cfg, xi, E, key):
+    """The metric's validity gate against the stored oracle results: |dE_x|
+    per atom, K psi on the stored trials (max |diff| / max |K psi|), M and the
+    quadratic form t^T K t; None when the workload has no stored results."""
+    import torch
+
+    import gen
+    g = golden(key)
+    if g is None:
+        return None
+    n = len(cfg["psi"])
+    T = max(int(g["n_kpsi"]), int(g["n_q"]))
+    tr = gen.random_trials(cfg["cell"], cfg["ecut"], T, seed=int(g["trials_seed"]))
+    dt = plan.cdtype
+    K = ace.ace_apply(plan, xi, torch.from_numpy(tr.astype(np.complex64 if dt == torch.complex64 else np.complex128))
+                      .cuda()).cpu().numpy().astype(np.complex128)
+    Kg = g["Kpsi"].astype(np.complex128)
+    _, M = ace.ace_last_intermediates(plan, n)
+    Q = gen.gamma_overlap(tr[:int(g["n_q"])], K[:int(g["n_q"])])
+    rows = g["M_rows"]
+    return {"dE_x_per_atom_vs_oracle": abs(E - g["E_x"]) / cfg["n_atom"],
+            "Kpsi_rel_vs_oracle": float(np.abs(K[:len(Kg)] - Kg).max() / np.abs(Kg).max()),
+            "M_rel_vs_oracle": float(np.abs(M[rows] - g["M"]).max() / np.abs(g["M"]).max()),
+            "Q_rel_vs_oracle": float(np.abs(Q - g["Q"]).max() / np.abs(g["Q"]).max()),
+            "E_x_oracle": g["E_x"], "trials": T, "tolerance": {"dE_x_per_atom": 1e-6, "Kpsi_rel": 1e-6}}
+
+
+def workload_leg(ace, cfg, key, hbm, steps=2, warmup=1, trial_sets=(), pairs=None, fp64=True):
+    """Another configuration of the metric, timed like the headline (CUDA
+    events on the call's stream, L2 flushed between steps): a step is one
+    ace_build over the listed pairs plus one ace_apply per trial set.  Reports
+    pairs/s and builds/s of the mixed form, its pair-pass roofline (16 N bytes
+    per pair over the pair wall time), the stored-oracle deltas, and the FP64
+    GPU form of the same step (one step, no warm-up: it is slow)."""
+    import torch
+
+    n = len(cfg["psi"])
+    npairs = n * (n + 1) // 2 if pairs is None else int(pairs[0][-1])
+    N = int(np.prod(cfg["grid"]))
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {"workload": cfg["name"], "pairs_per_build": npairs, "apply_calls_per_step": len(trial_sets),
+           "apply_trials": int(trial_sets[0].shape[0]) if len(trial_sets) else 0}
+    for prec in ("mixed", "fp64") if fp64 else ("mixed",):
+        plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, prec)
+        dt = np.complex64 if prec == "mixed" else np.complex128
+        psi = torch.from_numpy(cfg["psi"].astype(dt)).cuda()
+        trs = [torch.from_numpy(t.astype(dt)).cuda() for t in trial_sets]
+        xi = torch.empty_like(psi)
+        outs = [torch.empty_like(t) for t in trs]
+        E = [None]
+
+        def step():
+            _, E[0] = ace.ace_build(plan, psi, cfg["alpha"], pairs=pairs, xi=xi)
+            for t, o in zip(trs, outs):
+                ace.ace_apply(plan, xi, t, out=o)
+
+        nw, ns = (warmup, steps) if prec == "mixed" else (0, 1)
+        for _ in range(nw):
+            step()
+        torch.cuda.synchronize()
+        ace.ace_get_stats(plan)
+        ace.ace_set_timing(plan, prec == "mixed")
+        total = 0.0
+        for _ in range(ns):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            step()
+            b.record()
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+        st = ace.ace_get_stats(plan)
+        ace.ace_set_timing(plan, False)
+        ms = total / ns
+        rec = {"ms_per_step": ms, "pairs_per_s": npairs / (ms / 1e3), "builds_per_s": 1e3 / ms, "E_x": E[0]}
+        if prec == "mixed":
+            wall = st["pair_wall_ms"] / ns
+            ach = ALG_BYTES_PER_PAIR_PER_POINT * N * npairs / (wall / 1e3) / 1e9 if wall > 0 else 0.0
+            rec.update(pair_wall_ms_per_build=wall, apply_ms_per_step=(st["gram_ms"] + st["xi_ms"]) / ns,
+                       roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                                 "count": "16 N bytes per pair over the pair passes' wall time"},
+                       pair_kernels=plan.config(),
+                       parity=parity_vs_oracle(ace, plan, cfg, xi, E[0], key) if key else None)
+            out["mixed"] = rec
+        else:
+            rec["dE_x_per_atom_mixed_vs_fp64"] = abs(out["mixed"]["E_x"] - E[0]) / cfg["n_atom"]
+            out["fp64_gpu"] = rec
+        plan.close()
+        del psi, trs, xi, outs
+    del flush
+    torch.cuda.empty_cache()
+    return out
 
 
 def pair_quads(n):
@@ -175,17 +284,24 @@ def run_reference(args):
     # of oracle work on 16 cores); warm-up steps one row
     for _ in range(args.warmup):
         cpu_baseline(cfg, rows=1)
-    vals = []
+    vals, walls = [], []
     sample = None
     for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
         cb = cpu_baseline(cfg, rows=2)
+        walls.append((time.perf_counter() - t0) * 1e3)
         vals.append(cb["value"])
         sample = cb
     v = statistics.median(vals)
+    n = cfg["psi"].shape[0]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 8256 / v * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample["sample"]},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(walls),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"water32 sample: the {2 * n - 1} pairs of rows 0-1 of the {n * (n + 1) // 2}-pair "
+                                   "list (128 orbitals, 96^3, 18.6 bohr, 80 Ry), all orbital transforms; "
+                                   "value = sampled pairs / pair-solve seconds",
+                       "sample": sample["sample"]},
+            "full_build_ms_extrapolated": n * (n + 1) // 2 / v * 1e3,
             "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": sample["cores"], "kind": "oracle",
                              "sample": sample["sample"]},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -273,6 +389,8 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     total_ms, E_mixed, stats = timed_steps(plan, psi, tr, xi, K, args.steps, args.warmup, with_timing=True)
+    # the metric's validity gate on this build, against the stored FP64 oracle results
+    parity = parity_vs_oracle(ace, plan, cfg, xi, E_mixed, "water32") if world == 1 else None
     clocks = sampler.stop()
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -296,11 +414,19 @@ def run_ours(args):
              4: "plane-kernel forward pass, tile passes after it"}[variant]
     group = 32 if (variant != 3 and streams == 2) else 64  # transforms per launch (algorithmic count)
     pbg, _ = pass_bytes(n, N, batch=group)
-    pipe_bytes = sum(pbg.values())  # per build
+    pipe_bytes = sum(pbg.values())  # per build, counted per launch (orbital reads and W updates included)
+    share = 1.0
     if world > 1:  # this rank's shard of the pairs: its share of the transforms
-        pipe_bytes *= (stats["pair_transforms"] / args.steps) / len(pair_quads(n))
+        share = (stats["pair_transforms"] / args.steps) / len(pair_quads(n))
+        pipe_bytes *= share
     pair_wall = stats["pair_wall_ms"] / args.steps
-    achieved = pipe_bytes / (pair_wall / 1e3) / 1e9 if pair_wall > 0 else 0.0
+    # the roofline unit: 16 N bytes per pair -- the spectrum's four FP32
+    # complex HBM transfers (written after the forward plane pass, read and
+    # written by the Coulomb pass, read by the accumulation pass) per packed
+    # transform of two pairs; orbital reads and W updates are not counted
+    alg_bytes = ALG_BYTES_PER_PAIR_PER_POINT * N * npairs * share
+    achieved = alg_bytes / (pair_wall / 1e3) / 1e9 if pair_wall > 0 else 0.0
+    achieved_launch = pipe_bytes / (pair_wall / 1e3) / 1e9 if pair_wall > 0 else 0.0
     fwd_key = "pair_fwd_hybrid" if variant == 4 else "pair_fwd"
     traffic_step = (MEASURED_TRAFFIC_PER_LAUNCH[fwd_key] + MEASURED_TRAFFIC_PER_LAUNCH["pair_coulomb"] +
                     MEASURED_TRAFFIC_PER_LAUNCH["pair_inv"]) * (stats["pair_transforms"] / args.steps) / 64
@@ -334,8 +460,15 @@ def run_ours(args):
                 "traffic": traffic_step if world == 1 and variant in (1, 4) else None,
                 "traffic_unit": "bytes per build (sum of the three passes' DRAM bytes from the ncu "
                 "captures, scaled from 64-transform launches)",
-                "algorithmic_bytes_per_build": pipe_bytes, "pair_wall_ms_per_build": pair_wall,
+                "algorithmic_bytes_per_build": alg_bytes,
+                "algorithmic_count": "16 N bytes per pair (N = 96^3): the spectrum's four FP32 complex HBM "
+                                     "transfers per packed transform of two pairs",
+                "pair_wall_ms_per_build": pair_wall,
                 "share_of_step": pair_wall / max(stats["total_ms"] / args.steps, 1e-9),
+                "per_launch_count": {
+                    "bytes_per_build": pipe_bytes, "achieved_gbs": achieved_launch, "frac": achieved_launch / hbm,
+                    "count": "every distinct orbital read and W read-modify-write of each "
+                             f"{group}-transform launch added to the spectrum transfers (depends on launch size)"},
                 "per_pass_alone": per_pass}
     # ALU view of the same passes (the FFT/pair path is near the FP32 ridge,
     # about 6 flops per algorithmic byte): the FFT flops of every packed
@@ -359,7 +492,7 @@ def run_ours(args):
         dom = max(phase_ms, key=phase_ms.get)
         live_ms = phase_ms[dom] / args.steps
         roofline["dominant_kernel_live"] = {
-            "pass": dom, "ms_per_build": live_ms, "algorithmic_bytes_per_build": pbg[dom],
+            "pass": dom, "ms_per_build": live_ms, "bytes_per_build_launch_count": pbg[dom],
             "achieved_gbs": pbg[dom] / (live_ms / 1e3) / 1e9 if live_ms > 0 else 0.0,
             "frac": (pbg[dom] / (live_ms / 1e3) / 1e9) / hbm if live_ms > 0 else 0.0}
     gpu_launches = int(stats["launches"]) + 0
@@ -475,6 +608,26 @@ def run_ours(args):
             p_.close()
         del bpsi, bsys
 
+    # ---- the other configurations of the metric: 256 orbitals on 120^3 with
+    # ten applies on 256 trials per build (an MTS outer step and its inner
+    # steps), 512 localised orbitals on 160^3 with the screened pair list, and
+    # the 8-orbital 32^3 case (latency)
+    legs = None
+    if world == 1 and not args.no_legs:
+        import gen
+
+        hbm_, _ = peaks()
+        legs = {}
+        c3 = gen.config_water64(n_trial_sets=10, T=256)
+        legs["water64"] = workload_leg(ace, c3, "water64", hbm_, trial_sets=c3["trials"])
+        del c3
+        c5 = gen.config_localized()
+        legs["localized"] = workload_leg(ace, c5, "localized", hbm_, pairs=c5["pairs"])
+        del c5
+        c1 = gen.config_small()
+        legs["small"] = workload_leg(ace, c1, None, hbm_, steps=20, warmup=3,
+                                     trial_sets=[gen.random_trials(c1["cell"], c1["ecut"], 8, 2)])
+
     # ---- the same step replayed from a CUDA graph (build + apply captured once),
     # and on the small 8-orbital / 32^3 case, where launches dominate
     graph = None
@@ -588,6 +741,7 @@ def run_ours(args):
             "phases_ms_per_step": {k: v / args.steps for k, v in stats.items() if k.endswith("_ms")},
             "s_mtace": s_mtace, "cuda_graph": graph, "batched_16_systems": batched,
             "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": gpu_launches,
+            "parity_vs_oracle": parity, "workloads": legs,
             "clocks": clocks}
     print(json.dumps(line), flush=True)
 
@@ -688,6 +842,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-legs", action="store_true", help="skip the 120^3, 160^3 and 32^3 workloads")
     ap.add_argument("--profile-case", type=int, default=0, help="run one small build with this many orbitals")
     ap.add_argument("--profile-apply", type=int, default=0, help="run ACE applies on this many trial vectors")
     ap.add_argument("--profile-overlap", type=int, default=0, help="run the overlap screen on this many orbitals")

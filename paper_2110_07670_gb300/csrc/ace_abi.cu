@@ -88,6 +88,11 @@ int largest_divisor_at_most(int n, int cap) {
 
 struct ace_plan {
     int dev = 0;
+    int sms = 152;             // SMs of the plan's device
+    int gram_kmax = 0;         // at most this many reals per K slice of the streamed Gram (0: one wave of
+                               // blocks; env ACE_GRAM_KMAX)
+    float* d_csplit = nullptr; // TF32 hi / lo of the apply's C [2][T][np]
+    size_t csplit_cap = 0;
     int prec = ACE_MIXED;
     int n[3] = {0, 0, 0};
     long long N = 0;
@@ -522,11 +527,12 @@ int gram(ace_plan* P, const cx<R>* A, int m, const cx<R>* B, int n, double* G, c
     mark(P, PH_GRAM, st);
     if constexpr (sizeof(R) == 4) {
         if (P->tensor_gram) {
-            const int nchunk = gram_umma_chunks(K);
+            const long long kc = gram_stream_kchunk(m, n, K, P->sms, P->gram_kmax);
+            const int nchunk = (int)((K + kc - 1) / kc);
             // single-precision partials: half the doubles' room is enough
             ACE_TRY(grow(&P->d_part, &P->part_cap, ((size_t)nchunk * m * n + 1) / 2));
             float* part = reinterpret_cast<float*>(P->d_part);
-            ACE_CKL(launch_gram_partial_umma((const float*)A, (const float*)B, m, n, K, part, P->d_err, st));
+            ACE_CKL(launch_gram_stream((const float*)A, (const float*)B, m, n, K, kc, part, P->d_err, st));
             ACE_CKL(launch_gram_finish_f32(part, nchunk, (const float*)A, (const float*)B, m, n, K, G, n, st));
             return ACE_OK;
         }
@@ -1022,6 +1028,16 @@ int apply_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, v
     ACE_TRY(grow(&P->d_C, &P->C_cap, (size_t)T * n_occ));
     ACE_TRY(gram<R>(P, (const cx<R>*)psi, T, (const cx<R>*)xi, n_occ, P->d_C, st));  // C[t][k] = <psi_t|xi_k>
     mark(P, PH_XI, st);
+    if constexpr (sizeof(R) == 4) {
+        if (P->tensor_gram) {  // -xi C on the tensor cores
+            const size_t np = (size_t)apply_product_np(n_occ);
+            ACE_TRY(grow(&P->d_csplit, &P->csplit_cap, 2 * (size_t)T * np));
+            ACE_CKL(launch_apply_product(P->d_C, T, n_occ, (const float*)xi, 2LL * P->npw, P->d_csplit,
+                                         P->d_csplit + (size_t)T * np, (float*)out, P->sms, P->d_err, st));
+            mark(P, PH_IDLE, st);
+            return ACE_OK;
+        }
+    }
     ACE_CKL(launch_gemm_nn<R>(P->d_C, T, n_occ, (const R*)xi, 2LL * P->npw, -1.0, (R*)out, false, st));
     mark(P, PH_IDLE, st);
     return ACE_OK;
@@ -1055,7 +1071,7 @@ void free_plan(ace_plan* P) {
     if (P->fork_ev) cudaEventDestroy(P->fork_ev);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
                     P->d_WG, P->d_M, P->d_S, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
-                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_kern_t, P->d_kern_r, P->d_pipe,
+                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_kern_t, P->d_kern_r, P->d_pipe, P->d_csplit,
                     P->scdm.gv, P->scdm.dpsi, P->scdm.dens, P->scdm.isel, P->scdm.A, P->scdm.nu,
                     P->scdm.part, P->scdm.mats, P->scdm.ipiv};
     for (void* p : ptrs)
@@ -1242,6 +1258,12 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     if (const char* env = std::getenv("ACE_LOOKAHEAD")) P->lookahead = std::max(0, std::atoi(env));
     if (const char* env = std::getenv("ACE_PAIR_TILE")) P->pair_tile = std::max(0, std::atoi(env));
     if (const char* env = std::getenv("ACE_ROW_BLOCK")) P->row_block = std::max(0, std::atoi(env));
+    if (const char* env = std::getenv("ACE_GRAM_KMAX")) P->gram_kmax = std::max(0, std::atoi(env));
+    {
+        int sm_count = 0;
+        if (cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, P->dev) == cudaSuccess && sm_count > 0)
+            P->sms = sm_count;
+    }
     if (opts && opts->pair_streams > 0) P->pair_streams = opts->pair_streams;
     if (const char* env = std::getenv("ACE_PAIR_SUB")) P->pair_sub = std::max(0, std::atoi(env));
     ACE_TRY(setup_shapes<R>(P));

@@ -164,11 +164,19 @@ cudaError_t launch_gather(const cx<R>* box, const Quad* quads, int t0, int batch
 template <typename R>
 cudaError_t launch_gram_partial(const R* A, const R* B, int m, int n, long long K, int nchunk, double* P,
                                 cudaStream_t st);
-// The same partials on tcgen05 tensor cores (split TF32, FP32 accumulation in
-// TMEM), gram_umma_chunks(K) K-slices; err: device error flag for bounded waits.
-int gram_umma_chunks(long long K);
-cudaError_t launch_gram_partial_umma(const float* A, const float* B, int m, int n, long long K, float* P, int* err,
-                                     cudaStream_t st);
+// The same partials on tcgen05 tensor cores, streamed (umma_apply.cu): split
+// TF32, FP32 accumulation in TMEM, P [ceil(K / kchunk)][m][n] float; kchunk a
+// multiple of 32 from gram_stream_kchunk (about one block per SM, at most
+// max_k reals per slice when max_k > 0); err: device error flag for bounded waits.
+long long gram_stream_kchunk(int m, int n, long long K, int sms, int max_k);
+cudaError_t launch_gram_stream(const float* A, const float* B, int m, int n, long long K, long long kchunk, float* P,
+                               int* err, cudaStream_t st);
+// out[t][j] = -sum_k C[t][k] xi[k][j] on tcgen05 (K psi = -xi C^T, Eq. 5):
+// C [T][n] double, xi [n][K] float, out [T][K] float; Ch, Cl: scratch of
+// T * apply_product_np(n) floats each (16-byte aligned) for C's TF32 split.
+int apply_product_np(int n);
+cudaError_t launch_apply_product(const double* C, int T, int n, const float* xi, long long K, float* Ch, float* Cl,
+                                 float* out, int sms, int* err, cudaStream_t st);
 // Overlap partials |A|^T |A| (A [m][K], K-slices of kchunk, a multiple of 32,
 // each accumulated in TMEM) on tcgen05: P [ceil(K / kchunk)][m][m] float.
 cudaError_t launch_overlap_partial_umma(const float* A, int m, long long K, long long kchunk, float* P, int* err,

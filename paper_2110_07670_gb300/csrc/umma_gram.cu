@@ -1,29 +1,27 @@
-// umma_gram.cu -- Gamma-point Gram partials on the 5th-generation tensor cores.
+// umma_gram.cu -- the s-MTACE overlap S_ij = (Omega / N) sum_r |phi_i(r)| |phi_j(r)|
+// (arXiv:2110.07670 Section 2.4) as a Gram product of |phi| on the tcgen05
+// tensor cores.
 //
-// G = A B^T over the real views of two sets of plane-wave vectors (K = 2
-// n_pw_half reals per row): M = Phi^T W of the ACE construction and
-// C = psi^T xi of the ACE apply (arXiv:2110.07670 Section 2.2, Eq. 5).
 // Split precision: every FP32 operand x is split into x_hi = tf32(x) and
 // x_lo = tf32(x - x_hi), and the four products hi.hi + hi.lo + lo.hi + lo.lo
 // are accumulated in FP32 in tensor memory (TMEM) by tcgen05.mma kind::tf32,
 // which carries the product to about 2^-22 of |a||b|.  Each thread block owns
-// a 128 x 128 output tile and one 128-wide slice of K; the large products
+// a 128 x 128 output tile and one K slice of grid points; the large products
 // (hi.hi) and the three small ones accumulate in separate TMEM accumulators,
 // the slice's partial is written in single precision and the slices are
-// summed in double by launch_gram_finish (la.cu).
+// summed in double by launch_overlap_finish (la.cu).
 //
-// Data movement: the block's threads load 128 x 32 FP32 slices of both
-// operands as 8-byte vectors (rows of n_pw_half complex numbers are only
-// 8-byte aligned, so tensor-map copies do not apply), split them and store
-// hi / lo in the K-major 128-byte swizzle layout (the next slice is already
-// loading into registers while the tensor core works); one thread issues the
-// MMAs and commits them to an mbarrier; tcgen05.ld drains the accumulators.
-// 64 KB of shared memory and 256 TMEM columns let two blocks share an SM.  Every wait is bounded in time and sets the plan's device
-// error flag when it gives up.
+// Data movement: the block's threads load 128 x 32 FP32 slices of the
+// real-space orbitals as 8-byte vectors, split them and store hi / lo in the
+// K-major 128-byte swizzle layout (the next slice is already loading into
+// registers while the tensor core works); one thread issues the MMAs and
+// commits them to an mbarrier; tcgen05.ld drains the accumulators.  64 KB of
+// shared memory and 256 TMEM columns let two blocks share an SM.  Every wait
+// is bounded in time and sets the plan's device error flag when it gives up.
 #include <cstdio>
 
 #include "internal.h"
-#include "tma.cuh"
+#include "umma.cuh"
 
 namespace ace {
 
@@ -43,56 +41,19 @@ struct __align__(1024) GramSmem {
     int abort;
 };
 
-// K-major operand in the 128-byte swizzle layout: rows of 128 bytes, 8-row
-// groups 1024 bytes apart (stride byte offset), descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
-    const uint32_t a = smem_addr(p);
-    return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
 // instruction descriptor: D f32, A/B tf32, both K-major, M = TM, N = TN
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t kIdesc = umma::idesc_tf32(TM, TN);
+using umma::sw128_offset;
+using umma::tf32_round;
+using umma::tmem_ld32;
+
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) { return umma::desc_sw128(p); }
 
 __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ uint32_t tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
+    umma::mma_tf32(d_tmem, a, b, kIdesc, accumulate);
 }
 
 constexpr int NTHR = 256;
-
-// Byte offset of element (row, k) of a 128-row x 32-float K-major tile in the
-// 128-byte swizzle layout: 16-byte chunk c of row r sits at chunk c ^ (r % 8).
-__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
-    return (uint32_t)(row * 128 + ((k * 4) ^ ((row & 7) << 4)));
-}
 
 __global__ void __launch_bounds__(NTHR, 2)
     gram_partial_umma(const float* __restrict__ A, const float* __restrict__ B, int m, int n, long long K,
@@ -190,7 +151,7 @@ __global__ void __launch_bounds__(NTHR, 2)
                 umma_tf32(tmem + TN, dah, dbl, 1u);
                 umma_tf32(tmem, dah, dbh, acc0);
             }
-            umma_commit(&sm.mma_done);
+            umma::commit(&sm.mma_done);
         }
         ++committed;
     }
@@ -226,21 +187,6 @@ __global__ void __launch_bounds__(NTHR, 2)
 }
 
 }  // namespace
-
-int gram_umma_chunks(long long K) { return (int)((K + KCHUNK - 1) / KCHUNK); }
-
-cudaError_t launch_gram_partial_umma(const float* A, const float* B, int m, int n, long long K, float* P, int* err,
-                                     cudaStream_t st) {
-    if (K % 2 != 0 || ((uintptr_t)A % 8) || ((uintptr_t)B % 8)) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(GramSmem) + 1024;
-    if (!stream_capturing(st)) {
-        cudaError_t e = cudaFuncSetAttribute(gram_partial_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    dim3 grid((m + TM - 1) / TM, (n + TN - 1) / TN, gram_umma_chunks(K));
-    gram_partial_umma<<<grid, NTHR, smem, st>>>(A, B, m, n, K, (long long)KCHUNK, 0, P, err);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_overlap_partial_umma(const float* A, int m, long long K, long long kchunk, float* P, int* err,
                                         cudaStream_t st) {

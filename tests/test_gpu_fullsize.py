@@ -1,7 +1,10 @@
 """Parity at the workloads' full sizes, in the launch configuration bench.py
-times (mixed precision, default plan), on outputs the oracle can compute one
-by one, plus properties that hold at any size:
+times (mixed precision, default plan):
 
+* E_x over every pair (Eq. 4), M = Phi^T W (all rows for the water boxes),
+  K psi (Eq. 5) on stored trials and the quadratic form t^T K t, against the
+  FP64 oracle's values stored by tests/golden/make_fullsize_oracle.py (the
+  oracle's own xi, not the GPU's intermediates);
 * sampled rows of W = alpha V_X Phi (Eq. 2) against the FP64 oracle;
 * M = Phi^T W recomputed in FP64 on the host from the GPU's W;
 * E_x (Eq. 4) = tr(M), and the oracle's row energies <phi_i|W_i> = M_ii;
@@ -11,6 +14,7 @@ by one, plus properties that hold at any size:
 * checkpoint save / load of the ACE vectors.
 """
 import os
+import sys
 import tempfile
 
 import numpy as np
@@ -45,13 +49,31 @@ def _lib():
 
 
 _ORACLE_ROWS = {}
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+import make_fullsize_oracle as golden  # noqa: E402
 
 
-def check_full(cfg, rows, pairs=None, n_trials=8, pair_variant=0):
+def check_golden(cfg, plan, xi, E, M, key):
+    """The stored oracle results of a full-size workload: |dE_x| per atom and
+    K psi at the metric's 1e-6, M and t^T K t at 2e-6 of their maxima."""
+    g = golden.load(key)
+    T = max(int(g["n_kpsi"]), int(g["n_q"]))
+    tr = gen.random_trials(cfg["cell"], cfg["ecut"], T, seed=int(g["trials_seed"]))
+    K = host(ace.ace_apply(plan, xi, dev(tr, plan)))
+    assert abs(E - g["E_x"]) / cfg["n_atom"] <= 1e-6
+    assert rel(K[:len(g["Kpsi"])], g["Kpsi"].astype(np.complex128)) <= 1e-6
+    assert rel(M[g["M_rows"]], g["M"]) <= 2e-6
+    nq = int(g["n_q"])
+    assert rel(gen.gamma_overlap(tr[:nq], K[:nq]), g["Q"]) <= 2e-6
+
+
+def check_full(cfg, rows, pairs=None, n_trials=8, pair_variant=0, key=None):
     n = len(cfg["psi"])
     plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], n, "mixed", pair_variant=pair_variant)
     xi, E = ace.ace_build(plan, dev(cfg["psi"], plan), cfg["alpha"], pairs=pairs)
     W, M = ace.ace_last_intermediates(plan, n)
+    if key is not None:
+        check_golden(cfg, plan, xi, E, M, key)
     Wh = host(W)
     m = oracle.half_sphere(cfg["cell"], cfg["ecut"])
     # sampled rows of W against the oracle
@@ -91,19 +113,19 @@ def test_water32_full_size(pair_variant):
     global _WATER32
     if _WATER32 is None:
         _WATER32 = gen.config_water32()
-    check_full(_WATER32, rows=[0, 77, 127], pair_variant=pair_variant)
+    check_full(_WATER32, rows=[0, 77, 127], pair_variant=pair_variant, key="water32")
 
 
 def test_water64_full_size():
     """256 orbitals, 120^3, with one of its trial sets."""
     cfg = gen.config_water64(n_trial_sets=1, T=8)
-    check_full(cfg, rows=[131])
+    check_full(cfg, rows=[131], key="water64")
 
 
 def test_localized_screened_full_size():
     """512 localised orbitals, 160^3, pairs with centre distance < 8 bohr."""
     cfg = gen.config_localized()
-    check_full(cfg, rows=[0, 300], pairs=cfg["pairs"])
+    check_full(cfg, rows=[0, 300], pairs=cfg["pairs"], key="localized")
 
 
 def _small_systems():
