@@ -120,6 +120,19 @@ void ace_plan_destroy(ace_plan* plan);
  * passes, persistent kernel, hybrid} (0 = not timed).  Any output may be NULL. */
 int ace_plan_config(const ace_plan* plan, int* pair_variant, int* pair_streams, float* tune_ms);
 
+/* The pair-tile shape of the plan's pair passes: row_block = 0 packs
+ * consecutive pairs of the row-ordered list two per transform; 2, 4 or 8
+ * packs (i1, j) with (i2, j) -- pairs sharing their column orbital -- in
+ * blocks of that many rows, so one fresh orbital and one merged accumulator
+ * update serve each transform while the block's rows stay in L2.  Plan
+ * creation times the four at the chosen pair_variant (row_block_ms[4], 0 =
+ * not timed) unless the environment fixes ACE_ROW_BLOCK.  With ACE_TUNE_CACHE
+ * naming a file, the choice of pair_variant, pair_streams and row_block is
+ * looked up there by grid, n_occ_max, precision and device before any timing
+ * and appended after it (*from_cache = 1 when it came from the file).  Any
+ * output may be NULL. */
+int ace_plan_tuning(const ace_plan* plan, int* row_block, float* row_block_ms, int* from_cache);
+
 /* Number of half-sphere plane waves and, when miller != NULL, their Miller
  * indices [n_pw_half][3] (host memory, canonical order). */
 int ace_gvec(const ace_plan* plan, int* n_pw_half, int32_t* miller);

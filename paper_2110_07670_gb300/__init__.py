@@ -25,7 +25,7 @@ SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_
            "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc",
            "ace_build_batched", "ace_save", "ace_load", "ace_build_pairs", "ace_build_finish",
            "ace_plan_config", "ace_overlap_screen", "ace_build_async", "ace_build_result",
-           "ace_check_timeout_path", "ace_scdm", "ace_apply_energy")
+           "ace_check_timeout_path", "ace_scdm", "ace_apply_energy", "ace_plan_tuning")
 
 _lib = None
 
@@ -87,6 +87,7 @@ def load(build_if_missing=False):
     lib.ace_build_result.argtypes = [P, ctypes.POINTER(f64), P]
     lib.ace_overlap_screen.argtypes = [P, P, i32, f64, P, P, ctypes.POINTER(i32), P, P]
     lib.ace_plan_config.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+    lib.ace_plan_tuning.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)]
     lib.ace_scdm.argtypes = [P, P, i32, i32, P, P, ctypes.POINTER(i32), P, P]
     lib.ace_apply_noalloc.argtypes = [P, i32, P, i32, i32, i32, P, P]
     lib.hfx_apply_exact.argtypes = [P, P, i32, f64, P, i32, P, P]
@@ -173,15 +174,21 @@ class Plan:
             pass
 
     def config(self):
-        """dict(pair_variant, pair_streams, tune_ms) of the pair-pass kernels
-        (1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid)."""
+        """dict(pair_variant, pair_streams, row_block, tune_ms, ...) of the pair-pass
+        kernels (1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid)
+        and the pair-tile shape (ace_plan_tuning)."""
         v, st = ctypes.c_int(0), ctypes.c_int(0)
         tm = (ctypes.c_float * 5)()
         _check(load().ace_plan_config(self.handle, ctypes.byref(v), ctypes.byref(st), tm))
-        return {"pair_variant": v.value, "pair_streams": st.value,
+        rb, cached = ctypes.c_int(0), ctypes.c_int(0)
+        rbm = (ctypes.c_float * 4)()
+        _check(load().ace_plan_tuning(self.handle, ctypes.byref(rb), rbm, ctypes.byref(cached)))
+        return {"pair_variant": v.value, "pair_streams": st.value, "row_block": rb.value,
+                "from_tune_cache": bool(cached.value),
                 "tune_ms": {k: round(float(x), 3) for k, x in
                             zip(("tile_1_stream", "tile_2_streams", "planes", "pipeline", "hybrid"), tm)
-                            if x > 0}}
+                            if x > 0},
+                "row_block_ms": {k: round(float(x), 3) for k, x in zip(("rows", "2", "4", "8"), rbm) if x > 0}}
 
     def _vec(self, t, name):
         if t.dtype != self.cdtype or not t.is_cuda or not t.is_contiguous() or t.dim() != 2 \

@@ -131,6 +131,8 @@ struct ace_plan {
     int variant = 1;           // pair passes: 1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid
     bool hybrid = false;       // variant 4: plane-kernel P1 in the tile layout, then the tile P2 / P3
     float tune_ms[5] = {0, 0, 0, 0, 0};  // autotune: tile x1 stream, tile x2, planes x2, pipeline, hybrid x2
+    float tune_rb_ms[4] = {0, 0, 0, 0};  // autotune of the chosen variant's row block: row order, 2, 4, 8 rows
+    int tune_cached = 0;                 // 1: the choice came from the tune cache (ACE_TUNE_CACHE)
     bool tplane = false;       // pair passes with transposed spectrum planes (plane.cuh; needs zline)
     int pair_tile = 0;         // pairs ordered in pair_tile x pair_tile orbital blocks (0: row by row; env ACE_PAIR_TILE)
     int row_block = 4;         // pairs packed column-shared in blocks of this many rows (pack_pairs_blocked;
@@ -1123,6 +1125,44 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
         set_variant(P, 1, fixed_streams ? fixed_streams : 2);
         return ACE_OK;
     }
+    // the tune cache: one line per (grid, n_occ_max, precision, device)
+    char key[256] = {0};
+    const char* cache = std::getenv("ACE_TUNE_CACHE");
+    if (cache && *cache && !fixed_streams) {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, P->dev) != cudaSuccess) {
+            cudaGetLastError();
+            prop.name[0] = 0;
+        }
+        for (char* c = prop.name; *c; ++c)
+            if (*c == ' ') *c = '_';
+        std::snprintf(key, sizeof key, "%dx%dx%d n%d f%d %s sm%d", P->n[0], P->n[1], P->n[2], P->n_occ_max,
+                      (int)sizeof(R) * 8, prop.name, P->sms);
+        if (FILE* f = std::fopen(cache, "r")) {
+            char line[512];
+            int v = 0, st = 0, rb = -1;
+            bool hit = false;
+            while (std::fgets(line, sizeof line, f)) {
+                const size_t kl = std::strlen(key);
+                int v2, s2, rb2;
+                if (std::strncmp(line, key, kl) == 0 && line[kl] == ' ' &&
+                    std::sscanf(line + kl, " = %d %d %d", &v2, &s2, &rb2) == 3 && v2 >= 1 && v2 <= 4 && s2 >= 1 &&
+                    s2 <= 8 && rb2 >= 0 && rb2 <= 64 && (v2 != 2 && v2 != 3 ? true : t_ok) && (v2 != 4 || h_ok)) {
+                    v = v2;  // the last matching line wins
+                    st = s2;
+                    rb = rb2;
+                    hit = true;
+                }
+            }
+            std::fclose(f);
+            if (hit) {
+                set_variant(P, v, st);
+                P->row_block = rb;
+                P->tune_cached = 1;
+                return ACE_OK;
+            }
+        }
+    }
     // timing pairs: the first transforms of every pair i <= j of n_occ_max
     // rows, packed as a build packs them
     const int n = P->n_occ_max;
@@ -1132,10 +1172,13 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
             pa.push_back(i);
             pb.push_back(j);
         }
-    std::vector<Quad> q;
-    pack_pairs_blocked(n, pa, pb, P->row_block, q);
-    q.resize(std::min(q.size(), (size_t)std::min(4 * P->batch, std::max(1, n * (n + 1) / 4))));
-    const int K = (int)q.size();
+    const size_t want = (size_t)std::min(4 * P->batch, std::max(1, n * (n + 1) / 4));
+    auto quads_for = [&](int rb) {
+        std::vector<Quad> q;
+        pack_pairs_blocked(n, pa, pb, rb, q);
+        q.resize(std::min(q.size(), want));
+        return q;
+    };
     cudaStream_t ts = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto cleanup = [&] {
@@ -1149,45 +1192,75 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
         cudaGetLastError();
         return fail(ACE_ERR_CUDA, "autotune: stream or event creation failed");
     }
+    // ms per run of the current variant on quads q (one warm-up, two timed runs)
+    auto time_runs = [&](const std::vector<Quad>& q, float* out) -> int {
+        const int K = (int)q.size();
+        ACE_TRY(upload_quads(P, q, ts));
+        ACE_TRY(grow(&P->d_epart, &P->epart_cap, (size_t)K * P->ntiles_last * 2));
+        R* phi = (R*)P->d_phi;
+        R* acc = (R*)P->d_acc;
+        for (int rep = 0; rep < 3; ++rep) {
+            if (rep == 1 && cudaEventRecord(e0, ts) != cudaSuccess) return fail(ACE_ERR_CUDA, "autotune: event");
+            ACE_TRY(run_pairs<R>(P, phi, phi, acc, acc, 1, P->d_quads, K, P->d_epart, ts));
+        }
+        float ms = 0;
+        if (cudaEventRecord(e1, ts) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            return fail(ACE_ERR_CUDA, "autotune: timing failed");
+        *out = ms / 2;
+        return ACE_OK;
+    };
     int rc = ACE_OK;
     float best = 1e30f;
-    int best_v = 1, best_s = 2;
+    int best_v = 1, best_s = 2, best_rb = P->row_block;
     do {
-        if ((rc = upload_quads(P, q, ts)) != ACE_OK) break;
-        if ((rc = grow(&P->d_epart, &P->epart_cap, (size_t)K * P->ntiles_last * 2)) != ACE_OK) break;
         if (cudaMemsetAsync(P->d_phi, 0, (size_t)n * P->N * sizeof(R), ts) != cudaSuccess ||
             cudaMemsetAsync(P->d_acc, 0, (size_t)n * P->N * sizeof(R), ts) != cudaSuccess) {
             rc = fail(ACE_ERR_CUDA, "autotune: memset failed");
             break;
         }
-        R* phi = (R*)P->d_phi;
-        R* acc = (R*)P->d_acc;
+        const std::vector<Quad> q = quads_for(P->row_block);
         for (const Cand& c : cand) {
             set_variant(P, c.v, c.streams);
-            for (int rep = 0; rep < 3 && rc == ACE_OK; ++rep) {
-                if (rep == 1 && cudaEventRecord(e0, ts) != cudaSuccess) rc = fail(ACE_ERR_CUDA, "autotune: event");
-                if (rc == ACE_OK) rc = run_pairs<R>(P, phi, phi, acc, acc, 1, P->d_quads, K, P->d_epart, ts);
-            }
-            if (rc != ACE_OK) break;
             float ms = 0;
-            if (cudaEventRecord(e1, ts) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                rc = fail(ACE_ERR_CUDA, "autotune: timing failed");
-                break;
-            }
-            P->tune_ms[c.slot] = ms / 2;
+            if ((rc = time_runs(q, &ms)) != ACE_OK) break;
+            P->tune_ms[c.slot] = ms;
             if (ms < best) {
                 best = ms;
                 best_v = c.v;
                 best_s = c.streams;
             }
         }
+        if (rc != ACE_OK) break;
+        // then the pair-tile shape of the chosen kernels: row order, or column-
+        // shared transforms in blocks of 2, 4 or 8 rows (pack_pairs_blocked)
+        if (!std::getenv("ACE_ROW_BLOCK")) {
+            set_variant(P, best_v, best_s);
+            const int rbs[4] = {0, 2, 4, 8};
+            float best_rb_ms = 1e30f;
+            for (int k = 0; k < 4 && rc == ACE_OK; ++k) {
+                float ms = 0;
+                if ((rc = time_runs(quads_for(rbs[k]), &ms)) != ACE_OK) break;
+                P->tune_rb_ms[k] = ms;
+                if (ms < best_rb_ms) {
+                    best_rb_ms = ms;
+                    best_rb = rbs[k];
+                }
+            }
+        }
         if (rc == ACE_OK) rc = check_device_error(P, ts);
     } while (false);
     cleanup();
     set_variant(P, best_v, best_s);
+    P->row_block = best_rb;
     P->pair_transforms = 0;
     P->launches = 0;
+    if (rc == ACE_OK && key[0]) {
+        if (FILE* f = std::fopen(cache, "a")) {
+            std::fprintf(f, "%s = %d %d %d\n", key, best_v, best_s, best_rb);
+            std::fclose(f);
+        }
+    }
     return rc;
 }
 
@@ -1732,6 +1805,15 @@ int ace_plan_config(const ace_plan* plan, int* pair_variant, int* pair_streams, 
     if (pair_streams) *pair_streams = plan->variant == 3 ? 1 : plan->pair_streams;
     if (tune_ms)
         for (int i = 0; i < 5; ++i) tune_ms[i] = plan->tune_ms[i];
+    return ACE_OK;
+}
+
+int ace_plan_tuning(const ace_plan* plan, int* row_block, float* row_block_ms, int* from_cache) {
+    if (!plan) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (row_block) *row_block = plan->row_block;
+    if (row_block_ms)
+        for (int i = 0; i < 4; ++i) row_block_ms[i] = plan->tune_rb_ms[i];
+    if (from_cache) *from_cache = plan->tune_cached;
     return ACE_OK;
 }
 

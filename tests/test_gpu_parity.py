@@ -257,6 +257,64 @@ def test_pair_variants_match_oracle(variant, streams):
     plan.close()
 
 
+@pytest.mark.parametrize("row_block", ["0", "2", "3", "4", "8"])
+def test_row_blocks_match_oracle(monkeypatch, row_block):
+    """Every pair-tile shape (row order; column-shared transforms in blocks of
+    2, 3, 4, 8 rows, with blocks that do not divide the 13 orbitals and a
+    screened list whose columns leave unpaired rows) gives the oracle's E_x,
+    W_G and K psi."""
+    monkeypatch.setenv("ACE_ROW_BLOCK", row_block)
+    tol = TOL["mixed"]
+    cell = gen.cubic_cell(9.0)
+    ecut, grid, alpha = 20.0, (32, 32, 32), 0.25
+    n = 13
+    psi0 = gen.random_orbitals(cell, ecut, n, seed=41)
+    keep = [(i, j) for i in range(n) for j in range(i, n) if i == j or (5 * i + 3 * j) % 7 < 4]
+    rp = np.zeros(n + 1, dtype=np.int32)
+    for i, _ in keep:
+        rp[i + 1] += 1
+    screened = (np.cumsum(rp).astype(np.int32), np.array([j for _, j in keep], dtype=np.int32))
+    plan = ace.Plan(grid, cell, ecut, n, "mixed", pair_variant=4)
+    assert plan.config()["row_block"] == int(row_block)
+    psi = dev(psi0, plan)
+    tr = gen.random_trials(cell, ecut, 5, seed=8)
+    for pairs in (None, screened):
+        ref = oracle.ace_build(psi0, cell, grid, ecut, alpha, pairs=pairs)
+        xi, E = ace.ace_build(plan, psi, alpha, pairs=pairs)
+        W, _ = ace.ace_last_intermediates(plan, n)
+        assert abs(E - ref["E_x"]) / (3 * n / 4) <= tol["E"]
+        assert rel(host(W), ref["W_G"]) <= tol["W"]
+        K = host(ace.ace_apply(plan, xi, dev(tr, plan)))
+        assert rel(K, oracle.ace_apply(ref["xi"], tr, ref["miller"])) <= tol["K"]
+    plan.close()
+
+
+def test_tune_cache_round_trip(monkeypatch, tmp_path):
+    """Plan creation with ACE_TUNE_CACHE: the first plan times the variants and
+    row blocks and appends its choice; a second plan of the same grid, size
+    and precision takes the same choice from the file without timing."""
+    monkeypatch.delenv("ACE_ROW_BLOCK", raising=False)
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("ACE_TUNE_CACHE", str(path))
+    s = gen.config_small()
+    p1 = ace.Plan(s["grid"], s["cell"], s["ecut"], 8, "mixed")
+    c1 = p1.config()
+    assert not c1["from_tune_cache"] and c1["row_block_ms"] and c1["tune_ms"]
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("32x32x32 n8 f32 ")
+    assert lines[0].endswith(f"= {c1['pair_variant']} {c1['pair_streams']} {c1['row_block']}")
+    p2 = ace.Plan(s["grid"], s["cell"], s["ecut"], 8, "mixed")
+    c2 = p2.config()
+    assert c2["from_tune_cache"] and not c2["tune_ms"] and not c2["row_block_ms"]
+    assert (c2["pair_variant"], c2["pair_streams"], c2["row_block"]) == \
+        (c1["pair_variant"], c1["pair_streams"], c1["row_block"])
+    xi1, E1 = ace.ace_build(p1, dev(s["psi"], p1), s["alpha"])
+    xi2, E2 = ace.ace_build(p2, dev(s["psi"], p2), s["alpha"])
+    assert E1 == E2
+    p1.close()
+    p2.close()
+
+
 def test_automatic_variant_choice_and_rejections():
     s = gen.config_small()
     n = len(s["psi"])
