@@ -91,7 +91,7 @@ struct ace_plan {
     int sms = 152;             // SMs of the plan's device
     int gram_kmax = 0;         // at most this many reals per K slice of the streamed Gram (0: one wave of
                                // blocks; env ACE_GRAM_KMAX)
-    float* d_csplit = nullptr; // TF32 hi / lo of the apply's C [2][T][np]
+    float* d_csplit = nullptr; // TF32 hi / lo images of the apply's C (apply_product_scratch floats)
     size_t csplit_cap = 0;
     int prec = ACE_MIXED;
     int n[3] = {0, 0, 0};
@@ -1032,10 +1032,9 @@ int apply_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, v
     mark(P, PH_XI, st);
     if constexpr (sizeof(R) == 4) {
         if (P->tensor_gram) {  // -xi C on the tensor cores
-            const size_t np = (size_t)apply_product_np(n_occ);
-            ACE_TRY(grow(&P->d_csplit, &P->csplit_cap, 2 * (size_t)T * np));
-            ACE_CKL(launch_apply_product(P->d_C, T, n_occ, (const float*)xi, 2LL * P->npw, P->d_csplit,
-                                         P->d_csplit + (size_t)T * np, (float*)out, P->sms, P->d_err, st));
+            ACE_TRY(grow(&P->d_csplit, &P->csplit_cap, apply_product_scratch(T, n_occ)));
+            ACE_CKL(launch_apply_product(P->d_C, T, n_occ, (const float*)xi, 2LL * P->npw, P->d_csplit, (float*)out,
+                                         P->sms, P->d_err, st));
             mark(P, PH_IDLE, st);
             return ACE_OK;
         }

@@ -172,11 +172,11 @@ long long gram_stream_kchunk(int m, int n, long long K, int sms, int max_k);
 cudaError_t launch_gram_stream(const float* A, const float* B, int m, int n, long long K, long long kchunk, float* P,
                                int* err, cudaStream_t st);
 // out[t][j] = -sum_k C[t][k] xi[k][j] on tcgen05 (K psi = -xi C^T, Eq. 5):
-// C [T][n] double, xi [n][K] float, out [T][K] float; Ch, Cl: scratch of
-// T * apply_product_np(n) floats each (16-byte aligned) for C's TF32 split.
-int apply_product_np(int n);
-cudaError_t launch_apply_product(const double* C, int T, int n, const float* xi, long long K, float* Ch, float* Cl,
-                                 float* out, int sms, int* err, cudaStream_t st);
+// C [T][n] double, xi [n][K] float, out [T][K] float; Cimg: scratch of
+// apply_product_scratch(T, n) floats (16-byte aligned) for C's TF32 split.
+size_t apply_product_scratch(int T, int n);
+cudaError_t launch_apply_product(const double* C, int T, int n, const float* xi, long long K, float* Cimg, float* out,
+                                 int sms, int* err, cudaStream_t st);
 // Overlap partials |A|^T |A| (A [m][K], K-slices of kchunk, a multiple of 32,
 // each accumulated in TMEM) on tcgen05: P [ceil(K / kchunk)][m][m] float.
 cudaError_t launch_overlap_partial_umma(const float* A, int m, long long K, long long kchunk, float* P, int* err,

@@ -125,31 +125,32 @@ __global__ void gram_finish_kernel(const PT* __restrict__ P, int nchunk, const R
     G[(long long)i * ldg + j] = 2.0 * s - g0;
 }
 
-// The same from single-precision partials with many K slices: a block owns 64
-// consecutive elements and its four warp pairs sum interleaved quarters of
-// the slices (four loads in flight each), combined in a fixed order.
+// The same from single-precision partials with many K slices: a block owns
+// 32 consecutive elements (one per lane) and its eight warps sum interleaved
+// eighths of the slices (four loads in flight each), combined in a fixed order.
 __global__ void __launch_bounds__(256) gram_finish_f32_kernel(const float* __restrict__ P, int nchunk,
                                                               const float* __restrict__ A,
                                                               const float* __restrict__ B, int m, int n, long long K,
                                                               double* __restrict__ G, int ldg) {
-    __shared__ double part[4][64];
+    __shared__ double part[8][32];
     const long long tot = (long long)m * n;
-    const long long e = (long long)blockIdx.x * 64 + (threadIdx.x & 63);
-    const int q = threadIdx.x >> 6;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long e = (long long)blockIdx.x * 32 + lane;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     if (e < tot) {
-        int c = q;
-        for (; c + 12 < nchunk; c += 16) {
+        int c = w;
+        for (; c + 24 < nchunk; c += 32) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) s[u] += (double)P[(long long)(c + 4 * u) * tot + e];
+            for (int u = 0; u < 4; ++u) s[u] += (double)P[(long long)(c + 8 * u) * tot + e];
         }
-        for (; c < nchunk; c += 4) s[0] += (double)P[(long long)c * tot + e];
+        for (; c < nchunk; c += 8) s[0] += (double)P[(long long)c * tot + e];
     }
-    part[q][threadIdx.x & 63] = (s[0] + s[1]) + (s[2] + s[3]);
+    part[w][lane] = (s[0] + s[1]) + (s[2] + s[3]);
     __syncthreads();
-    if (q == 0 && e < tot) {
+    if (w == 0 && e < tot) {
+        double sum = 0.0;
+        for (int k = 0; k < 8; ++k) sum += part[k][lane];
         const int i = (int)(e / n), j = (int)(e % n);
-        const double sum = (part[0][threadIdx.x] + part[1][threadIdx.x]) + (part[2][threadIdx.x] + part[3][threadIdx.x]);
         const double g0 = double(A[(long long)i * K]) * double(B[(long long)j * K]) +
                           double(A[(long long)i * K + 1]) * double(B[(long long)j * K + 1]);
         G[(long long)i * ldg + j] = 2.0 * sum - g0;
@@ -507,7 +508,7 @@ template cudaError_t launch_overlap_finish<double>(const double*, int, int, doub
 cudaError_t launch_gram_finish_f32(const float* P, int nchunk, const float* A, const float* B, int m, int n,
                                    long long K, double* G, int ldg, cudaStream_t st) {
     const long long tot = (long long)m * n;
-    gram_finish_f32_kernel<<<(unsigned)((tot + 63) / 64), 256, 0, st>>>(P, nchunk, A, B, m, n, K, G, ldg);
+    gram_finish_f32_kernel<<<(unsigned)((tot + 31) / 32), 256, 0, st>>>(P, nchunk, A, B, m, n, K, G, ldg);
     return cudaGetLastError();
 }
 
