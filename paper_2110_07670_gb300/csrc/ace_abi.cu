@@ -763,7 +763,10 @@ int finish_enqueue(ace_plan* P, const void* psi_G, int n_occ, const void* WG_in,
     mark(P, PH_FACTOR, st);
     ACE_CKL(launch_neg_cholesky_inverse(P->d_M, n_occ, P->d_L, P->d_Linv, P->d_status, st));
     mark(P, PH_XI, st);
-    ACE_CKL(launch_gemm_nn<R>(P->d_Linv, n_occ, n_occ, (const R*)WG, 2LL * P->npw, 1.0, (R*)xi, true, st, true));
+    if constexpr (sizeof(R) == 4)  // float-float: double-precision accuracy on the FP32 pipes
+        ACE_CKL(launch_gemm_nn_ff(P->d_Linv, n_occ, n_occ, (const float*)WG, 2LL * P->npw, 1.0, (float*)xi, true, st));
+    else
+        ACE_CKL(launch_gemm_nn<R>(P->d_Linv, n_occ, n_occ, (const R*)WG, 2LL * P->npw, 1.0, (R*)xi, true, st, true));
     mark(P, PH_IDLE, st);
     ACE_CK(cudaMemcpyAsync(&P->h_res->status, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     P->pending_n_occ = n_occ;

@@ -253,6 +253,11 @@ cudaError_t launch_polar_start(const T* A, int n, long long m, const int* piv, d
 cudaError_t launch_newton_schulz_step(double* X, double* T, double* Y, int n, double alpha, double* err,
                                       cudaStream_t st);
 
+// The same product with A double, B and out float in float-float arithmetic
+// (about 2^-44 of sum |A||B|) on the FP32 pipes.
+cudaError_t launch_gemm_nn_ff(const double* A, int m, int k, const float* B, long long ncols, double alpha, float* out,
+                              bool lower, cudaStream_t st);
+
 // Cholesky of -M and the inverse of its factor, in double, one thread block.
 // status: 0 ok, 1 not positive definite.
 cudaError_t launch_neg_cholesky_inverse(const double* M, int n, double* L, double* Linv, int* status,

@@ -512,6 +512,84 @@ cudaError_t launch_gram_finish_f32(const float* P, int nchunk, const float* A, c
     return cudaGetLastError();
 }
 
+// out[i][c] = alpha sum_k A[i][k] B[k][c] with A double, B and out float, in
+// float-float arithmetic on the FP32 pipes (GB300's FP64 rate is 1/64 of
+// its FP32 rate): A[i][k] = ah + al as two floats, each product ah b split
+// exactly into ph + pl (an FMA gives pl), al b added to the low part, and the
+// running sum kept as an unevaluated float pair (hi, lo) by TwoSum.  The sum
+// is good to about 2^-44 of sum |A||B| -- the double-precision form's
+// accuracy once rounded to the float output.  Tiling as gemm_nn_kernel.
+__global__ void __launch_bounds__(256) gemm_nn_ff_kernel(const double* __restrict__ A, int m, int kdim,
+                                                         const float* __restrict__ B, long long ncols, double alpha,
+                                                         float* __restrict__ out, int lower) {
+    __shared__ float Ah[NK][NM], Al[NK][NM];
+    __shared__ float Bs[NK][NC];
+    const int i0 = blockIdx.x * NM;
+    const long long c0 = (long long)blockIdx.y * NC;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = 0.f;
+    const int kend = lower ? (kdim < i0 + NM ? kdim : i0 + NM) : kdim;
+    for (int k0 = 0; k0 < kend; k0 += NK) {
+        for (int e = threadIdx.x; e < NK * NM; e += 256) {
+            const int r = e / NK, c = e % NK;
+            const double v = (i0 + r < m && k0 + c < kdim) ? A[(long long)(i0 + r) * kdim + k0 + c] : 0.0;
+            const float h = __double2float_rn(v);
+            Ah[c][r] = h;
+            Al[c][r] = __double2float_rn(v - (double)h);
+        }
+        for (int e = threadIdx.x; e < NK * NC; e += 256) {
+            const int r = e / NC, c = e % NC;
+            Bs[r][c] = (k0 + r < kdim && c0 + c < ncols) ? B[(long long)(k0 + r) * ncols + c0 + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < NK; ++c) {
+            float ah[4], al[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                ah[a] = Ah[c][ty + 8 * a];
+                al[a] = Al[c][ty + 8 * a];
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[c][tx + 32 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const float ph = __fmul_rn(ah[a], bv[b]);
+                    const float pl = __fmaf_rn(al[a], bv[b], __fmaf_rn(ah[a], bv[b], -ph));
+                    const float t = __fadd_rn(hi[a][b], ph);
+                    const float bb = __fsub_rn(t, hi[a][b]);
+                    const float err = __fadd_rn(__fsub_rn(hi[a][b], __fsub_rn(t, bb)), __fsub_rn(ph, bb));
+                    hi[a][b] = t;
+                    lo[a][b] = __fadd_rn(lo[a][b], __fadd_rn(err, pl));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = i0 + ty + 8 * a;
+        if (i >= m) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const long long c = c0 + tx + 32 * b;
+            if (c < ncols) out[(long long)i * ncols + c] = (float)(alpha * ((double)hi[a][b] + (double)lo[a][b]));
+        }
+    }
+}
+
+cudaError_t launch_gemm_nn_ff(const double* A, int m, int k, const float* B, long long ncols, double alpha, float* out,
+                              bool lower, cudaStream_t st) {
+    dim3 grid((m + NM - 1) / NM, (unsigned)((ncols + NC - 1) / NC));
+    gemm_nn_ff_kernel<<<grid, 256, 0, st>>>(A, m, k, B, ncols, alpha, out, lower ? 1 : 0);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_gemm_nn(const double* A, int m, int k, const R* B, long long ncols, double alpha, R* out,
                            bool fp64_math, cudaStream_t st, bool lower) {
