@@ -161,6 +161,7 @@ struct ace_plan {
     size_t S_cap = 0;
     double* d_L = nullptr;
     double* d_Linv = nullptr;
+    double* d_chol = nullptr;  // blocked Cholesky workspace (neg_cholesky_work(n_occ_max) doubles)
     double* d_E = nullptr;
     int* d_status = nullptr;
     int* d_err = nullptr;
@@ -761,7 +762,13 @@ int finish_enqueue(ace_plan* P, const void* psi_G, int n_occ, const void* WG_in,
     const cx<R>* WG = (const cx<R>*)WG_in;
     ACE_TRY(gram<R>(P, psi, n_occ, WG, n_occ, P->d_M, st));
     mark(P, PH_FACTOR, st);
-    ACE_CKL(launch_neg_cholesky_inverse(P->d_M, n_occ, P->d_L, P->d_Linv, P->d_status, st));
+    if (n_occ > 64) {  // over many blocks: one block's FP64 rate would take milliseconds
+        int nl = 1;
+        ACE_CKL(launch_neg_cholesky_blocked(P->d_M, n_occ, P->d_L, P->d_Linv, P->d_status, P->d_chol, &nl, st));
+        P->launches += nl - 1;
+    } else {
+        ACE_CKL(launch_neg_cholesky_inverse(P->d_M, n_occ, P->d_L, P->d_Linv, P->d_status, st));
+    }
     mark(P, PH_XI, st);
     if constexpr (sizeof(R) == 4)  // float-float: double-precision accuracy on the FP32 pipes
         ACE_CKL(launch_gemm_nn_ff(P->d_Linv, n_occ, n_occ, (const float*)WG, 2LL * P->npw, 1.0, (float*)xi, true, st));
@@ -1074,7 +1081,7 @@ void free_plan(ace_plan* P) {
     for (auto e : P->aux_ev) cudaEventDestroy(e);
     if (P->fork_ev) cudaEventDestroy(P->fork_ev);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
-                    P->d_WG, P->d_M, P->d_S, P->d_L, P->d_Linv, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
+                    P->d_WG, P->d_M, P->d_S, P->d_L, P->d_Linv, P->d_chol, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
                     P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_kern_t, P->d_kern_r, P->d_pipe, P->d_csplit,
                     P->scdm.gv, P->scdm.dpsi, P->scdm.dens, P->scdm.isel, P->scdm.A, P->scdm.nu,
                     P->scdm.part, P->scdm.mats, P->scdm.ipiv};
@@ -1436,6 +1443,7 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     ACE_TRY(dalloc((void**)&P->d_M, nn * sizeof(double)));
     ACE_TRY(dalloc((void**)&P->d_L, nn * sizeof(double)));
     ACE_TRY(dalloc((void**)&P->d_Linv, nn * sizeof(double)));
+    ACE_TRY(dalloc((void**)&P->d_chol, neg_cholesky_work(P->n_occ_max) * sizeof(double)));
     ACE_TRY(dalloc((void**)&P->d_E, (1 + 16384) * sizeof(double)));  // E_x, then the energy reduction's block sums
     ACE_TRY(dalloc((void**)&P->d_status, sizeof(int)));
     ACE_TRY(dalloc((void**)&P->d_err, sizeof(int)));

@@ -258,6 +258,13 @@ cudaError_t launch_newton_schulz_step(double* X, double* T, double* Y, int n, do
 cudaError_t launch_gemm_nn_ff(const double* A, int m, int k, const float* B, long long ncols, double alpha, float* out,
                               bool lower, cudaStream_t st);
 
+// The same over many thread blocks (blocked right-looking factorisation and
+// column-block inverse): work holds neg_cholesky_work(n) doubles; *nlaunch
+// receives the number of kernels launched.
+size_t neg_cholesky_work(int n);
+cudaError_t launch_neg_cholesky_blocked(const double* M, int n, double* L, double* Linv, int* status, double* work,
+                                        int* nlaunch, cudaStream_t st);
+
 // Cholesky of -M and the inverse of its factor, in double, one thread block.
 // status: 0 ok, 1 not positive definite.
 cudaError_t launch_neg_cholesky_inverse(const double* M, int n, double* L, double* Linv, int* status,

@@ -601,6 +601,168 @@ cudaError_t launch_gemm_nn(const double* A, int m, int k, const R* B, long long 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ blocked Cholesky
+// -M = L L^T and X = L^-1 in double over many thread blocks, for the larger
+// occupied sets: blocks of CB x CB, the working matrix padded to np = CB
+// ceil(n / CB) with the identity outside the n x n part.  Step k of the
+// right-looking factorisation: the diagonal block and its inverse T_kk in one
+// block (shared memory), the panel L_ik = A_ik T_kk^T for the rows below, the
+// trailing update A_ij -= L_ik L_jk^T of the lower triangle; then X by column
+// blocks, X_ic = T_ii (delta_ic I - sum_{c <= j < i} L_ij X_jc).
+constexpr int CB = 32;
+
+__global__ void chol_init_kernel(const double* __restrict__ M, int n, int np, double* __restrict__ W,
+                                 double* __restrict__ X, int* __restrict__ status) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e == 0) *status = 0;
+    if (e >= (long long)np * np) return;
+    const int i = (int)(e / np), j = (int)(e % np);
+    double v = i == j ? 1.0 : 0.0;
+    if (i < n && j < n) v = i >= j ? -0.5 * (M[(long long)i * n + j] + M[(long long)j * n + i]) : 0.0;
+    W[e] = v;
+    X[e] = 0.0;
+}
+
+__global__ void __launch_bounds__(1024) chol_diag_kernel(double* __restrict__ W, int np, int k,
+                                                         double* __restrict__ T, int* __restrict__ status) {
+    __shared__ double a[CB][CB + 1], t[CB][CB + 1];
+    const int r = threadIdx.x / CB, c = threadIdx.x % CB;
+    double* blk = W + (long long)(k * CB) * np + k * CB;
+    a[r][c] = blk[(long long)r * np + c];
+    __syncthreads();
+    for (int p = 0; p < CB; ++p) {
+        if (threadIdx.x == 0) {
+            double d = a[p][p];
+            if (!(d > 0.0)) {
+                atomicExch(status, 1);
+                d = 1.0;
+            }
+            a[p][p] = sqrt(d);
+        }
+        __syncthreads();
+        if (r > p && c == p) a[r][p] /= a[p][p];
+        __syncthreads();
+        if (r > p && c > p && c <= r) a[r][c] -= a[r][p] * a[c][p];
+        __syncthreads();
+    }
+    blk[(long long)r * np + c] = c <= r ? a[r][c] : 0.0;
+    if (threadIdx.x < CB) {  // column c of the inverse of the lower-triangular factor
+        const int col = threadIdx.x;
+        for (int i = 0; i < CB; ++i) {
+            if (i < col) {
+                t[i][col] = 0.0;
+            } else if (i == col) {
+                t[i][col] = 1.0 / a[i][i];
+            } else {
+                double s = 0.0;
+                for (int j = col; j < i; ++j) s += a[i][j] * t[j][col];
+                t[i][col] = -s / a[i][i];
+            }
+        }
+    }
+    __syncthreads();
+    T[(long long)k * CB * CB + r * CB + c] = t[r][c];
+}
+
+__global__ void __launch_bounds__(1024) chol_panel_kernel(double* __restrict__ W, int np, int k,
+                                                          const double* __restrict__ T) {
+    __shared__ double a[CB][CB + 1], t[CB][CB + 1];
+    const int r = threadIdx.x / CB, c = threadIdx.x % CB;
+    const int i = k + 1 + blockIdx.x;
+    double* blk = W + (long long)(i * CB) * np + k * CB;
+    a[r][c] = blk[(long long)r * np + c];
+    t[r][c] = T[(long long)k * CB * CB + r * CB + c];
+    __syncthreads();
+    double s = 0.0;
+    for (int q = 0; q <= c; ++q) s += a[r][q] * t[c][q];  // (A T^T)[r][c], T lower triangular
+    __syncthreads();
+    blk[(long long)r * np + c] = s;
+}
+
+__global__ void __launch_bounds__(1024) chol_update_kernel(double* __restrict__ W, int np, int k) {
+    __shared__ double li[CB][CB + 1], lj[CB][CB + 1];
+    const int r = threadIdx.x / CB, c = threadIdx.x % CB;
+    // lower-triangle tile (ii, jj), jj <= ii, of the trailing matrix
+    const int tb = blockIdx.x;
+    int ii = (int)((sqrt(8.0 * tb + 1.0) - 1.0) * 0.5);
+    while ((ii + 1) * (ii + 2) / 2 <= tb) ++ii;
+    while (ii * (ii + 1) / 2 > tb) --ii;
+    const int jj = tb - ii * (ii + 1) / 2;
+    const int i = k + 1 + ii, j = k + 1 + jj;
+    li[r][c] = W[(long long)(i * CB + r) * np + k * CB + c];
+    lj[r][c] = W[(long long)(j * CB + r) * np + k * CB + c];
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll 8
+    for (int q = 0; q < CB; ++q) s += li[r][q] * lj[c][q];
+    W[(long long)(i * CB + r) * np + j * CB + c] -= s;
+}
+
+__global__ void __launch_bounds__(1024) chol_inverse_kernel(const double* __restrict__ W, int np,
+                                                            const double* __restrict__ T, double* __restrict__ X) {
+    __shared__ double l[CB][CB + 1], x[CB][CB + 1], s[CB][CB + 1];
+    const int r = threadIdx.x / CB, cc = threadIdx.x % CB;
+    const int nb = np / CB, c = blockIdx.x;
+    for (int i = c; i < nb; ++i) {
+        double acc = (i == c && r == cc) ? 1.0 : 0.0;
+        for (int j = c; j < i; ++j) {
+            l[r][cc] = W[(long long)(i * CB + r) * np + j * CB + cc];
+            x[r][cc] = X[(long long)(j * CB + r) * np + c * CB + cc];  // written by this block at row block j
+            __syncthreads();
+#pragma unroll 8
+            for (int q = 0; q < CB; ++q) acc -= l[r][q] * x[q][cc];
+            __syncthreads();
+        }
+        s[r][cc] = acc;
+        l[r][cc] = T[(long long)i * CB * CB + r * CB + cc];
+        __syncthreads();
+        double v = 0.0;
+        for (int q = 0; q <= r; ++q) v += l[r][q] * s[q][cc];
+        X[(long long)(i * CB + r) * np + c * CB + cc] = v;
+        __syncthreads();
+    }
+}
+
+__global__ void chol_extract_kernel(const double* __restrict__ W, const double* __restrict__ X, int n, int np,
+                                    double* __restrict__ L, double* __restrict__ Linv) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n * n) return;
+    const int i = (int)(e / n), j = (int)(e % n);
+    L[e] = j <= i ? W[(long long)i * np + j] : 0.0;
+    Linv[e] = j <= i ? X[(long long)i * np + j] : 0.0;
+}
+
+size_t neg_cholesky_work(int n) {
+    const size_t np = (size_t)(n + CB - 1) / CB * CB;
+    return 2 * np * np + np * CB;
+}
+
+cudaError_t launch_neg_cholesky_blocked(const double* M, int n, double* L, double* Linv, int* status, double* work,
+                                        int* nlaunch, cudaStream_t st) {
+    const int np = (n + CB - 1) / CB * CB, nb = np / CB;
+    double* W = work;
+    double* X = work + (size_t)np * np;
+    double* T = X + (size_t)np * np;
+    int count = 0;
+    chol_init_kernel<<<(unsigned)(((long long)np * np + 255) / 256), 256, 0, st>>>(M, n, np, W, X, status);
+    ++count;
+    for (int k = 0; k < nb; ++k) {
+        chol_diag_kernel<<<1, CB * CB, 0, st>>>(W, np, k, T, status);
+        ++count;
+        const int m = nb - k - 1;
+        if (m > 0) {
+            chol_panel_kernel<<<m, CB * CB, 0, st>>>(W, np, k, T);
+            chol_update_kernel<<<m * (m + 1) / 2, CB * CB, 0, st>>>(W, np, k);
+            count += 2;
+        }
+    }
+    chol_inverse_kernel<<<nb, CB * CB, 0, st>>>(W, np, T, X);
+    chol_extract_kernel<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, st>>>(W, X, n, np, L, Linv);
+    count += 2;
+    if (nlaunch) *nlaunch = count;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_neg_cholesky_inverse(const double* M, int n, double* L, double* Linv, int* status,
                                         cudaStream_t st) {
     const size_t smem = (size_t)n * n * sizeof(double);

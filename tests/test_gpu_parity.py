@@ -289,6 +289,33 @@ def test_row_blocks_match_oracle(monkeypatch, row_block):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_blocked_cholesky_70_orbitals(prec):
+    """70 orbitals take the multi-block Cholesky and inverse (blocks of 32,
+    padded to 96): E_x, M and K psi against the oracle; and a zero orbital in
+    the third block (M exactly singular) is rejected as not positive
+    definite."""
+    tol = TOL[prec]
+    s = gen.config_small()
+    n = 70
+    psi0 = gen.random_orbitals(s["cell"], s["ecut"], n, seed=61)
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, prec)
+    ref = oracle.ace_build(psi0, s["cell"], s["grid"], s["ecut"], s["alpha"])
+    xi, E = ace.ace_build(plan, dev(psi0, plan), s["alpha"])
+    _, M = ace.ace_last_intermediates(plan, n)
+    assert abs(E - ref["E_x"]) / (3 * n / 4) <= tol["E"]
+    assert np.abs(M - ref["M"]).max() <= tol["W"] * np.abs(ref["M"]).max()
+    tr = gen.random_trials(s["cell"], s["ecut"], 6, seed=62)
+    K = host(ace.ace_apply(plan, xi, dev(tr, plan)))
+    assert rel(K, oracle.ace_apply(ref["xi"], tr, ref["miller"])) <= tol["K"]
+    dep = psi0.copy()
+    dep[67] = 0.0
+    with pytest.raises(ace.AceError) as e:
+        ace.ace_build(plan, dev(dep, plan), s["alpha"])
+    assert e.value.code == -3
+    plan.close()
+
+
 def test_tune_cache_round_trip(monkeypatch, tmp_path):
     """Plan creation with ACE_TUNE_CACHE: the first plan times the variants and
     row blocks and appends its choice; a second plan of the same grid, size
