@@ -110,6 +110,7 @@ __device__ __forceinline__ void chunk_at(const Shape& a, int k, int z0, int y0, 
 
 // Runtime tile geometry (any grid) ...
 struct DynShape {
+    static constexpr bool kCube = false;
     static constexpr int kMaxThreads = 512;
     static constexpr int kMinBlocks = 1;
     int n0, n1, n2, tz, ty, tx, axes;
@@ -213,6 +214,7 @@ __device__ __forceinline__ void static_fft_rows_swizzled(cx<R>* buf, const cx<R>
 // index division becomes a multiply-shift and every stage loop a fixed count.
 template <int N, int TZ, int TY, int TX, int NT>
 struct CubeShape {
+    static constexpr bool kCube = true;
     static constexpr int kMaxThreads = NT;
     // two resident plane blocks where two N x N complex tiles fit in shared
     // memory (N <= 108); otherwise one, with the whole register file for it
@@ -256,6 +258,39 @@ struct CubeShape {
         static_fft<SGN, N, TY * TX, TY * TX, 1, NT, R>(t, tw);
     }
 };
+
+// The tile's four consecutive elements e .. e + 3 (e a multiple of 4 inside one
+// row).  Single-precision compile-time tiles read them as two 16-byte shared
+// loads: the plane swizzle keeps an aligned group of four x positions in one
+// aligned group of four slots, element i in slot i ^ c with c the low two bits
+// of the row's swizzle word, so the first load takes the slot pair holding
+// elements 0 and 1 and a swap inside each pair undoes c's low bit.  (Four
+// 8-byte loads at a 32-byte lane stride conflicted 8-way in the banks.)
+template <typename Shape, typename R>
+__device__ __forceinline__ void tile_load4(const Shape& S, const cx<R>* tile, int e, cx<R> (&v)[4]) {
+    if constexpr (sizeof(R) == 4 && Shape::kCube) {
+        int base = e, c = 0;
+        if constexpr (Shape::kSwzTile) {
+            const int row = e / Shape::n2, col = e - row * Shape::n2;
+            const int k = ((col >> 4) & 7) | ((row & 1) << 3);
+            base = row * Shape::n2 + (col ^ (k & 12));
+            c = k & 3;
+        }
+        const int h = (c >> 1) & 1;
+        const float4 q0 = *reinterpret_cast<const float4*>(tile + base + 2 * h);
+        const float4 q1 = *reinterpret_cast<const float4*>(tile + base + 2 * (h ^ 1));
+        const bool sw = (c & 1) != 0;
+        v[0] = sw ? mk(q0.z, q0.w) : mk(q0.x, q0.y);
+        v[1] = sw ? mk(q0.x, q0.y) : mk(q0.z, q0.w);
+        v[2] = sw ? mk(q1.z, q1.w) : mk(q1.x, q1.y);
+        v[3] = sw ? mk(q1.x, q1.y) : mk(q1.z, q1.w);
+    } else {
+        v[0] = tile[S.slot(e)];
+        v[1] = tile[S.slot(e + 1)];
+        v[2] = tile[S.slot(e + 2)];
+        v[3] = tile[S.slot(e + 3)];
+    }
+}
 
 template <typename Shape, typename R, int PRO, int EPI, int MID, int SGN>
 __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pass(PassArgs a) {
@@ -530,7 +565,8 @@ __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pa
                 const int e = g << 2;
                 const int ex = e % S.tx, ey = (e / S.tx) % S.ty, ez = e / txy;
                 const long long r = ((long long)(z0 + ez) * S.n1 + (y0 + ey)) * S.n2 + (x0 + ex);
-                const cx<R> v[4] = {tile[S.slot(e)], tile[S.slot(e + 1)], tile[S.slot(e + 2)], tile[S.slot(e + 3)]};
+                cx<R> v[4];
+                tile_load4(S, tile, e, v);
                 st4(accl + q.a * N + r, V4<R>{v[0].re * s, v[1].re * s, v[2].re * s, v[3].re * s});
                 if (q.c >= 0) st4(accl + q.c * N + r, V4<R>{v[0].im * s, v[1].im * s, v[2].im * s, v[3].im * s});
             }
@@ -582,7 +618,8 @@ __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pa
                 if (ee[u] < 0) continue;
                 const int e = ee[u];
                 const long long r = rr[u];
-                const cx<R> v[4] = {tile[S.slot(e)], tile[S.slot(e + 1)], tile[S.slot(e + 2)], tile[S.slot(e + 3)]};
+                cx<R> v[4];
+                tile_load4(S, tile, e, v);
                 const V4<R> v1 = {v[0].re, v[1].re, v[2].re, v[3].re};
                 const V4<R> v2 = {v[0].im, v[1].im, v[2].im, v[3].im};
                 V4<R> wa = mul4(v1, rb[u]);
