@@ -11,7 +11,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libace_gb300.so")
 SOURCES = ["passes.cu", "cube_a.cu", "cube_b.cu", "cube_c.cu", "cube_dispatch.cu", "la.cu", "ace_abi.cu",
-           "noalloc.cu", "umma_gram.cu", "umma_stream.cu", "scdm.cu"]
+           "noalloc.cu", "umma_stream.cu", "scdm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                      "-I", CSRC]

@@ -884,15 +884,13 @@ int overlap_impl(ace_plan* P, const void* psi_G, int n, double rho_cut, int32_t*
     bool done = false;
     if constexpr (sizeof(R) == 4) {
         if (P->tensor_gram && K % 2 == 0) {
-            // K-slices of at most 16384 points (each summed in FP32 in TMEM,
-            // the slices in FP64), at least about two blocks per SM
-            const long long tiles = (long long)((n + 127) / 128) * ((n + 127) / 128);
-            long long kc = (K + std::max<long long>(1, 304 / tiles) - 1) / std::max<long long>(1, 304 / tiles);
-            kc = std::min<long long>(16384, (kc + 31) / 32 * 32);
+            // the streamed tcgen05 Gram of |phi| (about one block per SM, K
+            // slices summed in FP64 by the finish)
+            const long long kc = gram_stream_kchunk(n, n, K, P->sms, P->gram_kmax);
             const int nchunk = (int)((K + kc - 1) / kc);
             ACE_TRY(grow(&P->d_part, &P->part_cap, ((size_t)nchunk * n * n + 1) / 2));
             float* part = reinterpret_cast<float*>(P->d_part);
-            ACE_CKL(launch_overlap_partial_umma((const float*)phi, n, K, kc, part, P->d_err, st));
+            ACE_CKL(launch_gram_stream((const float*)phi, (const float*)phi, n, n, K, kc, part, P->d_err, st, true));
             ACE_CKL(launch_overlap_finish<float>(part, nchunk, n, scale, P->d_S, st));
             done = true;
         }

@@ -169,18 +169,15 @@ cudaError_t launch_gram_partial(const R* A, const R* B, int m, int n, long long 
 // multiple of 32 from gram_stream_kchunk (about one block per SM, at most
 // max_k reals per slice when max_k > 0); err: device error flag for bounded waits.
 long long gram_stream_kchunk(int m, int n, long long K, int sms, int max_k);
+// absval: products of |A| and |B| (the overlap integrals of the s-MTACE screen).
 cudaError_t launch_gram_stream(const float* A, const float* B, int m, int n, long long K, long long kchunk, float* P,
-                               int* err, cudaStream_t st);
+                               int* err, cudaStream_t st, bool absval = false);
 // out[t][j] = -sum_k C[t][k] xi[k][j] on tcgen05 (K psi = -xi C^T, Eq. 5):
 // C [T][n] double, xi [n][K] float, out [T][K] float; Cimg: scratch of
 // apply_product_scratch(T, n) floats (16-byte aligned) for C's TF32 split.
 size_t apply_product_scratch(int T, int n);
 cudaError_t launch_apply_product(const double* C, int T, int n, const float* xi, long long K, float* Cimg, float* out,
                                  int sms, int* err, cudaStream_t st);
-// Overlap partials |A|^T |A| (A [m][K], K-slices of kchunk, a multiple of 32,
-// each accumulated in TMEM) on tcgen05: P [ceil(K / kchunk)][m][m] float.
-cudaError_t launch_overlap_partial_umma(const float* A, int m, long long K, long long kchunk, float* P, int* err,
-                                        cudaStream_t st);
 // The same on CUDA cores with double partials over nchunk K-slices.
 template <typename R>
 cudaError_t launch_overlap_partial(const R* A, int m, long long K, int nchunk, double* P, cudaStream_t st);

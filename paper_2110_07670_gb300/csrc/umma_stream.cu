@@ -169,6 +169,8 @@ __device__ __forceinline__ void ws_drain(WsSmem& sm, uint32_t tmem, int set, boo
 // K range [bz kchunk, min(K, (bz + 1) kchunk)).  P[bz][i][j] = the slice's sum.
 // Producer thread p owns, in every stage, the K pair 2 (p % 16) of rows
 // p / 16 + 16 u (u = 0..7) of A and of B.
+// ABS: the products of |A| and |B| (the s-MTACE overlap integrals).
+template <bool ABS>
 __global__ void __launch_bounds__(NTHR, 1)
     gram_stream(const float* __restrict__ A, const float* __restrict__ B, int m, int n, long long K, long long kchunk,
                 float* __restrict__ P, int* err) {
@@ -215,8 +217,8 @@ __global__ void __launch_bounds__(NTHR, 1)
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
                 uint32_t hx, lx, hy, ly;
-                umma::split_tf32(r[u].x, hx, lx);
-                umma::split_tf32(r[u].y, hy, ly);
+                umma::split_tf32(ABS ? fabsf(r[u].x) : r[u].x, hx, lx);
+                umma::split_tf32(ABS ? fabsf(r[u].y) : r[u].y, hy, ly);
                 *reinterpret_cast<uint2*>((u < 8 ? ah : bh) + 2048 * (u & 7)) = make_uint2(hx, hy);
                 *reinterpret_cast<uint2*>((u < 8 ? al : bl) + 2048 * (u & 7)) = make_uint2(lx, ly);
             }
@@ -465,13 +467,16 @@ long long gram_stream_kchunk(int m, int n, long long K, int sms, int max_k) {
 }
 
 cudaError_t launch_gram_stream(const float* A, const float* B, int m, int n, long long K, long long kchunk, float* P,
-                               int* err, cudaStream_t st) {
+                               int* err, cudaStream_t st, bool absval) {
     if (K % 2 != 0 || kchunk % TK != 0 || kchunk <= 0 || ((uintptr_t)A % 8) || ((uintptr_t)B % 8))
         return cudaErrorInvalidValue;
-    cudaError_t e = set_smem((const void*)gram_stream, st);
+    cudaError_t e = set_smem(absval ? (const void*)gram_stream<true> : (const void*)gram_stream<false>, st);
     if (e != cudaSuccess) return e;
     dim3 grid((m + 127) / 128, (n + 127) / 128, (unsigned)((K + kchunk - 1) / kchunk));
-    gram_stream<<<grid, NTHR, sizeof(WsSmem) + 1024, st>>>(A, B, m, n, K, kchunk, P, err);
+    if (absval)
+        gram_stream<true><<<grid, NTHR, sizeof(WsSmem) + 1024, st>>>(A, B, m, n, K, kchunk, P, err);
+    else
+        gram_stream<false><<<grid, NTHR, sizeof(WsSmem) + 1024, st>>>(A, B, m, n, K, kchunk, P, err);
     return cudaGetLastError();
 }
 
