@@ -44,6 +44,7 @@ namespace {
 constexpr int TK = 32;               // K values per stage: one 128-byte swizzle row
 constexpr int NB = 3;                // shared operand buffers (split, swizzled)
 constexpr int DS = 2;                // stages per accumulator turn
+constexpr int PF = 2;                // K stages each producer thread keeps in flight in registers (2 or 3)
 constexpr int NPROD = 8;             // producer warps
 constexpr int NTHR = 16 * 32;        // producers, then the drain warps
 constexpr int WARP_DRAIN0 = 8;
@@ -202,8 +203,8 @@ __global__ void __launch_bounds__(NTHR, 1)
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
                 r[u] = make_float2(0.f, 0.f);
-                if (in && ((valid >> u) & 1))
-                    r[u] = __ldg(reinterpret_cast<const float2*>((u < 8 ? pa : pb) + (u & 7) * rs + ko));
+                if (in && ((valid >> u) & 1))  // read once: cached in L2 only
+                    r[u] = __ldcg(reinterpret_cast<const float2*>((u < 8 ? pa : pb) + (u & 7) * rs + ko));
             }
         };
         auto produce = [&](float2 (&r)[16], int s) -> bool {
@@ -222,15 +223,16 @@ __global__ void __launch_bounds__(NTHR, 1)
                 *reinterpret_cast<uint2*>((u < 8 ? ah : bh) + 2048 * (u & 7)) = make_uint2(hx, hy);
                 *reinterpret_cast<uint2*>((u < 8 ? al : bl) + 2048 * (u & 7)) = make_uint2(lx, ly);
             }
-            load(r, s + 2);  // two stages ahead
+            load(r, s + PF);  // PF stages ahead
             ws_produced(&sm.full[b]);
             return true;
         };
-        float2 ra[16], rb[16];
+        float2 ra[16], rb[16], rc[16];
         load(ra, 0);
         load(rb, 1);
-        for (int s = 0; s < nst; s += 2)
-            if (!produce(ra, s) || !produce(rb, s + 1)) break;
+        if (PF == 3) load(rc, 2);
+        for (int s = 0; s < nst; s += PF)
+            if (!produce(ra, s) || !produce(rb, s + 1) || (PF == 3 && !produce(rc, s + 2))) break;
     } else {
         // drain warps; lane 0 of the first also issues the MMAs, one turn
         // ahead of its own drains
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(NTHR, 1)
                 *reinterpret_cast<uint32_t*>(ah + a1) = hy;
                 *reinterpret_cast<uint32_t*>(al + a1) = ly;
             }
-            load(r);  // two stages ahead
+            load(r);  // PF stages ahead
             if (++cks == nks) {
                 cks = 0;
                 ctile += G;
@@ -366,11 +368,12 @@ __global__ void __launch_bounds__(NTHR, 1)
             ws_produced(&sm.full[b]);
             return true;
         };
-        float2 ra[8], rb[8];
+        float2 ra[8], rb[8], rc[8];
         load(ra);
         load(rb);
-        for (long long g = 0; g < S; g += 2)
-            if (!produce(ra, g) || !produce(rb, g + 1)) break;
+        if (PF == 3) load(rc);
+        for (long long g = 0; g < S; g += PF)
+            if (!produce(ra, g) || !produce(rb, g + 1) || (PF == 3 && !produce(rc, g + 2))) break;
     } else {
         // drain warps; lane 0 of the first also issues the MMAs, one turn
         // ahead of its own drains.  Turn q: tile q / nsub, stages DS (q % nsub) ..
