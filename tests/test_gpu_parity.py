@@ -289,6 +289,32 @@ def test_row_blocks_match_oracle(monkeypatch, row_block):
     plan.close()
 
 
+@pytest.mark.parametrize("n,T", [(1, 1), (33, 300), (130, 257), (300, 5)])
+def test_tensor_core_apply_ragged_shapes(n, T):
+    """The streamed tcgen05 Gram and product on ragged shapes: one vector and
+    one trial; a partial K stage of ACE vectors (33) and three trial blocks
+    (300); 130 vectors (two 128-row Gram tiles) and 257 trials; 300 vectors
+    (three Gram tiles, ten product stages) on 5 trials -- against an FP64
+    evaluation of -xi (xi^T psi) on the same float inputs, and the fast
+    energy against -sum C^2."""
+    cfg = gen.config_small()
+    plan = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], 8, "mixed")
+    npw = plan.n_pw_half
+    rng = np.random.default_rng(n * 1000 + T)
+    xi = (rng.standard_normal((n, npw)) + 1j * rng.standard_normal((n, npw))) / np.sqrt(npw)
+    xi[:, 0] = xi[:, 0].real
+    tr = gen.random_trials(cfg["cell"], cfg["ecut"], T, seed=T)
+    d_xi, d_tr = dev(xi, plan), dev(tr, plan)
+    xh, th = host(d_xi), host(d_tr)  # the float inputs, exactly
+    C = gen.gamma_overlap(th, xh)
+    ref = -(C @ xh)
+    K = host(ace.ace_apply(plan, d_xi, d_tr))
+    assert rel(K, ref) <= 1e-6
+    E = ace.ace_apply_energy(plan, d_xi, d_tr)
+    assert abs(E + np.sum(C * C)) <= 1e-6 * np.sum(C * C)
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_blocked_cholesky_70_orbitals(prec):
     """70 orbitals take the multi-block Cholesky and inverse (blocks of 32,
