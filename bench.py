@@ -259,8 +259,8 @@ def pass_bytes(n, N, esz=4, batch=64):
 # profiles/dram_pair_passes_water32_96cubed.md): the tile-pass forward kernel,
 # the plane-kernel forward pass of the hybrid variant, and the Coulomb and
 # accumulation kernels both variants share.
-MEASURED_TRAFFIC_PER_LAUNCH = {"pair_fwd": 0.8625e9, "pair_fwd_hybrid": 0.8690e9, "pair_coulomb": 0.8472e9,
-                               "pair_inv": 1.7969e9}
+MEASURED_TRAFFIC_PER_LAUNCH = {"pair_fwd": None, "pair_fwd_hybrid": 0.5464e9, "pair_coulomb": 0.8472e9,
+                               "pair_inv": 0.8511e9}
 
 
 def cpu_baseline(cfg, rows=5):
@@ -438,8 +438,12 @@ def run_ours(args):
     achieved = alg_bytes / (pair_wall / 1e3) / 1e9 if pair_wall > 0 else 0.0
     achieved_launch = pipe_bytes / (pair_wall / 1e3) / 1e9 if pair_wall > 0 else 0.0
     fwd_key = "pair_fwd_hybrid" if variant == 4 else "pair_fwd"
-    traffic_step = (MEASURED_TRAFFIC_PER_LAUNCH[fwd_key] + MEASURED_TRAFFIC_PER_LAUNCH["pair_coulomb"] +
-                    MEASURED_TRAFFIC_PER_LAUNCH["pair_inv"]) * (stats["pair_transforms"] / args.steps) / 64
+    # the ncu DRAM capture covers the hybrid variant's passes (column-shared
+    # packing, row blocks of 4); other variants report no traffic
+    traffic_step = None
+    if variant == 4:
+        traffic_step = (MEASURED_TRAFFIC_PER_LAUNCH[fwd_key] + MEASURED_TRAFFIC_PER_LAUNCH["pair_coulomb"] +
+                        MEASURED_TRAFFIC_PER_LAUNCH["pair_inv"]) * (stats["pair_transforms"] / args.steps) / 64
     # each pass alone (one stream, 64-transform launches), timed the same way:
     # the chosen variant's passes, or the tile passes when the choice is the
     # persistent kernel (which has no separate passes)
@@ -461,13 +465,13 @@ def run_ours(args):
                            "achieved_gbs": pb64[k] / (ms / 1e3) / 1e9 if ms > 0 else 0.0,
                            "frac": (pb64[k] / (ms / 1e3) / 1e9) / hbm if ms > 0 else 0.0,
                            "traffic_per_launch": MEASURED_TRAFFIC_PER_LAUNCH[fwd_key if k == "pair_fwd" else k]
-                           if variant in (1, 3, 4) else None}
+                           if variant == 4 else None}
     layout = ("one launch for all transforms" if variant == 3 else
               "32-transform sub-batches on 2 streams" if streams == 2 else "64-transform launches on one stream")
     roofline = {"bound": "hbm",
                 "kernel": f"pair pipeline: P1 + P2 + P3 ({vname}), {layout}",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind,
-                "traffic": traffic_step if world == 1 and variant in (1, 4) else None,
+                "traffic": traffic_step if world == 1 else None,
                 "traffic_unit": "bytes per build (sum of the three passes' DRAM bytes from the ncu "
                 "captures, scaled from 64-transform launches)",
                 "algorithmic_bytes_per_build": alg_bytes,

@@ -164,7 +164,7 @@ cudaError_t launch_gather(const cx<R>* box, const Quad* quads, int t0, int batch
 template <typename R>
 cudaError_t launch_gram_partial(const R* A, const R* B, int m, int n, long long K, int nchunk, double* P,
                                 cudaStream_t st);
-// The same partials on tcgen05 tensor cores, streamed (umma_apply.cu): split
+// The same partials on tcgen05 tensor cores, streamed (umma_stream.cu): split
 // TF32, FP32 accumulation in TMEM, P [ceil(K / kchunk)][m][n] float; kchunk a
 // multiple of 32 from gram_stream_kchunk (about one block per SM, at most
 // max_k reals per slice when max_k > 0); err: device error flag for bounded waits.
