@@ -133,6 +133,20 @@ int ace_plan_config(const ace_plan* plan, int* pair_variant, int* pair_streams, 
  * output may be NULL. */
 int ace_plan_tuning(const ace_plan* plan, int* row_block, float* row_block_ms, int* from_cache);
 
+/* The radix plan of the pair passes' 3D FFTs (the Poisson solves of Eq. 3):
+ * every axis of the box in two stages, radix *radix0 and then n / *radix0.
+ * On single-precision n^3 plans with n = 96, 120 or 160, plan creation times
+ * each candidate plan (96: 12 x 8, 8 x 12, 16 x 6; 120: 12 x 10, 10 x 12,
+ * 8 x 15; 160: 16 x 10, 10 x 16) with every pair_variant and keeps the
+ * fastest: candidates[k] are their first radices, candidate_ms[k] the best
+ * pair-pass time of each (k < *n_candidates <= 4; later entries 0).  Other
+ * plans have one candidate, make_axis_plan's.  The pair passes' spectrum
+ * never leaves them, so the orbital and W transforms keep the first
+ * candidate's plan.  ACE_PAIR_RADIX=<first radix> in the environment fixes the
+ * plan (a radix that is no candidate of the grid: ACE_ERR_INVALID_ARG at plan
+ * creation); ACE_TUNE_CACHE lines carry the choice.  Any output may be NULL. */
+int ace_plan_radix(const ace_plan* plan, int* radix0, int* n_candidates, int* candidates, float* candidate_ms);
+
 /* Number of half-sphere plane waves and, when miller != NULL, their Miller
  * indices [n_pw_half][3] (host memory, canonical order). */
 int ace_gvec(const ace_plan* plan, int* n_pw_half, int32_t* miller);

@@ -25,7 +25,7 @@ SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_
            "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc",
            "ace_build_batched", "ace_save", "ace_load", "ace_build_pairs", "ace_build_finish",
            "ace_plan_config", "ace_overlap_screen", "ace_build_async", "ace_build_result",
-           "ace_check_timeout_path", "ace_scdm", "ace_apply_energy", "ace_plan_tuning")
+           "ace_check_timeout_path", "ace_scdm", "ace_apply_energy", "ace_plan_tuning", "ace_plan_radix")
 
 _lib = None
 
@@ -88,6 +88,8 @@ def load(build_if_missing=False):
     lib.ace_overlap_screen.argtypes = [P, P, i32, f64, P, P, ctypes.POINTER(i32), P, P]
     lib.ace_plan_config.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
     lib.ace_plan_tuning.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)]
+    lib.ace_plan_radix.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                   ctypes.POINTER(ctypes.c_float)]
     lib.ace_scdm.argtypes = [P, P, i32, i32, P, P, ctypes.POINTER(i32), P, P]
     lib.ace_apply_noalloc.argtypes = [P, i32, P, i32, i32, i32, P, P]
     lib.hfx_apply_exact.argtypes = [P, P, i32, f64, P, i32, P, P]
@@ -176,14 +178,21 @@ class Plan:
     def config(self):
         """dict(pair_variant, pair_streams, row_block, tune_ms, ...) of the pair-pass
         kernels (1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid)
-        and the pair-tile shape (ace_plan_tuning)."""
+        the pair-tile shape (ace_plan_tuning) and the pair passes' FFT radix plan
+        (ace_plan_radix: first radix of every axis, and the candidates timed)."""
         v, st = ctypes.c_int(0), ctypes.c_int(0)
         tm = (ctypes.c_float * 5)()
         _check(load().ace_plan_config(self.handle, ctypes.byref(v), ctypes.byref(st), tm))
         rb, cached = ctypes.c_int(0), ctypes.c_int(0)
         rbm = (ctypes.c_float * 4)()
         _check(load().ace_plan_tuning(self.handle, ctypes.byref(rb), rbm, ctypes.byref(cached)))
+        r0, nc = ctypes.c_int(0), ctypes.c_int(0)
+        rc, rms = (ctypes.c_int * 4)(), (ctypes.c_float * 4)()
+        _check(load().ace_plan_radix(self.handle, ctypes.byref(r0), ctypes.byref(nc), rc, rms))
         return {"pair_variant": v.value, "pair_streams": st.value, "row_block": rb.value,
+                "radix_plan": f"{r0.value} x {self.grid[0] // r0.value}" if r0.value > 0 else None,
+                "radix_ms": {f"{rc[k]} x {self.grid[0] // rc[k]}": round(float(rms[k]), 3)
+                             for k in range(nc.value) if rms[k] > 0},
                 "from_tune_cache": bool(cached.value),
                 "tune_ms": {k: round(float(x), 3) for k, x in
                             zip(("tile_1_stream", "tile_2_streams", "planes", "pipeline", "hybrid"), tm)

@@ -10,8 +10,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libace_gb300.so")
-SOURCES = ["passes.cu", "cube_a.cu", "cube_b.cu", "cube_c.cu", "cube_dispatch.cu", "la.cu", "ace_abi.cu",
-           "noalloc.cu", "umma_stream.cu", "scdm.cu"]
+SOURCES = ["passes.cu", "cube_a.cu", "cube_b.cu", "cube_c.cu", "cube_r96.cu", "cube_r120.cu", "cube_r160.cu",
+           "cube_dispatch.cu", "la.cu", "ace_abi.cu", "noalloc.cu", "umma_stream.cu", "scdm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                      "-I", CSRC]

@@ -133,6 +133,10 @@ struct ace_plan {
     float tune_ms[5] = {0, 0, 0, 0, 0};  // autotune: tile x1 stream, tile x2, planes x2, pipeline, hybrid x2
     float tune_rb_ms[4] = {0, 0, 0, 0};  // autotune of the chosen variant's row block: row order, 2, 4, 8 rows
     int tune_cached = 0;                 // 1: the choice came from the tune cache (ACE_TUNE_CACHE)
+    int pair_r0 = 0;                     // first radix of the pair passes' plan on every axis (0: make_axis_plan's)
+    int r0_cand[4] = {0, 0, 0, 0};       // the first radices the autotuner timed (0: make_axis_plan's)
+    float tune_r0_ms[4] = {0, 0, 0, 0};  // the best pair-pass time of each
+    int n_r0_cand = 1;
     bool tplane = false;       // pair passes with transposed spectrum planes (plane.cuh; needs zline)
     int pair_tile = 0;         // pairs ordered in pair_tile x pair_tile orbital blocks (0: row by row; env ACE_PAIR_TILE)
     int row_block = 4;         // pairs packed column-shared in blocks of this many rows (pack_pairs_blocked;
@@ -467,6 +471,7 @@ int run_pairs(ace_plan* P, const R* fl, const R* fr, R* accl, R* accr, int symme
     a.symmetric = symmetric;
     a.quads = dq;
     a.e_part = e_part;
+    a.r0 = P->pair_r0;  // the spectrum tables were made for this plan
     if (P->fused && ntrans > 0) {
         // one persistent kernel over every transform (pipeline.cuh)
         ACE_TRY(grow(&P->d_pipe, &P->pipe_cap, (size_t)3 * ntrans + 2));
@@ -1101,8 +1106,32 @@ void set_variant(ace_plan* P, int v, int streams) {
 // first transforms of the full pair list of n_occ_max orbitals, one warm-up
 // and two timed runs each) and the fastest kept.
 template <typename R>
+int pair_tables(ace_plan* P, int r0);
+
+// First radix of the pair passes' plan: r0, or make_axis_plan's for r0 = 0.
+int first_radix(const ace_plan* P, int r0) { return r0 ? r0 : (P->ax[0].nstages > 0 ? P->ax[0].radix[0] : 1); }
+
+template <typename R>
 int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     const int req = opts ? opts->pair_variant : 0;
+    // the pair passes' radix plans: make_axis_plan's (r0 = 0), then the
+    // alternatives with compile-time kernels (single-precision cube plans);
+    // ACE_PAIR_RADIX=<first radix> keeps one of them
+    int r0s[4] = {0, 0, 0, 0};
+    int nr0 = 1;
+    if (sizeof(R) == 4 && P->zline && P->cube_kernels) nr0 += pair_radix_alternatives(P->n[0], r0s + 1);
+    if (const char* env = std::getenv("ACE_PAIR_RADIX")) {
+        const int want = std::atoi(env);
+        int hit = -1;
+        for (int k = 0; k < nr0; ++k)
+            if (first_radix(P, r0s[k]) == want) hit = k;
+        if (hit < 0) return fail(ACE_ERR_INVALID_ARG, "ACE_PAIR_RADIX names no pair radix plan of this grid");
+        r0s[0] = r0s[hit];
+        nr0 = 1;
+        ACE_TRY(pair_tables<R>(P, r0s[0]));
+    }
+    P->n_r0_cand = nr0;
+    for (int k = 0; k < 4; ++k) P->r0_cand[k] = k < nr0 ? r0s[k] : 0;
     const int fixed_streams = opts && opts->pair_streams > 0 ? opts->pair_streams : 0;
     const bool t_ok = sizeof(R) == 4 && P->zline && P->d_kern_t != nullptr;
     const bool h_ok = sizeof(R) == 4 && P->zline;  // every compile-time cube
@@ -1147,22 +1176,28 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
                       (int)sizeof(R) * 8, prop.name, P->sms);
         if (FILE* f = std::fopen(cache, "r")) {
             char line[512];
-            int v = 0, st = 0, rb = -1;
+            int v = 0, st = 0, rb = -1, r0 = 0;
             bool hit = false;
             while (std::fgets(line, sizeof line, f)) {
                 const size_t kl = std::strlen(key);
-                int v2, s2, rb2;
-                if (std::strncmp(line, key, kl) == 0 && line[kl] == ' ' &&
-                    std::sscanf(line + kl, " = %d %d %d", &v2, &s2, &rb2) == 3 && v2 >= 1 && v2 <= 4 && s2 >= 1 &&
-                    s2 <= 8 && rb2 >= 0 && rb2 <= 64 && (v2 != 2 && v2 != 3 ? true : t_ok) && (v2 != 4 || h_ok)) {
+                int v2, s2, rb2, r2 = 0;
+                const int got = std::strncmp(line, key, kl) == 0 && line[kl] == ' '
+                                    ? std::sscanf(line + kl, " = %d %d %d %d", &v2, &s2, &rb2, &r2)
+                                    : 0;
+                bool r_ok = false;  // the radix plan (a fourth field; 0 when absent) is one of this plan's
+                for (int k = 0; k < nr0; ++k) r_ok = r_ok || r0s[k] == r2;
+                if ((got == 3 || got == 4) && v2 >= 1 && v2 <= 4 && s2 >= 1 && s2 <= 8 && rb2 >= 0 && rb2 <= 64 &&
+                    (v2 != 2 && v2 != 3 ? true : t_ok) && (v2 != 4 || h_ok) && r_ok) {
                     v = v2;  // the last matching line wins
                     st = s2;
                     rb = rb2;
+                    r0 = r2;
                     hit = true;
                 }
             }
             std::fclose(f);
             if (hit) {
+                if (r0 != P->pair_r0) ACE_TRY(pair_tables<R>(P, r0));
                 set_variant(P, v, st);
                 P->row_block = rb;
                 P->tune_cached = 1;
@@ -1219,7 +1254,8 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     };
     int rc = ACE_OK;
     float best = 1e30f;
-    int best_v = 1, best_s = 2, best_rb = P->row_block;
+    int best_v = 1, best_s = 2, best_rb = P->row_block, best_r0 = P->pair_r0;
+    float var_ms[4][5] = {};  // per radix plan and variant slot
     do {
         if (cudaMemsetAsync(P->d_phi, 0, (size_t)n * P->N * sizeof(R), ts) != cudaSuccess ||
             cudaMemsetAsync(P->d_acc, 0, (size_t)n * P->N * sizeof(R), ts) != cudaSuccess) {
@@ -1227,18 +1263,30 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
             break;
         }
         const std::vector<Quad> q = quads_for(P->row_block);
-        for (const Cand& c : cand) {
-            set_variant(P, c.v, c.streams);
-            float ms = 0;
-            if ((rc = time_runs(q, &ms)) != ACE_OK) break;
-            P->tune_ms[c.slot] = ms;
-            if (ms < best) {
-                best = ms;
-                best_v = c.v;
-                best_s = c.streams;
+        // every radix plan with every variant
+        for (int k = 0; k < nr0 && rc == ACE_OK; ++k) {
+            if (r0s[k] != P->pair_r0 && (rc = pair_tables<R>(P, r0s[k])) != ACE_OK) break;
+            float best_k = 1e30f;
+            for (const Cand& c : cand) {
+                set_variant(P, c.v, c.streams);
+                float ms = 0;
+                if ((rc = time_runs(q, &ms)) != ACE_OK) break;
+                var_ms[k][c.slot] = ms;
+                best_k = std::min(best_k, ms);
+                if (ms < best) {
+                    best = ms;
+                    best_v = c.v;
+                    best_s = c.streams;
+                    best_r0 = r0s[k];
+                }
             }
+            P->tune_r0_ms[k] = best_k;
         }
         if (rc != ACE_OK) break;
+        for (int k = 0; k < nr0; ++k)
+            if (r0s[k] == best_r0)
+                for (int v = 0; v < 5; ++v) P->tune_ms[v] = var_ms[k][v];
+        if (best_r0 != P->pair_r0 && (rc = pair_tables<R>(P, best_r0)) != ACE_OK) break;
         // then the pair-tile shape of the chosen kernels: row order, or column-
         // shared transforms in blocks of 2, 4 or 8 rows (pack_pairs_blocked)
         if (!std::getenv("ACE_ROW_BLOCK")) {
@@ -1264,7 +1312,7 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     P->launches = 0;
     if (rc == ACE_OK && key[0]) {
         if (FILE* f = std::fopen(cache, "a")) {
-            std::fprintf(f, "%s = %d %d %d\n", key, best_v, best_s, best_rb);
+            std::fprintf(f, "%s = %d %d %d %d\n", key, best_v, best_s, best_rb, best_r0);
             std::fclose(f);
         }
     }
@@ -1306,6 +1354,77 @@ double auxiliary_function_k0(const double cell[9], const double b[9], double ome
     return 4 * M_PI * (integral - (lattice - a));
 }
 
+// The pair passes' spectrum tables for the radix plan whose first stage has
+// radix r0 on every axis (0: make_axis_plan's plan, the one the orbital and W
+// transforms use): the frequency at every position (the tile passes' Coulomb
+// stage) and the Coulomb factors K(G) / N (Eq. 3) at every stored position,
+// computed in double: the per-pencil pass always reads one; the Coulomb stage
+// of the tile passes reads one for the cut-off interaction and in double
+// precision (one load is cheaper than a double division there); in single
+// precision it forms 4 pi / |G|^2 from G itself.  Device buffers are made on
+// the first call and rewritten by later ones (the autotuner times each plan).
+template <typename R>
+int pair_tables(ace_plan* P, int r0) {
+    std::vector<int> frq[3];
+    for (int d = 0; d < 3; ++d) {
+        AxisPlan ax = P->ax[d];
+        if (r0 != 0 && !make_axis_plan_first(P->n[d], r0, ax))
+            return fail(ACE_ERR_INVALID_ARG, "pair radix plan: the radix does not split the grid into two codelets");
+        frq[d].resize(P->n[d]);
+        for (int k = 0; k < P->n[d]; ++k) frq[d][digit_reversed_position(ax, k)] = k;
+        if (!P->d_freq[d]) ACE_TRY(dalloc((void**)&P->d_freq[d], P->n[d] * sizeof(int)));
+        ACE_CK(cudaMemcpy(P->d_freq[d], frq[d].data(), P->n[d] * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    P->pair_r0 = r0;
+    const bool swz = P->s_xy.cube && cube_swizzle(P->n[2]);
+    const bool inline_tab = !P->zline && (P->coul_rc > 0 || P->coul_g0 || sizeof(R) == 8);
+    if (!P->zline && !inline_tab) return ACE_OK;
+    const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
+    const bool with_t = P->zline && tplane_supported(n0);
+    const bool swz_i = P->s_z.cube && cube_swizzle(n2);  // x slots of the tile passes' Coulomb stage
+    std::vector<float> kern(P->zline ? (size_t)P->N : 0), kern_t(with_t ? (size_t)P->N : 0);
+    std::vector<R> kern_r(inline_tab ? (size_t)P->N : 0);
+    auto fold = [](int k, int n) { return k < n - n / 2 ? k : k - n; };
+    auto g2_at = [&](int z, int y, int xp) {
+        const int m[3] = {fold(frq[0][z], n0), fold(frq[1][y], n1), fold(frq[2][xp], n2)};
+        double q2 = 0;
+        for (int c = 0; c < 3; ++c) {
+            const double g = m[0] * P->b[c] + m[1] * P->b[3 + c] + m[2] * P->b[6 + c];
+            q2 += g * g;
+        }
+        return q2;
+    };
+    // 4 pi / |G|^2 with G = 0 dropped, or the transform of 1/r cut off at
+    // R_c: 4 pi (1 - cos(|G| R_c)) / |G|^2, and 2 pi R_c^2 at G = 0
+    const double rc = P->coul_rc;
+    auto k = [&](double q2) {
+        if (rc > 0)
+            return (q2 > 0 ? 4 * M_PI * (1 - std::cos(std::sqrt(q2) * rc)) / q2 : 2 * M_PI * rc * rc) / (double)P->N;
+        return q2 > 0 ? 4 * M_PI / (q2 * (double)P->N) : P->coul_k0 / (double)P->N;
+    };
+    for (int z = 0; z < n0; ++z)
+        for (int y = 0; y < n1; ++y)
+            for (int xs = 0; xs < n2; ++xs) {
+                const size_t e = ((size_t)z * n1 + y) * n2 + xs;
+                if (P->zline) kern[e] = (float)k(g2_at(z, y, swz ? plane_swizzle(xs, y) : xs));
+                if (with_t) kern_t[((size_t)z * n2 + xs) * n1 + y] = (float)k(g2_at(z, y, xs));  // plane [x][y]
+                if (inline_tab) kern_r[e] = (R)k(g2_at(z, y, swz_i ? plane_swizzle(xs, y) : xs));
+            }
+    if (with_t) {
+        if (!P->d_kern_t) ACE_TRY(dalloc((void**)&P->d_kern_t, kern_t.size() * sizeof(float)));
+        ACE_CK(cudaMemcpy(P->d_kern_t, kern_t.data(), kern_t.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (P->zline) {
+        if (!P->d_kern) ACE_TRY(dalloc((void**)&P->d_kern, kern.size() * sizeof(float)));
+        ACE_CK(cudaMemcpy(P->d_kern, kern.data(), kern.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (inline_tab) {
+        if (!P->d_kern_r) ACE_TRY(dalloc(&P->d_kern_r, kern_r.size() * sizeof(R)));
+        ACE_CK(cudaMemcpy(P->d_kern_r, kern_r.data(), kern_r.size() * sizeof(R), cudaMemcpyHostToDevice));
+    }
+    return ACE_OK;
+}
+
 template <typename R>
 int create_impl(ace_plan* P, const ace_opts* opts) {
     P->esz = sizeof(R);
@@ -1320,18 +1439,12 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
         ACE_TRY(dalloc(&P->d_tw[d], tw.size() * sizeof(cx<R>)));
         ACE_CK(cudaMemcpy(P->d_tw[d], tw.data(), tw.size() * sizeof(cx<R>), cudaMemcpyHostToDevice));
     }
-    // digit-reversed positions of every frequency, per axis, and their inverse
-    std::vector<int> pos[3], frq[3];
+    // digit-reversed positions of every frequency, per axis (the orbital and
+    // W transforms' plan)
+    std::vector<int> pos[3];
     for (int d = 0; d < 3; ++d) {
         pos[d].resize(P->n[d]);
-        std::vector<int>& fr = frq[d];
-        fr.resize(P->n[d]);
-        for (int k = 0; k < P->n[d]; ++k) {
-            pos[d][k] = digit_reversed_position(P->ax[d], k);
-            fr[pos[d][k]] = k;
-        }
-        ACE_TRY(dalloc((void**)&P->d_freq[d], P->n[d] * sizeof(int)));
-        ACE_CK(cudaMemcpy(P->d_freq[d], fr.data(), P->n[d] * sizeof(int), cudaMemcpyHostToDevice));
+        for (int k = 0; k < P->n[d]; ++k) pos[d][k] = digit_reversed_position(P->ax[d], k);
     }
     if (opts && opts->kernels >= 2) P->cube_kernels = false;  // generic runtime-size FFT passes
     P->tensor_gram = !(opts && opts->kernels >= 1) && sizeof(R) == 4;
@@ -1349,11 +1462,6 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     ACE_TRY(setup_shapes<R>(P));
     // the compile-time plane kernels of N % 16 == 0 boxes keep x swizzled per row
     const bool swz = P->s_xy.cube && cube_swizzle(P->n[2]);
-    // Coulomb tables K(G) / N (Eq. 3) at every stored position of the spectrum,
-    // computed in double: the per-pencil pass always reads one; the Coulomb
-    // stage of the tile passes reads one for the cut-off interaction and in
-    // double precision (one load is cheaper than a double division there); in
-    // single precision it forms 4 pi / |G|^2 from G itself.
     if (opts) {
         P->coul_rc = opts->coulomb_rc;
         P->coul_g0 = opts->coulomb_g0;
@@ -1361,52 +1469,7 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
     }
     P->zline = P->s_xy.cube && P->s_z.cube && zline_group(P->n[0]) > 0;
     if (const char* env = std::getenv("ACE_ZLINE")) P->zline = P->zline && std::atoi(env) != 0;
-    const bool inline_tab = !P->zline && (P->coul_rc > 0 || P->coul_g0 || sizeof(R) == 8);
-    if (P->zline || inline_tab) {
-        const int n0 = P->n[0], n1 = P->n[1], n2 = P->n[2];
-        const bool with_t = P->zline && tplane_supported(n0);
-        const bool swz_i = P->s_z.cube && cube_swizzle(n2);  // x slots of the tile passes' Coulomb stage
-        std::vector<float> kern(P->zline ? (size_t)P->N : 0), kern_t(with_t ? (size_t)P->N : 0);
-        std::vector<R> kern_r(inline_tab ? (size_t)P->N : 0);
-        auto fold = [](int k, int n) { return k < n - n / 2 ? k : k - n; };
-        auto g2_at = [&](int z, int y, int xp) {
-            const int m[3] = {fold(frq[0][z], n0), fold(frq[1][y], n1), fold(frq[2][xp], n2)};
-            double q2 = 0;
-            for (int c = 0; c < 3; ++c) {
-                const double g = m[0] * P->b[c] + m[1] * P->b[3 + c] + m[2] * P->b[6 + c];
-                q2 += g * g;
-            }
-            return q2;
-        };
-        // 4 pi / |G|^2 with G = 0 dropped, or the transform of 1/r cut off at
-        // R_c: 4 pi (1 - cos(|G| R_c)) / |G|^2, and 2 pi R_c^2 at G = 0
-        const double rc = P->coul_rc;
-        auto k = [&](double q2) {
-            if (rc > 0) return (q2 > 0 ? 4 * M_PI * (1 - std::cos(std::sqrt(q2) * rc)) / q2 : 2 * M_PI * rc * rc) /
-                               (double)P->N;
-            return q2 > 0 ? 4 * M_PI / (q2 * (double)P->N) : P->coul_k0 / (double)P->N;
-        };
-        for (int z = 0; z < n0; ++z)
-            for (int y = 0; y < n1; ++y)
-                for (int xs = 0; xs < n2; ++xs) {
-                    const size_t e = ((size_t)z * n1 + y) * n2 + xs;
-                    if (P->zline) kern[e] = (float)k(g2_at(z, y, swz ? plane_swizzle(xs, y) : xs));
-                    if (with_t) kern_t[((size_t)z * n2 + xs) * n1 + y] = (float)k(g2_at(z, y, xs));  // plane [x][y]
-                    if (inline_tab) kern_r[e] = (R)k(g2_at(z, y, swz_i ? plane_swizzle(xs, y) : xs));
-                }
-        if (with_t) {
-            ACE_TRY(dalloc((void**)&P->d_kern_t, kern_t.size() * sizeof(float)));
-            ACE_CK(cudaMemcpy(P->d_kern_t, kern_t.data(), kern_t.size() * sizeof(float), cudaMemcpyHostToDevice));
-        }
-        if (P->zline) {
-            ACE_TRY(dalloc((void**)&P->d_kern, kern.size() * sizeof(float)));
-            ACE_CK(cudaMemcpy(P->d_kern, kern.data(), kern.size() * sizeof(float), cudaMemcpyHostToDevice));
-        }
-        if (inline_tab) {
-            ACE_TRY(dalloc(&P->d_kern_r, kern_r.size() * sizeof(R)));
-            ACE_CK(cudaMemcpy(P->d_kern_r, kern_r.data(), kern_r.size() * sizeof(R), cudaMemcpyHostToDevice));
-        }
-    }
+    ACE_TRY(pair_tables<R>(P, 0));
     std::vector<int> ip(P->npw), in(P->npw);
     for (int p = 0; p < P->npw; ++p) {
         int m[3], mn[3];
@@ -1822,6 +1885,17 @@ int ace_plan_tuning(const ace_plan* plan, int* row_block, float* row_block_ms, i
     if (row_block_ms)
         for (int i = 0; i < 4; ++i) row_block_ms[i] = plan->tune_rb_ms[i];
     if (from_cache) *from_cache = plan->tune_cached;
+    return ACE_OK;
+}
+
+int ace_plan_radix(const ace_plan* plan, int* radix0, int* n_candidates, int* candidates, float* candidate_ms) {
+    if (!plan) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (radix0) *radix0 = first_radix(plan, plan->pair_r0);
+    if (n_candidates) *n_candidates = plan->n_r0_cand;
+    for (int k = 0; k < 4; ++k) {
+        if (candidates) candidates[k] = k < plan->n_r0_cand ? first_radix(plan, plan->r0_cand[k]) : 0;
+        if (candidate_ms) candidate_ms[k] = k < plan->n_r0_cand ? plan->tune_r0_ms[k] : 0.0f;
+    }
     return ACE_OK;
 }
 

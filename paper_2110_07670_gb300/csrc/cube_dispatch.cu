@@ -22,6 +22,29 @@ ACE_CUBE_DECL(160)
 #undef ACE_CUBE_DECL
 }  // namespace pass_detail
 
+// the pair passes' alternative radix plans (pair_radix_alternatives), in cube_r*.cu
+#define ACE_ALT_PLANS(X) X(96, 8) X(96, 16) X(120, 10) X(120, 8) X(160, 10)
+#define ACE_ALT_PIPE_PLANS(X) X(96, 8) X(96, 16) X(160, 10)
+namespace pass_detail {
+#define ACE_ALT_CUBE_DECL(N, F)                                                                                  \
+    extern template cudaError_t dispatch_cube<N, F>(const PassArgs&, const PassShape&, int, int, int, int, int, \
+                                                    cudaStream_t);
+ACE_ALT_PLANS(ACE_ALT_CUBE_DECL)
+#undef ACE_ALT_CUBE_DECL
+}  // namespace pass_detail
+#define ACE_ALT_DECL(N, F)                                                              \
+    extern template cudaError_t zline_launch<N, F>(const PassArgs&, int, cudaStream_t); \
+    extern template cudaError_t tplane_launch<N, F>(int, const PassArgs&, int, cudaStream_t);
+ACE_ALT_PLANS(ACE_ALT_DECL)
+#undef ACE_ALT_DECL
+#define ACE_ALT_PIPE_DECL(N, F) \
+    extern template cudaError_t pipeline_launch<N, F>(const PassArgs&, const PipeArgs&, cudaStream_t);
+ACE_ALT_PIPE_PLANS(ACE_ALT_PIPE_DECL)
+#undef ACE_ALT_PIPE_DECL
+
+// (n, first radix) as one switch key
+constexpr int alt_key(int n, int r0) { return n * 32 + r0; }
+
 #define ACE_ZLINE_DECL(N) extern template cudaError_t zline_launch<N>(const PassArgs&, int, cudaStream_t);
 ACE_ZLINE_DECL(32)
 ACE_ZLINE_DECL(60)
@@ -35,6 +58,15 @@ ACE_ZLINE_DECL(160)
 #undef ACE_ZLINE_DECL
 
 cudaError_t zline_coulomb_launch(int n, const PassArgs& a, int batch, cudaStream_t st) {
+    if (a.r0 != 0) {
+        switch (alt_key(n, a.r0)) {
+#define ACE_ALT_CASE(N, F) \
+    case alt_key(N, F): return zline_launch<N, F>(a, batch, st);
+            ACE_ALT_PLANS(ACE_ALT_CASE)
+#undef ACE_ALT_CASE
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (n) {
         case 32: return zline_launch<32>(a, batch, st);
         case 60: return zline_launch<60>(a, batch, st);
@@ -62,6 +94,15 @@ ACE_TPLANE_DECL(160)
 #undef ACE_TPLANE_DECL
 
 cudaError_t tplane_pair_launch(int n, int which, const PassArgs& a, int batch, cudaStream_t st) {
+    if (a.r0 != 0) {
+        switch (alt_key(n, a.r0)) {
+#define ACE_ALT_CASE(N, F) \
+    case alt_key(N, F): return tplane_launch<N, F>(which, a, batch, st);
+            ACE_ALT_PLANS(ACE_ALT_CASE)
+#undef ACE_ALT_CASE
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (n) {
         case 32: return tplane_launch<32>(which, a, batch, st);
         case 60: return tplane_launch<60>(which, a, batch, st);
@@ -84,6 +125,15 @@ ACE_PIPE_DECL(160)
 #undef ACE_PIPE_DECL
 
 cudaError_t pipeline_pair_launch(int n, const PassArgs& a, const PipeArgs& p, cudaStream_t st) {
+    if (a.r0 != 0) {
+        switch (alt_key(n, a.r0)) {
+#define ACE_ALT_CASE(N, F) \
+    case alt_key(N, F): return pipeline_launch<N, F>(a, p, st);
+            ACE_ALT_PIPE_PLANS(ACE_ALT_CASE)
+#undef ACE_ALT_CASE
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (n) {
         case 32: return pipeline_launch<32>(a, p, st);
         case 80: return pipeline_launch<80>(a, p, st);
@@ -96,6 +146,15 @@ cudaError_t pipeline_pair_launch(int n, const PassArgs& a, const PipeArgs& p, cu
 cudaError_t cube_pass_launch(int n, const PassArgs& a, const PassShape& s, int pro, int epi, int mid, int sgn,
                              int batch, cudaStream_t st) {
     using namespace pass_detail;
+    if (a.r0 != 0) {
+        switch (alt_key(n, a.r0)) {
+#define ACE_ALT_CASE(N, F) \
+    case alt_key(N, F): return dispatch_cube<N, F>(a, s, pro, epi, mid, sgn, batch, st);
+            ACE_ALT_PLANS(ACE_ALT_CASE)
+#undef ACE_ALT_CASE
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (n) {
         case 32: return dispatch_cube<32>(a, s, pro, epi, mid, sgn, batch, st);
         case 60: return dispatch_cube<60>(a, s, pro, epi, mid, sgn, batch, st);

@@ -405,14 +405,30 @@ constexpr bool make_axis_plan(int n, AxisPlan& P) {
     return true;
 }
 
-// Compile-time plan of an axis of length N.
-template <int N>
+// Two stages with the given first radix: r0, then n / r0 (both codelets).
+// The candidates the plan autotuner times for one axis length.
+constexpr bool make_axis_plan_first(int n, int r0, AxisPlan& P) {
+    P.n = n;
+    P.nstages = 0;
+    if (r0 < 2 || n % r0 != 0 || !is_codelet(r0) || !is_codelet(n / r0)) return false;
+    P.radix[P.nstages++] = r0;
+    P.radix[P.nstages++] = n / r0;
+    return true;
+}
+
+// Compile-time plan of an axis of length N: make_axis_plan's choice (R0 = 0)
+// or the two stages R0, N / R0.
+template <int N, int R0 = 0>
 struct CPlan {
     static constexpr AxisPlan P = [] {
         AxisPlan p{};
-        make_axis_plan(N, p);
+        if (R0 == 0)
+            make_axis_plan(N, p);
+        else
+            make_axis_plan_first(N, R0, p);
         return p;
     }();
+    static_assert(R0 == 0 || P.nstages == 2, "R0 and N / R0 must both be codelet radices");
     static constexpr int stages = P.nstages;
     static constexpr int radix(int s) { return P.radix[s]; }
     static constexpr int block_len(int s) {
@@ -445,9 +461,9 @@ __device__ __forceinline__ void static_stage(cx<R>* buf, const cx<R>* tw) {
     __syncthreads();
 }
 
-template <int SGN, int N, int NLINES, int ESTRIDE, int LSTRIDE, int NT, typename R>
+template <int SGN, int N, int NLINES, int ESTRIDE, int LSTRIDE, int NT, typename R, int R0 = 0>
 __device__ __forceinline__ void static_fft(cx<R>* buf, const cx<R>* tw) {
-    using PL = CPlan<N>;
+    using PL = CPlan<N, R0>;
     CLoop<0, PL::stages>::run([&](auto sc) {
         constexpr int s = SGN < 0 ? decltype(sc)::value : PL::stages - 1 - decltype(sc)::value;
         static_stage<PL::radix(s), SGN, N, PL::block_len(s), NLINES, ESTRIDE, LSTRIDE, NT, R>(buf, tw);

@@ -64,6 +64,8 @@ struct PassArgs {
     const void* kern;    // per-pencil Coulomb pass: 4 pi / |G|^2 / N in spectrum layout, [n0][n1][n2] float
     int kern_inline;     // 1: the tile passes' Coulomb stage reads K(G) / N from kern ([n0][n1][n2], type R,
                          // by x slot) instead of forming 4 pi / |G|^2 (cut-off interaction; double precision)
+    int r0;              // compile-time cube kernels: first radix of every axis (0: make_axis_plan's plan);
+                         // nonzero only for the pair passes, with freq and kern made for that plan
 };
 
 struct PassShape {
@@ -109,6 +111,17 @@ constexpr int zline_group(int n) {
     return 0;
 }
 cudaError_t zline_coulomb_launch(int n, const PassArgs& a, int batch, cudaStream_t st);
+// First radices, besides make_axis_plan's, of the two-stage plans the pair
+// passes have compile-time kernels for on an n^3 box (the autotuner times
+// them): written to r0[], count returned (at most 3).
+inline int pair_radix_alternatives(int n, int* r0) {
+    switch (n) {
+        case 96: r0[0] = 8; r0[1] = 16; return 2;    // 8 x 12, 16 x 6 (default 12 x 8)
+        case 120: r0[0] = 10; r0[1] = 8; return 2;   // 10 x 12, 8 x 15 (default 12 x 10)
+        case 160: r0[0] = 10; return 1;              // 10 x 16 (default 16 x 10)
+        default: return 0;
+    }
+}
 // plane passes with transposed spectrum planes (plane.cuh), N^3 boxes with
 // N % 16 == 0: which = 0 pair product + forward, 1 inverse + exchange accumulation
 constexpr bool tplane_supported(int n) { return n % 16 == 0; }

@@ -192,18 +192,18 @@ __device__ __forceinline__ void static_stage_cols_swizzled(cx<R>* buf, const cx<
     __syncthreads();
 }
 
-template <int SGN, int N, int NT, typename R>
+template <int SGN, int N, int NT, typename R, int R0 = 0>
 __device__ __forceinline__ void static_fft_cols_swizzled(cx<R>* buf, const cx<R>* tw) {
-    using PL = CPlan<N>;
+    using PL = CPlan<N, R0>;
     CLoop<0, PL::stages>::run([&](auto sc) {
         constexpr int s = SGN < 0 ? decltype(sc)::value : PL::stages - 1 - decltype(sc)::value;
         static_stage_cols_swizzled<PL::radix(s), SGN, N, PL::block_len(s), NT, R>(buf, tw);
     });
 }
 
-template <int SGN, int N, int NT, typename R>
+template <int SGN, int N, int NT, typename R, int R0 = 0>
 __device__ __forceinline__ void static_fft_rows_swizzled(cx<R>* buf, const cx<R>* tw) {
-    using PL = CPlan<N>;
+    using PL = CPlan<N, R0>;
     CLoop<0, PL::stages>::run([&](auto sc) {
         constexpr int s = SGN < 0 ? decltype(sc)::value : PL::stages - 1 - decltype(sc)::value;
         static_stage_rows_swizzled<PL::radix(s), SGN, N, PL::block_len(s), NT, R>(buf, tw);
@@ -212,7 +212,8 @@ __device__ __forceinline__ void static_fft_rows_swizzled(cx<R>* buf, const cx<R>
 
 // ... and compile-time geometry of an N^3 box with NT threads per block: every
 // index division becomes a multiply-shift and every stage loop a fixed count.
-template <int N, int TZ, int TY, int TX, int NT>
+// R0: the first radix of every axis (0: make_axis_plan's choice).
+template <int N, int TZ, int TY, int TX, int NT, int R0 = 0>
 struct CubeShape {
     static constexpr bool kCube = true;
     static constexpr int kMaxThreads = NT;
@@ -242,20 +243,20 @@ struct CubeShape {
     template <int SGN, typename R>
     __device__ void fft_x(cx<R>* t, const cx<R>* tw, const PassArgs&) const {
         if constexpr (kSwzTile)
-            static_fft_rows_swizzled<SGN, N, NT, R>(t, tw);
+            static_fft_rows_swizzled<SGN, N, NT, R, R0>(t, tw);
         else
-            static_fft<SGN, N, TZ * TY, 1, TX, NT, R>(t, tw);
+            static_fft<SGN, N, TZ * TY, 1, TX, NT, R, R0>(t, tw);
     }
     template <int SGN, typename R>
     __device__ void fft_y(cx<R>* t, const cx<R>* tw, const PassArgs&) const {
         if constexpr (kSwzTile)
-            static_fft_cols_swizzled<SGN, N, NT, R>(t, tw);
+            static_fft_cols_swizzled<SGN, N, NT, R, R0>(t, tw);
         else
-            static_fft<SGN, N, TX, TX, 1, NT, R>(t, tw);
+            static_fft<SGN, N, TX, TX, 1, NT, R, R0>(t, tw);
     }
     template <int SGN, typename R>
     __device__ void fft_z(cx<R>* t, const cx<R>* tw, const PassArgs&) const {
-        static_fft<SGN, N, TY * TX, TY * TX, 1, NT, R>(t, tw);
+        static_fft<SGN, N, TY * TX, TY * TX, 1, NT, R, R0>(t, tw);
     }
 };
 
@@ -716,26 +717,32 @@ cudaError_t dispatch(const PassArgs& a, const PassShape& s, int pro, int epi, in
 }
 
 // Cube kernels: the plane geometry carries the pair/accumulate/split/pack
-// passes, the pencil geometry the load/store and Coulomb passes.
-template <int N>
+// passes, the pencil geometry the load/store and Coulomb passes.  R0 != 0
+// (a tuned radix plan) exists for the pair passes only: their spectrum never
+// leaves them, while the orbital and W transforms keep the default plan.
+template <int N, int R0 = 0>
 cudaError_t dispatch_cube(const PassArgs& a, const PassShape& s, int pro, int epi, int mid, int sgn, int batch,
                           cudaStream_t st) {
-    using XY = CubeShape<N, 1, N, N, cube_xy_threads(N)>;
-    using Z = CubeShape<N, N, cube_z_ty(N), cube_z_tx(N), cube_z_threads(N)>;
+    using XY = CubeShape<N, 1, N, N, cube_xy_threads(N), R0>;
+    using Z = CubeShape<N, N, cube_z_ty(N), cube_z_tx(N), cube_z_threads(N), R0>;
     if (s.tz == 1 && s.ty == N && s.tx == N && s.threads == cube_xy_threads(N)) {
         if (pro == PRO_PAIR && epi == EPI_STORE && sgn < 0)
             return launch_one<XY, float, PRO_PAIR, EPI_STORE, MID_NONE, -1>(a, s, batch, st);
         if (pro == PRO_LOAD && epi == EPI_ACCUM && sgn > 0)
             return launch_one<XY, float, PRO_LOAD, EPI_ACCUM, MID_NONE, +1>(a, s, batch, st);
-        if (pro == PRO_LOAD && epi == EPI_SPLIT && sgn > 0)
-            return launch_one<XY, float, PRO_LOAD, EPI_SPLIT, MID_NONE, +1>(a, s, batch, st);
-        if (pro == PRO_PACK2 && epi == EPI_STORE && sgn < 0)
-            return launch_one<XY, float, PRO_PACK2, EPI_STORE, MID_NONE, -1>(a, s, batch, st);
+        if constexpr (R0 == 0) {
+            if (pro == PRO_LOAD && epi == EPI_SPLIT && sgn > 0)
+                return launch_one<XY, float, PRO_LOAD, EPI_SPLIT, MID_NONE, +1>(a, s, batch, st);
+            if (pro == PRO_PACK2 && epi == EPI_STORE && sgn < 0)
+                return launch_one<XY, float, PRO_PACK2, EPI_STORE, MID_NONE, -1>(a, s, batch, st);
+        }
     } else if (s.tz == N && s.ty == cube_z_ty(N) && s.tx == cube_z_tx(N) && s.threads == cube_z_threads(N)) {
         if (mid == MID_COULOMB) return launch_one<Z, float, PRO_LOAD, EPI_STORE, MID_COULOMB, -1>(a, s, batch, st);
-        if (pro == PRO_LOAD && epi == EPI_STORE)
-            return sgn < 0 ? launch_one<Z, float, PRO_LOAD, EPI_STORE, MID_NONE, -1>(a, s, batch, st)
-                           : launch_one<Z, float, PRO_LOAD, EPI_STORE, MID_NONE, +1>(a, s, batch, st);
+        if constexpr (R0 == 0) {
+            if (pro == PRO_LOAD && epi == EPI_STORE)
+                return sgn < 0 ? launch_one<Z, float, PRO_LOAD, EPI_STORE, MID_NONE, -1>(a, s, batch, st)
+                               : launch_one<Z, float, PRO_LOAD, EPI_STORE, MID_NONE, +1>(a, s, batch, st);
+        }
     }
     return cudaErrorInvalidValue;
 }

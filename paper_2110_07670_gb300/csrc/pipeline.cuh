@@ -89,10 +89,10 @@ __device__ __forceinline__ const int* dependency(const Item& it, const PipeArgs&
     return p.done + (it.pass - 1) * p.ntrans + it.t;
 }
 
-template <int N>
-__global__ void __launch_bounds__(plane_detail::Geo<N>::NT, plane_detail::Geo<N>::kMinBlocks)
+template <int N, int F0>
+__global__ void __launch_bounds__(plane_detail::Geo<N, F0>::NT, plane_detail::Geo<N, F0>::kMinBlocks)
     pair_pipeline(PassArgs a, PipeArgs p) {
-    using G = plane_detail::Geo<N>;
+    using G = plane_detail::Geo<N, F0>;
     constexpr int W = G::NT / 32;  // warps
     constexpr int GP = 16;         // pencils per warp in pass 1
     static_assert(W * GP == N, "a pass-1 item covers N pencils: N / 16 warps of 16");
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(plane_detail::Geo<N>::NT, plane_detail::Geo<N>
                 if (threadIdx.x == 32 && it.t + 1 < p.ntrans && (NN * 4) % 16 == 0)
                     plane_detail::prefetch_planes(a, a.quads[a.t0 + it.t + 1], it.idx * NN, (uint32_t)(NN * 4), N3,
                                                   false);
-                plane_detail::pair_fwd_plane<N>(a, q, it.idx, tile, tw, spec_t);
+                plane_detail::pair_fwd_plane<N, false, F0>(a, q, it.idx, tile, tw, spec_t);
             } else if (it.pass == 1) {
                 cx<float>* buf = tile + warp * N * GP;
                 const long long p0 = (long long)(it.idx * W + warp) * GP;
@@ -159,10 +159,10 @@ __global__ void __launch_bounds__(plane_detail::Geo<N>::NT, plane_detail::Geo<N>
                     *reinterpret_cast<float4*>(buf + r * GP + (lane & 7) * 2) = v;
                 }
                 __syncwarp();
-                zline_detail::pencils_compute<N, GP>(buf, tw, kern + p0, spec_t + p0, lane);
+                zline_detail::pencils_compute<N, GP, F0>(buf, tw, kern + p0, spec_t + p0, lane);
             } else {
                 const cx<float>* plane = spec_t + it.idx * NN;
-                plane_detail::inv_load_cg<N>(plane, tile);
+                plane_detail::inv_load_cg<N, F0>(plane, tile);
                 if (p.discard) {
                     __syncthreads();
                     // the plane is dead once in shared memory: drop it from L2
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(plane_detail::Geo<N>::NT, plane_detail::Geo<N>
                     for (int l = threadIdx.x; l < (int)(NN * 8 / 128); l += G::NT)
                         discard_l2(reinterpret_cast<const char*>(plane) + (long long)l * 128);
                 }
-                plane_detail::inv_accum_plane<N>(
+                plane_detail::inv_accum_plane<N, F0>(
                     a, q, it.idx, tile, tw, red,
                     a.e_part != nullptr ? a.e_part + ((long long)(a.t0 + it.t) * N + it.idx) * 2 : nullptr);
             }
@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(plane_detail::Geo<N>::NT, plane_detail::Geo<N>
 
 }  // namespace pipe_detail
 
-template <int N>
+template <int N, int F0 = 0>
 cudaError_t pipeline_launch(const PassArgs& a, const PipeArgs& p, cudaStream_t st) {
-    using G = plane_detail::Geo<N>;
-    auto k = pipe_detail::pair_pipeline<N>;
+    using G = plane_detail::Geo<N, F0>;
+    auto k = pipe_detail::pair_pipeline<N, F0>;
     static int per_sm = [&] {
         int b = 0;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem) != cudaSuccess ||

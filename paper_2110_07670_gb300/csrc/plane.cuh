@@ -31,9 +31,10 @@
 namespace ace {
 namespace plane_detail {
 
-template <int N>
+// F0: the first radix of both axes (0: make_axis_plan's choice)
+template <int N, int F0 = 0>
 struct Geo {
-    using PL = CPlan<N>;
+    using PL = CPlan<N, F0>;
     static_assert(PL::stages == 2, "plane passes assume two stages per axis");
     static constexpr int R0 = PL::radix(0), R1 = PL::radix(1);
     static constexpr int M0 = N / R0;  // stage-0 butterflies per line (stride M0)
@@ -113,10 +114,10 @@ __device__ __forceinline__ void prefetch_planes(const PassArgs& a, const Quad& q
 // plane_swizzle(p, y)), through the shared tile and one more block barrier.
 // tw holds the N twiddles in shared memory (visible to the block); the
 // block's threads all call this.
-template <int N, bool NATURAL = false>
+template <int N, bool NATURAL = false, int F0 = 0>
 __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q, int z, cx<float>* tile,
                                                const cx<float>* tw, cx<float>* spec_t) {
-    using G = Geo<N>;
+    using G = Geo<N, F0>;
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     const long long plane0 = (long long)z * NN;
     const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
@@ -202,9 +203,9 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
     }
 }
 
-template <int N, bool NATURAL>
-__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) pair_fwd(PassArgs a) {
-    using G = Geo<N>;
+template <int N, bool NATURAL, int F0>
+__global__ void __launch_bounds__(Geo<N, F0>::NT, Geo<N, F0>::kMinBlocks) pair_fwd(PassArgs a) {
+    using G = Geo<N, F0>;
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<float>* tile = reinterpret_cast<cx<float>*>(smem_raw);  // (y, x) at y * P + x
@@ -216,16 +217,16 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) pair_fwd(PassA
     if (threadIdx.x == 32 && a.lookahead > 0 && t + a.lookahead < (int)gridDim.y && (NN * 4) % 16 == 0)
         prefetch_planes(a, a.quads[a.t0 + t + a.lookahead], plane0, (uint32_t)(NN * 4), N3, false);
     __syncthreads();
-    pair_fwd_plane<N, NATURAL>(a, q, z, tile, tw, reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride);
+    pair_fwd_plane<N, NATURAL, F0>(a, q, z, tile, tw, reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride);
 }
 
 // Inputs of the inverse pass: thread (row y, half h) needs the transposed
 // plane's x positions of its first butterflies in its row of the tile.
 // Asynchronous 8-byte copies (the standalone kernel: all in flight at once,
 // completed by cp_async_wait_all) ...
-template <int N>
+template <int N, int F0 = 0>
 __device__ __forceinline__ void inv_issue_copies(const cx<float>* plane_in, cx<float>* tile) {
-    using G = Geo<N>;
+    using G = Geo<N, F0>;
     const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
     if (line < N) {
         const cx<float>* in = plane_in + line;
@@ -244,9 +245,9 @@ __device__ __forceinline__ cx<float> ld_cg2(const cx<float>* p) {
     asm volatile("ld.global.cg.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
     return mk(v.x, v.y);
 }
-template <int N>
+template <int N, int F0 = 0>
 __device__ __forceinline__ void inv_load_cg(const cx<float>* plane_in, cx<float>* tile) {
-    using G = Geo<N>;
+    using G = Geo<N, F0>;
     const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
     if (line < N) {
         const cx<float>* in = plane_in + line;
@@ -265,10 +266,10 @@ __device__ __forceinline__ void inv_load_cg(const cx<float>* plane_in, cx<float>
 // thread's own): 2-D inverse FFT, then W_a += v phi_b, W_b += v phi_a, ...
 // (Eq. 2) and the pair-energy partials (Eq. 4) into e_dst[2] (may be null).
 // red: 2 * NT / 32 doubles of shared memory.  Every thread of the block calls it.
-template <int N>
+template <int N, int F0 = 0>
 __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q, int z, cx<float>* tile,
                                                 const cx<float>* tw, double* red, double* e_dst) {
-    using G = Geo<N>;
+    using G = Geo<N, F0>;
     static_assert(N % 16 == 0, "the vector epilogue tiles planes by 4 rows x 16 columns");
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     const long long plane0 = (long long)z * NN;
@@ -413,9 +414,9 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) inv_accum(PassArgs a) {
-    using G = Geo<N>;
+template <int N, int F0>
+__global__ void __launch_bounds__(Geo<N, F0>::NT, Geo<N, F0>::kMinBlocks) inv_accum(PassArgs a) {
+    using G = Geo<N, F0>;
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[2 * (G::NT / 32)];
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) inv_accum(Pass
     cx<float>* tw = tile + N * G::P;
     const int z = blockIdx.x, t = blockIdx.y;
     const long long plane0 = (long long)z * NN;
-    inv_issue_copies<N>(reinterpret_cast<const cx<float>*>(a.src) + t * a.src_tstride + plane0, tile);
+    inv_issue_copies<N, F0>(reinterpret_cast<const cx<float>*>(a.src) + t * a.src_tstride + plane0, tile);
     const Quad q = a.quads[a.t0 + t];
     for (int j = threadIdx.x; j < N; j += G::NT) tw[j] = reinterpret_cast<const cx<float>*>(a.twx)[j];
     // the accumulation reads up to four function planes and updates up to four
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(Geo<N>::NT, Geo<N>::kMinBlocks) inv_accum(Pass
     if (threadIdx.x == 32 && (NN * 4) % 16 == 0) prefetch_planes(a, q, plane0, (uint32_t)(NN * 4), N3, true);
     cp_async_wait_all();
     __syncthreads();
-    inv_accum_plane<N>(a, q, z, tile, tw, red,
+    inv_accum_plane<N, F0>(a, q, z, tile, tw, red,
                        a.e_part != nullptr ? a.e_part + ((long long)(a.t0 + t) * gridDim.x + z) * 2 : nullptr);
 }
 
@@ -451,17 +452,17 @@ cudaError_t launch_plane(K k, size_t smem, int n, int nt, const PassArgs& a, int
 // which: 0 = pair product + forward plane FFT (transposed planes out),
 // 1 = inverse plane FFT + accumulation, 2 = the forward pass with the tile
 // passes' plane layout out (the hybrid variant)
-template <int N>
+template <int N, int F0 = 0>
 cudaError_t tplane_launch(int which, const PassArgs& a, int batch, cudaStream_t st) {
-    using G = plane_detail::Geo<N>;
+    using G = plane_detail::Geo<N, F0>;
     if (which == 2)
-        return plane_detail::launch_plane(plane_detail::pair_fwd<N, true>, G::smem, N, G::NT, a, batch, st);
+        return plane_detail::launch_plane(plane_detail::pair_fwd<N, true, F0>, G::smem, N, G::NT, a, batch, st);
     if constexpr (N % 16 != 0) {
         return cudaErrorInvalidValue;  // transposed planes: n % 16 == 0 only
     } else {
         if (which == 0)
-            return plane_detail::launch_plane(plane_detail::pair_fwd<N, false>, G::smem, N, G::NT, a, batch, st);
-        return plane_detail::launch_plane(plane_detail::inv_accum<N>, G::smem, N, G::NT, a, batch, st);
+            return plane_detail::launch_plane(plane_detail::pair_fwd<N, false, F0>, G::smem, N, G::NT, a, batch, st);
+        return plane_detail::launch_plane(plane_detail::inv_accum<N, F0>, G::smem, N, G::NT, a, batch, st);
     }
 }
 

@@ -90,10 +90,10 @@ __device__ __forceinline__ void pencil_last(const cx<float>* col, const cx<float
 // stride G), by one warp: forward stages, the fused middle with the Coulomb
 // factors kern_p0[z N^2 + p], the inverse stages, and the results to
 // dst_p0[z N^2 + p] (p = 0 .. G-1, in natural z order).
-template <int N, int G>
+template <int N, int G, int F0 = 0>
 __device__ __forceinline__ void pencils_compute(cx<float>* buf, const cx<float>* tw, const float* kern_p0,
                                                 cx<float>* dst_p0, int lane) {
-    using PL = CPlan<N>;
+    using PL = CPlan<N, F0>;
     // lanes past the group's pencils (G < 16) skip every step but the syncs
     const int pl = lane & 15, h = lane >> 4;
     const bool on = pl < G;
@@ -114,9 +114,9 @@ __device__ __forceinline__ void pencils_compute(cx<float>* buf, const cx<float>*
     if (on) pencil_last<PL::radix(0), N, G>(col, tw, out, h);
 }
 
-template <int N, int G>
+template <int N, int G, int F0>
 __global__ void __launch_bounds__(32) zline_coulomb(PassArgs a) {
-    using PL = CPlan<N>;
+    using PL = CPlan<N, F0>;
     static_assert(PL::stages >= 2, "the fused middle needs two stages or more");
     static_assert(G % 2 == 0 && G <= 16 && (N * N) % G == 0, "pencil group");
     constexpr long long NN = (long long)N * N;
@@ -144,16 +144,17 @@ __global__ void __launch_bounds__(32) zline_coulomb(PassArgs a) {
         mbar_wait_bounded(&bar, 0, nullptr, 0);
         return;
     }
-    pencils_compute<N, G>(buf, tw, reinterpret_cast<const float*>(a.kern) + p0,
+    pencils_compute<N, G, F0>(buf, tw, reinterpret_cast<const float*>(a.kern) + p0,
                           reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride + p0, lane);
 }
 
 }  // namespace zline_detail
 
-template <int N>
+// F0: the first radix of the z axis (0: make_axis_plan's choice)
+template <int N, int F0 = 0>
 cudaError_t zline_launch(const PassArgs& a, int batch, cudaStream_t st) {
     constexpr int G = zline_group(N);
-    auto k = zline_detail::zline_coulomb<N, G>;
+    auto k = zline_detail::zline_coulomb<N, G, F0>;
     static bool carveout = [&] {
         cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         cudaGetLastError();

@@ -355,7 +355,8 @@ def test_tune_cache_round_trip(monkeypatch, tmp_path):
     assert not c1["from_tune_cache"] and c1["row_block_ms"] and c1["tune_ms"]
     lines = path.read_text().splitlines()
     assert len(lines) == 1 and lines[0].startswith("32x32x32 n8 f32 ")
-    assert lines[0].endswith(f"= {c1['pair_variant']} {c1['pair_streams']} {c1['row_block']}")
+    # variant, streams, row block, radix plan (0: make_axis_plan's, the only one at 32^3)
+    assert lines[0].endswith(f"= {c1['pair_variant']} {c1['pair_streams']} {c1['row_block']} 0")
     p2 = ace.Plan(s["grid"], s["cell"], s["ecut"], 8, "mixed")
     c2 = p2.config()
     assert c2["from_tune_cache"] and not c2["tune_ms"] and not c2["row_block_ms"]
