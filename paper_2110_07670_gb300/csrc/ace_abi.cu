@@ -1406,9 +1406,9 @@ int pair_tables(ace_plan* P, int r0) {
         for (int y = 0; y < n1; ++y)
             for (int xs = 0; xs < n2; ++xs) {
                 const size_t e = ((size_t)z * n1 + y) * n2 + xs;
-                if (P->zline) kern[e] = (float)k(g2_at(z, y, swz ? plane_swizzle(xs, y) : xs));
+                if (P->zline) kern[e] = (float)k(g2_at(z, y, swz ? plane_swizzle(xs, y, n2) : xs));
                 if (with_t) kern_t[((size_t)z * n2 + xs) * n1 + y] = (float)k(g2_at(z, y, xs));  // plane [x][y]
-                if (inline_tab) kern_r[e] = (R)k(g2_at(z, y, swz_i ? plane_swizzle(xs, y) : xs));
+                if (inline_tab) kern_r[e] = (R)k(g2_at(z, y, swz_i ? plane_swizzle(xs, y, n2) : xs));
             }
     if (with_t) {
         if (!P->d_kern_t) ACE_TRY(dalloc((void**)&P->d_kern_t, kern_t.size() * sizeof(float)));
@@ -1479,8 +1479,8 @@ int create_impl(ace_plan* P, const ace_opts* opts) {
             mn[d] = pos[d][((-v % P->n[d]) + P->n[d]) % P->n[d]];
         }
         if (swz) {
-            m[2] = plane_swizzle(m[2], m[1]);
-            mn[2] = plane_swizzle(mn[2], mn[1]);
+            m[2] = plane_swizzle(m[2], m[1], P->n[2]);
+            mn[2] = plane_swizzle(mn[2], mn[1], P->n[2]);
         }
         ip[p] = (m[0] * P->n[1] + m[1]) * P->n[2] + m[2];
         in[p] = (mn[0] * P->n[1] + mn[1]) * P->n[2] + mn[2];

@@ -84,12 +84,20 @@ constexpr int cube_xy_threads(int n) {
     return n == 32 ? 128 : n == 96 ? 384 : n == 120 ? 480 : n == 160 ? 320 : (n * n >= 12000 ? 512 : 256);
 }
 // Plane layout of N % 16 == 0 cubes: within each 16-element block of a row,
-// x position p sits in slot p ^ (((p >> 4) & 7) | ((y & 1) << 3)); the
-// permutation is its own inverse, keeps blocks in place, spreads the
-// butterflies of the contiguous x stages over all shared-memory banks, and
-// alternates bank halves between neighbouring rows.
+// x position p sits in slot p ^ w, w = (((p >> 4) + s_N y) & 7) | ((y & 1) << 3);
+// the permutation is its own inverse and keeps blocks in place.  Bit 3 of w
+// alternates bank halves between neighbouring rows (the strided x stage: two
+// rows per half-warp, 8 butterflies each); the low bits rotate with the row by
+// s_N so that the contiguous x stage, whose 16 butterflies per half-warp run
+// across a row boundary (12 per row at N = 96), lands on 16 distinct 8-byte
+// bank pairs: s_N = 6 at N = 96 (radix 8 last), 5 at 80, 2 at 32, by a count
+// of the bank conflicts of every stage's accesses for each s in 0..7 (at 160
+// no s helps by more than 1%).  Columns always read 16 consecutive slots.
 constexpr bool cube_swizzle(int n) { return n % 16 == 0; }
-__host__ __device__ constexpr int plane_swizzle(int p, int y) { return p ^ (((p >> 4) & 7) | ((y & 1) << 3)); }
+__host__ __device__ constexpr int plane_swizzle_rot(int n) { return n == 96 ? 6 : n == 80 ? 5 : n == 32 ? 2 : 0; }
+__host__ __device__ constexpr int plane_swizzle(int p, int y, int n) {
+    return p ^ ((((p >> 4) + plane_swizzle_rot(n) * y) & 7) | ((y & 1) << 3));
+}
 constexpr int cube_z_threads(int) { return 256; }
 constexpr int cube_z_tx(int n) {  // largest even divisor of n up to 32
     for (int d = 32; d >= 2; d -= 2)

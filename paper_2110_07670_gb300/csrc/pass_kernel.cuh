@@ -169,7 +169,7 @@ __device__ __forceinline__ void static_stage_rows_swizzled(cx<R>* buf, const cx<
         const int p0 = beta * LB + j;
         int idx[RAD];
 #pragma unroll
-        for (int q = 0; q < RAD; ++q) idx[q] = plane_swizzle(p0 + q * M, line);
+        for (int q = 0; q < RAD; ++q) idx[q] = plane_swizzle(p0 + q * M, line, N);
         butterfly_at<RAD, SGN, R>(buf + line * N, idx, tw, TS * j, M > 1 && j > 0);
     }
     __syncthreads();
@@ -186,7 +186,7 @@ __device__ __forceinline__ void static_stage_cols_swizzled(cx<R>* buf, const cx<
         const int y0 = beta * LB + j;
         int idx[RAD];
 #pragma unroll
-        for (int q = 0; q < RAD; ++q) idx[q] = (y0 + q * M) * N + plane_swizzle(p, y0 + q * M);
+        for (int q = 0; q < RAD; ++q) idx[q] = (y0 + q * M) * N + plane_swizzle(p, y0 + q * M, N);
         butterfly_at<RAD, SGN, R>(buf, idx, tw, TS * j, M > 1 && j > 0);
     }
     __syncthreads();
@@ -231,13 +231,13 @@ struct CubeShape {
     __device__ static int slot(int e) {
         if constexpr (kSwzTile) {
             const int row = e / N, col = e - row * N;
-            return row * N + plane_swizzle(col, row);
+            return row * N + plane_swizzle(col, row, N);
         } else {
             return e;
         }
     }
     __device__ static int xpos(int s, int y) {
-        if constexpr (kSwzLayout) return plane_swizzle(s, y);
+        if constexpr (kSwzLayout) return plane_swizzle(s, y, N);
         else return s;
     }
     template <int SGN, typename R>
@@ -264,22 +264,29 @@ struct CubeShape {
 // row).  Single-precision compile-time tiles read them as two 16-byte shared
 // loads: the plane swizzle keeps an aligned group of four x positions in one
 // aligned group of four slots, element i in slot i ^ c with c the low two bits
-// of the row's swizzle word, so the first load takes the slot pair holding
-// elements 0 and 1 and a swap inside each pair undoes c's low bit.  (Four
-// 8-byte loads at a 32-byte lane stride conflicted 8-way in the banks.)
+// of the row's swizzle word: one load takes the slot pair holding elements 0
+// and 1, the other the pair holding 2 and 3, and a swap inside each pair
+// undoes c's low bit.  (Four 8-byte loads at a 32-byte lane stride conflicted
+// 8-way in the banks.)
 template <typename Shape, typename R>
 __device__ __forceinline__ void tile_load4(const Shape& S, const cx<R>* tile, int e, cx<R> (&v)[4]) {
     if constexpr (sizeof(R) == 4 && Shape::kCube) {
-        int base = e, c = 0;
+        int base = e, c = 0, first = 0;
         if constexpr (Shape::kSwzTile) {
             const int row = e / Shape::n2, col = e - row * Shape::n2;
-            const int k = ((col >> 4) & 7) | ((row & 1) << 3);
+            const int k = (((col >> 4) + plane_swizzle_rot(Shape::n2) * row) & 7) | ((row & 1) << 3);
             base = row * Shape::n2 + (col ^ (k & 12));
             c = k & 3;
+            first = (col >> 4) & 1;
         }
+        // the slot pair holding elements 0 and 1 is h; lanes of neighbouring
+        // 16-element blocks load their two pairs in opposite orders, so the 8
+        // lanes of a quarter-warp (two blocks) cover all 32 banks per load
         const int h = (c >> 1) & 1;
-        const float4 q0 = *reinterpret_cast<const float4*>(tile + base + 2 * h);
-        const float4 q1 = *reinterpret_cast<const float4*>(tile + base + 2 * (h ^ 1));
+        const float4 qa = *reinterpret_cast<const float4*>(tile + base + 2 * first);
+        const float4 qb = *reinterpret_cast<const float4*>(tile + base + 2 * (first ^ 1));
+        const float4 q0 = first == h ? qa : qb;
+        const float4 q1 = first == h ? qb : qa;
         const bool sw = (c & 1) != 0;
         v[0] = sw ? mk(q0.z, q0.w) : mk(q0.x, q0.y);
         v[1] = sw ? mk(q0.x, q0.y) : mk(q0.z, q0.w);

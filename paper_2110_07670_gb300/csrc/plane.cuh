@@ -198,7 +198,7 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
         cx<float>* out = spec_t + plane0;
         for (int e = threadIdx.x; e < N * N; e += G::NT) {
             const int y = e / N, x = e - y * N;
-            out[y * N + (cube_swizzle(N) ? plane_swizzle(x, y) : x)] = tile[y * G::P + x];
+            out[y * N + (cube_swizzle(N) ? plane_swizzle(x, y, N) : x)] = tile[y * G::P + x];
         }
     }
 }
