@@ -14,12 +14,13 @@
 // y (coalesced), while the pass that works on y lines meets the real-space
 // functions with the lanes along x (coalesced).
 //
-// Every line (a y column or an x row of the plane) belongs to two threads, the
-// two halves of a warp (lanes l and l + 16), which split its butterflies; a
-// stage needs only __syncwarp, and the plane needs one block barrier between
-// its y and x lines.  The shared tile has an odd row pitch (N + 1), so 16
-// lanes on 16 consecutive rows, or on 16 consecutive columns, hit 16 distinct
-// bank pairs.  The accumulation after the inverse runs on 4-wide vectors from
+// Every line (a y column or an x row of the plane) belongs to two threads,
+// thread l and thread N + l, which split its butterflies; a warp's lanes take
+// 32 consecutive lines, so a load of the functions' row segment is one
+// 128-byte line, and the two halves of a line meet at block barriers between
+// the stages.  The shared tile has an odd row pitch (N + 1), so 16 lanes on
+// 16 consecutive rows, or on 16 consecutive columns, hit 16 distinct bank
+// pairs.  The accumulation after the inverse runs on 4-wide vectors from
 // the shared tile (a final block barrier).  Both axes have two stages (radix R0 with N / R0 butterflies of
 // stride N / R0, then radix R1 on adjacent positions).
 #pragma once
@@ -120,8 +121,8 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
     using G = Geo<N, F0>;
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     const long long plane0 = (long long)z * NN;
-    const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
-    const bool active = line < N;
+    const int h = (int)threadIdx.x >= N, line = (int)threadIdx.x - h * N;
+    const bool active = line < N;  // threads past 2 N: line >= N
     const bool has2 = q.c >= 0;
 
     // y lines (thread owns column x): stage 0 straight from the functions
@@ -145,7 +146,7 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
             for (int s = 0; s < G::R0; ++s) tile[(j + s * G::M0) * G::P + x] = u[s];
         }
     }
-    __syncwarp();
+    __syncthreads();
     if (active) {
         const int x = line;
         for (int b = h; b < G::B1; b += 2) {
@@ -173,7 +174,7 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
             for (int s = 0; s < G::R0; ++s) row[j + s * G::M0] = u[s];
         }
     }
-    __syncwarp();
+    __syncthreads();
     if (active) {
         cx<float>* row = tile + line * G::P;
         cx<float>* out = spec_t + plane0 + line;
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(Geo<N, F0>::NT, Geo<N, F0>::kMinBlocks) pair_f
 template <int N, int F0 = 0>
 __device__ __forceinline__ void inv_issue_copies(const cx<float>* plane_in, cx<float>* tile) {
     using G = Geo<N, F0>;
-    const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
+    const int h = (int)threadIdx.x >= N, line = (int)threadIdx.x - h * N;
     if (line < N) {
         const cx<float>* in = plane_in + line;
         cx<float>* row = tile + line * G::P;
@@ -248,7 +249,7 @@ __device__ __forceinline__ cx<float> ld_cg2(const cx<float>* p) {
 template <int N, int F0 = 0>
 __device__ __forceinline__ void inv_load_cg(const cx<float>* plane_in, cx<float>* tile) {
     using G = Geo<N, F0>;
-    const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
+    const int h = (int)threadIdx.x >= N, line = (int)threadIdx.x - h * N;
     if (line < N) {
         const cx<float>* in = plane_in + line;
         cx<float>* row = tile + line * G::P;
@@ -273,8 +274,8 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
     static_assert(N % 16 == 0, "the vector epilogue tiles planes by 4 rows x 16 columns");
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     const long long plane0 = (long long)z * NN;
-    const int line = (threadIdx.x >> 5) * 16 + (threadIdx.x & 15), h = (threadIdx.x >> 4) & 1;
-    const bool active = line < N;
+    const int h = (int)threadIdx.x >= N, line = (int)threadIdx.x - h * N;
+    const bool active = line < N;  // threads past 2 N: line >= N
     // x lines (thread owns row y): both inverse stages in shared memory
     if (active) {
         cx<float>* row = tile + line * G::P;
@@ -287,7 +288,7 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
             for (int s = 0; s < G::R1; ++s) row[b * G::R1 + s] = u[s];
         }
     }
-    __syncwarp();
+    __syncthreads();
     if (active) {
         cx<float>* row = tile + line * G::P;
         for (int j = h; j < G::M0; j += 2) {
@@ -314,7 +315,7 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
             for (int s = 0; s < G::R1; ++s) tile[(b * G::R1 + s) * G::P + x] = u[s];
         }
     }
-    __syncwarp();
+    __syncthreads();
     if (active) {
         const int x = line;
         for (int j = h; j < G::M0; j += 2) {
