@@ -147,6 +147,26 @@ struct PipeArgs {
 };
 cudaError_t pipeline_pair_launch(int n, const PassArgs& a, const PipeArgs& p, cudaStream_t st);
 
+#if defined(__CUDACC__)
+// Sum of v over the 32 lanes of a warp in float-float arithmetic (Knuth's
+// TwoSum at every step, the rounding error carried in lo): about 2^-44 of
+// the sum of |v| on the FP32 pipes, where a double reduction would queue on
+// this GPU's FP64 pipe (a small fraction of the FP32 rate).  Every lane gets
+// the same result (TwoSum's error is exact, so both orders of a step agree).
+__device__ __forceinline__ double warp_sum_ff(float v) {
+    float hi = v, lo = 0.0f;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = hi + h2, bp = s - hi;
+        const float err = (hi - (s - bp)) + (h2 - bp);
+        hi = s;
+        lo = lo + l2 + err;
+    }
+    return (double)hi + (double)lo;
+}
+#endif
+
 // True while `st` records into a CUDA graph: launchers then leave kernel
 // attributes alone (set by the same launch outside capture before).
 inline bool stream_capturing(cudaStream_t st) {

@@ -666,10 +666,17 @@ __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pa
         }
     }
     if (a.e_part != nullptr) {
-        double d1 = double(e1), d2 = double(e2);
-        for (int o = 16; o > 0; o >>= 1) {
-            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-            d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        double d1, d2;
+        if constexpr (sizeof(R) == 4) {
+            d1 = warp_sum_ff(e1);
+            d2 = warp_sum_ff(e2);
+        } else {
+            d1 = double(e1);
+            d2 = double(e2);
+            for (int o = 16; o > 0; o >>= 1) {
+                d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+                d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+            }
         }
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = S.nt() >> 5;
         if (lane == 0) {

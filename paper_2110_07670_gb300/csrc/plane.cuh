@@ -392,11 +392,7 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
         }
     }
     if (e_dst != nullptr) {
-        double d1 = double(e1), d2 = double(e2);
-        for (int o = 16; o > 0; o >>= 1) {
-            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-            d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-        }
+        const double d1 = warp_sum_ff(e1), d2 = warp_sum_ff(e2);
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         if (lane == 0) {
             red[2 * warp] = d1;
