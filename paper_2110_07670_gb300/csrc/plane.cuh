@@ -15,7 +15,8 @@
 // functions with the lanes along x (coalesced).
 //
 // Every line (a y column or an x row of the plane) belongs to two threads,
-// thread l and thread N + l, which split its butterflies; a warp's lanes take
+// thread l and thread N + l (four, up to 3N + l, on the planes of 120^3 and
+// up, which leave one block per SM), which split its butterflies; a warp's lanes take
 // 32 consecutive lines, so a load of the functions' row segment is one
 // 128-byte line, and the two halves of a line meet at block barriers between
 // the stages.  The shared tile has an odd row pitch (N + 1), so 16 lanes on
@@ -32,8 +33,9 @@
 namespace ace {
 namespace plane_detail {
 
-// F0: the first radix of both axes (0: make_axis_plan's choice)
-template <int N, int F0 = 0>
+// F0: the first radix of both axes (0: make_axis_plan's choice); TPL: threads
+// per line (2, or 4 for the large planes that leave one block per SM)
+template <int N, int F0 = 0, int TPL = 2>
 struct Geo {
     using PL = CPlan<N, F0>;
     static_assert(PL::stages == 2, "plane passes assume two stages per axis");
@@ -41,7 +43,7 @@ struct Geo {
     static constexpr int M0 = N / R0;  // stage-0 butterflies per line (stride M0)
     static constexpr int B1 = N / R1;  // stage-1 butterflies per line (adjacent)
     static constexpr int P = N + 1;    // shared row pitch, odd
-    static constexpr int NT = (2 * N + 31) / 32 * 32;
+    static constexpr int NT = (TPL * N + 31) / 32 * 32;
     static constexpr size_t smem = (size_t)(N * P + N) * sizeof(cx<float>);
     // resident blocks per SM: 228 KB of shared memory, 1 KB reserved per block
     // (and a little static shared memory)
@@ -115,14 +117,14 @@ __device__ __forceinline__ void prefetch_planes(const PassArgs& a, const Quad& q
 // plane_swizzle(p, y)), through the shared tile and one more block barrier.
 // tw holds the N twiddles in shared memory (visible to the block); the
 // block's threads all call this.
-template <int N, bool NATURAL = false, int F0 = 0>
+template <int N, bool NATURAL = false, int F0 = 0, int TPL = 2>
 __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q, int z, cx<float>* tile,
                                                const cx<float>* tw, cx<float>* spec_t) {
-    using G = Geo<N, F0>;
+    using G = Geo<N, F0, TPL>;
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     const long long plane0 = (long long)z * NN;
-    const int h = (int)threadIdx.x >= N, line = (int)threadIdx.x - h * N;
-    const bool active = line < N;  // threads past 2 N: line >= N
+    const int h = (int)threadIdx.x / N, line = (int)threadIdx.x - h * N;
+    const bool active = h < TPL;  // threads past TPL N idle
     const bool has2 = q.c >= 0;
 
     // y lines (thread owns column x): stage 0 straight from the functions
@@ -132,7 +134,7 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
         const float* pb = reinterpret_cast<const float*>(a.fr) + q.b * N3 + plane0 + x;
         const float* pc = reinterpret_cast<const float*>(a.fl) + (has2 ? q.c : q.a) * N3 + plane0 + x;
         const float* pd = reinterpret_cast<const float*>(a.fr) + (has2 ? q.d : q.b) * N3 + plane0 + x;
-        for (int j = h; j < G::M0; j += 2) {
+        for (int j = h; j < G::M0; j += TPL) {
             cx<float> u[G::R0];
 #pragma unroll
             for (int k = 0; k < G::R0; ++k) {
@@ -149,7 +151,7 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
     __syncthreads();
     if (active) {
         const int x = line;
-        for (int b = h; b < G::B1; b += 2) {
+        for (int b = h; b < G::B1; b += TPL) {
             cx<float> u[G::R1];
 #pragma unroll
             for (int k = 0; k < G::R1; ++k) u[k] = tile[(b * G::R1 + k) * G::P + x];
@@ -164,7 +166,7 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
     // transposed spectrum plane
     if (active) {
         cx<float>* row = tile + line * G::P;
-        for (int j = h; j < G::M0; j += 2) {
+        for (int j = h; j < G::M0; j += TPL) {
             cx<float> u[G::R0];
 #pragma unroll
             for (int k = 0; k < G::R0; ++k) u[k] = row[j + k * G::M0];
@@ -178,7 +180,7 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
     if (active) {
         cx<float>* row = tile + line * G::P;
         cx<float>* out = spec_t + plane0 + line;
-        for (int b = h; b < G::B1; b += 2) {
+        for (int b = h; b < G::B1; b += TPL) {
             cx<float> u[G::R1];
 #pragma unroll
             for (int k = 0; k < G::R1; ++k) u[k] = row[b * G::R1 + k];
@@ -204,9 +206,9 @@ __device__ __forceinline__ void pair_fwd_plane(const PassArgs& a, const Quad& q,
     }
 }
 
-template <int N, bool NATURAL, int F0>
-__global__ void __launch_bounds__(Geo<N, F0>::NT, Geo<N, F0>::kMinBlocks) pair_fwd(PassArgs a) {
-    using G = Geo<N, F0>;
+template <int N, bool NATURAL, int F0, int TPL>
+__global__ void __launch_bounds__(Geo<N, F0, TPL>::NT, Geo<N, F0, TPL>::kMinBlocks) pair_fwd(PassArgs a) {
+    using G = Geo<N, F0, TPL>;
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<float>* tile = reinterpret_cast<cx<float>*>(smem_raw);  // (y, x) at y * P + x
@@ -218,21 +220,21 @@ __global__ void __launch_bounds__(Geo<N, F0>::NT, Geo<N, F0>::kMinBlocks) pair_f
     if (threadIdx.x == 32 && a.lookahead > 0 && t + a.lookahead < (int)gridDim.y && (NN * 4) % 16 == 0)
         prefetch_planes(a, a.quads[a.t0 + t + a.lookahead], plane0, (uint32_t)(NN * 4), N3, false);
     __syncthreads();
-    pair_fwd_plane<N, NATURAL, F0>(a, q, z, tile, tw, reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride);
+    pair_fwd_plane<N, NATURAL, F0, TPL>(a, q, z, tile, tw, reinterpret_cast<cx<float>*>(a.dst) + t * a.dst_tstride);
 }
 
 // Inputs of the inverse pass: thread (row y, half h) needs the transposed
 // plane's x positions of its first butterflies in its row of the tile.
 // Asynchronous 8-byte copies (the standalone kernel: all in flight at once,
 // completed by cp_async_wait_all) ...
-template <int N, int F0 = 0>
+template <int N, int F0 = 0, int TPL = 2>
 __device__ __forceinline__ void inv_issue_copies(const cx<float>* plane_in, cx<float>* tile) {
-    using G = Geo<N, F0>;
-    const int h = (int)threadIdx.x >= N, line = (int)threadIdx.x - h * N;
-    if (line < N) {
+    using G = Geo<N, F0, TPL>;
+    const int h = (int)threadIdx.x / N, line = (int)threadIdx.x - h * N;
+    if (h < TPL) {
         const cx<float>* in = plane_in + line;
         cx<float>* row = tile + line * G::P;
-        for (int b = h; b < G::B1; b += 2)
+        for (int b = h; b < G::B1; b += TPL)
 #pragma unroll
             for (int k = 0; k < G::R1; ++k) cp_async8(row + b * G::R1 + k, in + (long long)(b * G::R1 + k) * N);
     }
@@ -246,14 +248,14 @@ __device__ __forceinline__ cx<float> ld_cg2(const cx<float>* p) {
     asm volatile("ld.global.cg.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
     return mk(v.x, v.y);
 }
-template <int N, int F0 = 0>
+template <int N, int F0 = 0, int TPL = 2>
 __device__ __forceinline__ void inv_load_cg(const cx<float>* plane_in, cx<float>* tile) {
-    using G = Geo<N, F0>;
-    const int h = (int)threadIdx.x >= N, line = (int)threadIdx.x - h * N;
-    if (line < N) {
+    using G = Geo<N, F0, TPL>;
+    const int h = (int)threadIdx.x / N, line = (int)threadIdx.x - h * N;
+    if (h < TPL) {
         const cx<float>* in = plane_in + line;
         cx<float>* row = tile + line * G::P;
-        for (int b = h; b < G::B1; b += 2) {
+        for (int b = h; b < G::B1; b += TPL) {
             cx<float> u[G::R1];
 #pragma unroll
             for (int k = 0; k < G::R1; ++k) u[k] = ld_cg2(in + (long long)(b * G::R1 + k) * N);
@@ -267,19 +269,19 @@ __device__ __forceinline__ void inv_load_cg(const cx<float>* plane_in, cx<float>
 // thread's own): 2-D inverse FFT, then W_a += v phi_b, W_b += v phi_a, ...
 // (Eq. 2) and the pair-energy partials (Eq. 4) into e_dst[2] (may be null).
 // red: 2 * NT / 32 doubles of shared memory.  Every thread of the block calls it.
-template <int N, int F0 = 0>
+template <int N, int F0 = 0, int TPL = 2>
 __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q, int z, cx<float>* tile,
                                                 const cx<float>* tw, double* red, double* e_dst) {
-    using G = Geo<N, F0>;
+    using G = Geo<N, F0, TPL>;
     static_assert(N % 16 == 0, "the vector epilogue tiles planes by 4 rows x 16 columns");
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     const long long plane0 = (long long)z * NN;
-    const int h = (int)threadIdx.x >= N, line = (int)threadIdx.x - h * N;
-    const bool active = line < N;  // threads past 2 N: line >= N
+    const int h = (int)threadIdx.x / N, line = (int)threadIdx.x - h * N;
+    const bool active = h < TPL;  // threads past TPL N idle
     // x lines (thread owns row y): both inverse stages in shared memory
     if (active) {
         cx<float>* row = tile + line * G::P;
-        for (int b = h; b < G::B1; b += 2) {
+        for (int b = h; b < G::B1; b += TPL) {
             cx<float> u[G::R1];
 #pragma unroll
             for (int k = 0; k < G::R1; ++k) u[k] = row[b * G::R1 + k];
@@ -291,7 +293,7 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
     __syncthreads();
     if (active) {
         cx<float>* row = tile + line * G::P;
-        for (int j = h; j < G::M0; j += 2) {
+        for (int j = h; j < G::M0; j += TPL) {
             cx<float> u[G::R0];
 #pragma unroll
             for (int k = 0; k < G::R0; ++k) u[k] = row[j + k * G::M0];
@@ -306,7 +308,7 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
     // y lines (thread owns column x): both inverse stages in shared memory
     if (active) {
         const int x = line;
-        for (int b = h; b < G::B1; b += 2) {
+        for (int b = h; b < G::B1; b += TPL) {
             cx<float> u[G::R1];
 #pragma unroll
             for (int k = 0; k < G::R1; ++k) u[k] = tile[(b * G::R1 + k) * G::P + x];
@@ -318,7 +320,7 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
     __syncthreads();
     if (active) {
         const int x = line;
-        for (int j = h; j < G::M0; j += 2) {
+        for (int j = h; j < G::M0; j += TPL) {
             cx<float> u[G::R0];
 #pragma unroll
             for (int k = 0; k < G::R0; ++k) u[k] = tile[(j + k * G::M0) * G::P + x];
@@ -411,9 +413,9 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
     }
 }
 
-template <int N, int F0>
-__global__ void __launch_bounds__(Geo<N, F0>::NT, Geo<N, F0>::kMinBlocks) inv_accum(PassArgs a) {
-    using G = Geo<N, F0>;
+template <int N, int F0, int TPL>
+__global__ void __launch_bounds__(Geo<N, F0, TPL>::NT, Geo<N, F0, TPL>::kMinBlocks) inv_accum(PassArgs a) {
+    using G = Geo<N, F0, TPL>;
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[2 * (G::NT / 32)];
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(Geo<N, F0>::NT, Geo<N, F0>::kMinBlocks) inv_ac
     cx<float>* tw = tile + N * G::P;
     const int z = blockIdx.x, t = blockIdx.y;
     const long long plane0 = (long long)z * NN;
-    inv_issue_copies<N, F0>(reinterpret_cast<const cx<float>*>(a.src) + t * a.src_tstride + plane0, tile);
+    inv_issue_copies<N, F0, TPL>(reinterpret_cast<const cx<float>*>(a.src) + t * a.src_tstride + plane0, tile);
     const Quad q = a.quads[a.t0 + t];
     for (int j = threadIdx.x; j < N; j += G::NT) tw[j] = reinterpret_cast<const cx<float>*>(a.twx)[j];
     // the accumulation reads up to four function planes and updates up to four
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(Geo<N, F0>::NT, Geo<N, F0>::kMinBlocks) inv_ac
     if (threadIdx.x == 32 && (NN * 4) % 16 == 0) prefetch_planes(a, q, plane0, (uint32_t)(NN * 4), N3, true);
     cp_async_wait_all();
     __syncthreads();
-    inv_accum_plane<N, F0>(a, q, z, tile, tw, red,
+    inv_accum_plane<N, F0, TPL>(a, q, z, tile, tw, red,
                        a.e_part != nullptr ? a.e_part + ((long long)(a.t0 + t) * gridDim.x + z) * 2 : nullptr);
 }
 
@@ -451,15 +453,16 @@ cudaError_t launch_plane(K k, size_t smem, int n, int nt, const PassArgs& a, int
 // passes' plane layout out (the hybrid variant)
 template <int N, int F0 = 0>
 cudaError_t tplane_launch(int which, const PassArgs& a, int batch, cudaStream_t st) {
-    using G = plane_detail::Geo<N, F0>;
+    constexpr int TPL = N >= 120 ? 4 : 2;  // one plane block per SM from 120^3 up: more warps per line
+    using G = plane_detail::Geo<N, F0, TPL>;
     if (which == 2)
-        return plane_detail::launch_plane(plane_detail::pair_fwd<N, true, F0>, G::smem, N, G::NT, a, batch, st);
+        return plane_detail::launch_plane(plane_detail::pair_fwd<N, true, F0, TPL>, G::smem, N, G::NT, a, batch, st);
     if constexpr (N % 16 != 0) {
         return cudaErrorInvalidValue;  // transposed planes: n % 16 == 0 only
     } else {
         if (which == 0)
-            return plane_detail::launch_plane(plane_detail::pair_fwd<N, false, F0>, G::smem, N, G::NT, a, batch, st);
-        return plane_detail::launch_plane(plane_detail::inv_accum<N, F0>, G::smem, N, G::NT, a, batch, st);
+            return plane_detail::launch_plane(plane_detail::pair_fwd<N, false, F0, TPL>, G::smem, N, G::NT, a, batch, st);
+        return plane_detail::launch_plane(plane_detail::inv_accum<N, F0, TPL>, G::smem, N, G::NT, a, batch, st);
     }
 }
 

@@ -64,8 +64,10 @@ def system(n):
 
 
 # (box, first radix, variant): every radix plan with compile-time kernels,
-# make_axis_plan's first, under every pair-pass variant the box has
-CASES = [(96, r, v) for r in (12, 8, 16) for v in (1, 2, 3, 4)] + \
+# make_axis_plan's first, under every pair-pass variant the box has; 80^3
+# (one plan) for its own rotation of the plane swizzle
+CASES = [(80, 10, v) for v in (1, 2, 3, 4)] + \
+        [(96, r, v) for r in (12, 8, 16) for v in (1, 2, 3, 4)] + \
         [(120, r, v) for r in (12, 10, 8) for v in (1, 4)] + \
         [(160, r, v) for r in (16, 10) for v in (1, 2, 3, 4)]
 
