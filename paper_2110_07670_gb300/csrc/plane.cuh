@@ -47,7 +47,10 @@ struct Geo {
     static constexpr size_t smem = (size_t)(N * P + N) * sizeof(cx<float>);
     // resident blocks per SM: 228 KB of shared memory, 1 KB reserved per block
     // (and a little static shared memory)
-    static constexpr int kMinBlocks = 3 * (smem + 1280) <= 228 * 1024 ? 3 : (2 * (smem + 1280) <= 228 * 1024 ? 2 : 1);
+    static constexpr int kSmemBlocks = 3 * (smem + 1280) <= 228 * 1024 ? 3 : (2 * (smem + 1280) <= 228 * 1024 ? 2 : 1);
+    // and no more blocks than leave 72 registers per thread
+    static constexpr int kRegBlocks = 65536 / (NT * 72) > 0 ? 65536 / (NT * 72) : 1;
+    static constexpr int kMinBlocks = kSmemBlocks < kRegBlocks ? kSmemBlocks : kRegBlocks;
 };
 
 // forward stage-0 twiddles on the outputs (DIF), inverse on the inputs (conjugate)
@@ -453,7 +456,8 @@ cudaError_t launch_plane(K k, size_t smem, int n, int nt, const PassArgs& a, int
 // passes' plane layout out (the hybrid variant)
 template <int N, int F0 = 0>
 cudaError_t tplane_launch(int which, const PassArgs& a, int batch, cudaStream_t st) {
-    constexpr int TPL = N >= 120 ? 4 : 2;  // one plane block per SM from 120^3 up: more warps per line
+    constexpr int TPL = N >= 120 ? 4 : 2;  // one plane block per SM from 120^3 up: more warps per line (at 96^3 two
+                                           // blocks of four threads per line ran P1 4% slower than three of two)
     using G = plane_detail::Geo<N, F0, TPL>;
     if (which == 2)
         return plane_detail::launch_plane(plane_detail::pair_fwd<N, true, F0, TPL>, G::smem, N, G::NT, a, batch, st);
