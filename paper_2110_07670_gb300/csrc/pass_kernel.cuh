@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(Shape::kMaxThreads, Shape::kMinBlocks) tile_pa
     const Shape S(a);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
-    __shared__ double red[2 * 16];
+    __shared__ double red[2 * (Shape::kMaxThreads / 32)];  // a pair of energy partials per warp
     const int tile_elems = S.tz * S.ty * S.tx;
     cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
     cx<R>* twx = tile + tile_elems;

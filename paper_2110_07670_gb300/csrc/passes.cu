@@ -15,7 +15,8 @@ cudaError_t launch_pass(const PassArgs& a0, const PassShape& s, int pro, int epi
     a.bulk = s.bulk;
     a.vec = s.vec;
     if (batch <= 0) return cudaSuccess;
-    if (s.threads > 512 || (s.threads & 31)) return cudaErrorInvalidConfiguration;
+    // runtime-geometry kernels are bounded at 512 threads, compile-time cubes at their own count
+    if (s.threads > (s.cube ? 1024 : 512) || (s.threads & 31)) return cudaErrorInvalidConfiguration;
     if (s.cube) {
         if (sizeof(R) != 4 || a.n0 != a.n1 || a.n1 != a.n2) return cudaErrorInvalidValue;
         return cube_pass_launch(a.n0, a, s, pro, epi, mid, sgn, batch, st);
