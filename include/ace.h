@@ -268,6 +268,20 @@ int ace_scdm(ace_plan* plan, const void* psi_G, int n_occ, int preselect, void* 
 int ace_apply(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T, void* Kpsi, void* stream);
 
 /*
+ * Prepare the inner steps of one outer MTS step (Section 2.3): the plan makes
+ * a split copy of xi (TF32 hi / lo in the tensor cores' operand tiles, twice
+ * xi's size, plan-owned) that later ace_apply calls with the same xi pointer
+ * and n_occ read by bulk copies instead of splitting xi themselves (same
+ * arithmetic, same results).  The copy is used until the next ace_build /
+ * ace_build_async / ace_build_finish / ace_load on the plan or the next
+ * ace_apply_prepare; a caller that changes xi's contents by other means must
+ * call ace_apply_prepare again.  ACE_FP64 plans and plans with the CUDA-core
+ * Gram (ace_opts.kernels = 1) have nothing to prepare and return ACE_OK.
+ *   xi [n_occ][n_pw_half] device (read on `stream`).
+ */
+int ace_apply_prepare(ace_plan* plan, const void* xi, int n_occ, void* stream);
+
+/*
  * The fast energy of an inner MTS step (Section 2.3, Eq. 6-7, with the
  * operator of Eq. 5): E = sum_t <psi_t| K psi_t> = -sum_{t,k} <xi_k|psi_t>^2,
  * from the Gram C = xi^T psi of the apply (no K psi is formed), reduced in

@@ -25,7 +25,7 @@ SYMBOLS = ("ace_plan_create", "ace_plan_destroy", "ace_gvec", "ace_build", "ace_
            "ace_last_intermediates", "ace_set_timing", "ace_get_stats", "ace_last_error", "ace_apply_noalloc",
            "ace_build_batched", "ace_save", "ace_load", "ace_build_pairs", "ace_build_finish",
            "ace_plan_config", "ace_overlap_screen", "ace_build_async", "ace_build_result",
-           "ace_check_timeout_path", "ace_scdm", "ace_apply_energy", "ace_plan_tuning", "ace_plan_radix")
+           "ace_check_timeout_path", "ace_scdm", "ace_apply_energy", "ace_plan_tuning", "ace_plan_radix", "ace_apply_prepare")
 
 _lib = None
 
@@ -90,6 +90,7 @@ def load(build_if_missing=False):
     lib.ace_plan_tuning.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)]
     lib.ace_plan_radix.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(ctypes.c_float)]
+    lib.ace_apply_prepare.argtypes = [P, ctypes.c_void_p, i32, ctypes.c_void_p]
     lib.ace_scdm.argtypes = [P, P, i32, i32, P, P, ctypes.POINTER(i32), P, P]
     lib.ace_apply_noalloc.argtypes = [P, i32, P, i32, i32, i32, P, P]
     lib.hfx_apply_exact.argtypes = [P, P, i32, f64, P, i32, P, P]
@@ -380,6 +381,14 @@ def ace_apply(plan, xi, psi, out=None, stream=None):
     _check(load().ace_apply(plan.handle, _ptr(xi), xi.shape[0], _ptr(psi), psi.shape[0], _ptr(out),
                             _stream(stream)))
     return out
+
+
+def ace_apply_prepare(plan, xi, stream=None):
+    """Make the plan's split copy of xi for the inner steps that follow
+    (ace_apply_prepare): later ace_apply calls with this xi read it until the
+    next build, load or prepare on the plan."""
+    plan._vec(xi, "xi")
+    _check(load().ace_apply_prepare(plan.handle, _ptr(xi), xi.shape[0], _stream(stream)))
 
 
 def ace_apply_energy(plan, xi, psi, stream=None):

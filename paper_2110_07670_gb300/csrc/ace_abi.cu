@@ -134,6 +134,10 @@ struct ace_plan {
     float tune_rb_ms[4] = {0, 0, 0, 0};  // autotune of the chosen variant's row block: row order, 2, 4, 8 rows
     int tune_cached = 0;                 // 1: the choice came from the tune cache (ACE_TUNE_CACHE)
     int pair_r0 = 0;                     // first radix of the pair passes' plan on every axis (0: make_axis_plan's)
+    float* d_ximg = nullptr;             // split image of a prepared xi (ace_apply_prepare), xi_image_floats
+    size_t ximg_cap = 0;
+    mutable const void* ximg_src = nullptr;  // the xi it was made from (null: none; builds and loads clear it)
+    int ximg_n = 0;
     int r0_cand[4] = {0, 0, 0, 0};       // the first radices the autotuner timed (0: make_axis_plan's)
     float tune_r0_ms[4] = {0, 0, 0, 0};  // the best pair-pass time of each
     int n_r0_cand = 1;
@@ -763,6 +767,7 @@ int pairs_enqueue(ace_plan* P, const void* psi_G, int n_occ, double alpha, const
 // host slot.
 template <typename R>
 int finish_enqueue(ace_plan* P, const void* psi_G, int n_occ, const void* WG_in, void* xi, cudaStream_t st) {
+    P->ximg_src = nullptr;  // a prepared image may be of the xi this build overwrites
     const cx<R>* psi = (const cx<R>*)psi_G;
     const cx<R>* WG = (const cx<R>*)WG_in;
     ACE_TRY(gram<R>(P, psi, n_occ, WG, n_occ, P->d_M, st));
@@ -1046,8 +1051,10 @@ int apply_impl(ace_plan* P, const void* xi, int n_occ, const void* psi, int T, v
     if constexpr (sizeof(R) == 4) {
         if (P->tensor_gram) {  // -xi C on the tensor cores
             ACE_TRY(grow(&P->d_csplit, &P->csplit_cap, apply_product_scratch(T, n_occ)));
+            // xi's split image, when ace_apply_prepare made one of this xi
+            const float* ximg = P->ximg_src == xi && P->ximg_n == n_occ ? P->d_ximg : nullptr;
             ACE_CKL(launch_apply_product(P->d_C, T, n_occ, (const float*)xi, 2LL * P->npw, P->d_csplit, (float*)out,
-                                         P->sms, P->d_err, st));
+                                         P->sms, P->d_err, st, ximg));
             mark(P, PH_IDLE, st);
             return ACE_OK;
         }
@@ -1085,7 +1092,7 @@ void free_plan(ace_plan* P) {
     if (P->fork_ev) cudaEventDestroy(P->fork_ev);
     void* ptrs[] = {P->d_ip, P->d_in, P->d_tw[0], P->d_tw[1], P->d_tw[2], P->d_freq[0], P->d_freq[1], P->d_freq[2], P->d_phi, P->d_acc, P->d_spec,
                     P->d_WG, P->d_M, P->d_S, P->d_L, P->d_Linv, P->d_chol, P->d_E, P->d_status, P->d_err, P->d_part, P->d_quads,
-                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_kern_t, P->d_kern_r, P->d_pipe, P->d_csplit,
+                    P->d_epart, P->d_tphi, P->d_tacc, P->d_C, P->d_kern, P->d_kern_t, P->d_kern_r, P->d_pipe, P->d_csplit, P->d_ximg,
                     P->scdm.gv, P->scdm.dpsi, P->scdm.dens, P->scdm.isel, P->scdm.A, P->scdm.nu,
                     P->scdm.part, P->scdm.mats, P->scdm.ipiv};
     for (void* p : ptrs)
@@ -1671,6 +1678,29 @@ int ace_apply(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T,
     return rc;
 }
 
+int ace_apply_prepare(ace_plan* plan, const void* xi, int n_occ, void* stream) {
+    if (!plan || !xi) return fail(ACE_ERR_INVALID_ARG, "null argument");
+    if (n_occ < 1) return fail(ACE_ERR_INVALID_ARG, "n_occ must be >= 1");
+    plan->ximg_src = nullptr;
+    if (plan->prec == ACE_FP64 || !plan->tensor_gram) return ACE_OK;  // nothing to prepare: the product is not split
+    DeviceGuard g(plan->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    g_capture = capturing(st);
+    const long long K = 2LL * plan->npw;
+    int rc = grow(&plan->d_ximg, &plan->ximg_cap, xi_image_floats(n_occ, K));
+    if (rc == ACE_OK) {
+        const cudaError_t e = launch_xi_image((const float*)xi, n_occ, K, plan->d_ximg, st);
+        ++plan->launches;
+        rc = e == cudaSuccess ? ACE_OK : fail(ACE_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    }
+    g_capture = false;
+    if (rc == ACE_OK) {
+        plan->ximg_src = xi;
+        plan->ximg_n = n_occ;
+    }
+    return rc;
+}
+
 int ace_apply_energy(ace_plan* plan, const void* xi, int n_occ, const void* psi, int T, double* E, void* stream) {
     if (!plan || !xi || !E || (T > 0 && !psi)) return fail(ACE_ERR_INVALID_ARG, "null argument");
     if (n_occ < 1 || T < 0) return fail(ACE_ERR_INVALID_ARG, "n_occ must be >= 1 and T >= 0");
@@ -1809,6 +1839,7 @@ int ace_save(const char* path, const ace_plan* plan, const void* xi, int n_occ, 
 
 int ace_load(const char* path, const ace_plan* plan, void* xi, int* n_occ, double* alpha, double* E_x, void* stream) {
     if (!path || !plan || !xi || !n_occ) return fail(ACE_ERR_INVALID_ARG, "ace_load: invalid arguments");
+    plan->ximg_src = nullptr;  // xi's contents change
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(ACE_ERR_INVALID_ARG, std::string("ace_load: cannot open ") + path);
     SaveHeader h;

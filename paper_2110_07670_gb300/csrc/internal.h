@@ -216,9 +216,15 @@ cudaError_t launch_gram_stream(const float* A, const float* B, int m, int n, lon
 // out[t][j] = -sum_k C[t][k] xi[k][j] on tcgen05 (K psi = -xi C^T, Eq. 5):
 // C [T][n] double, xi [n][K] float, out [T][K] float; Cimg: scratch of
 // apply_product_scratch(T, n) floats (16-byte aligned) for C's TF32 split.
+// Ximg (or null): xi's split image from launch_xi_image, which feeds xi to the
+// tensor cores by bulk copies instead of the producer warps.
 size_t apply_product_scratch(int T, int n);
 cudaError_t launch_apply_product(const double* C, int T, int n, const float* xi, long long K, float* Cimg, float* out,
-                                 int sms, int* err, cudaStream_t st);
+                                 int sms, int* err, cudaStream_t st, const float* Ximg = nullptr);
+// xi [n][K] float -> Ximg: xi_image_floats(n, K) floats (16-byte aligned), the
+// TF32 hi / lo split of xi^T in the product's swizzled operand tiles.
+size_t xi_image_floats(int n, long long K);
+cudaError_t launch_xi_image(const float* xi, int n, long long K, float* Ximg, cudaStream_t st);
 // The same on CUDA cores with double partials over nchunk K-slices.
 template <typename R>
 cudaError_t launch_overlap_partial(const R* A, int m, long long K, int nchunk, double* P, cudaStream_t st);

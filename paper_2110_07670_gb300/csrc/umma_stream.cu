@@ -298,9 +298,13 @@ __global__ void __launch_bounds__(NTHR, 1)
 // copy per half fills a stage's B operand.  Producer thread p owns, in every
 // stage, xi[k0 + 4 u + (p / 8) % 4][j0 + 16 (p / 32) + 2 (p % 8) + {0, 1}]
 // (u = 0..7: a warp covers 4 rows of 16 reals).
+// IMG: xi comes as Ximg, its TF32 hi / lo images per 128-real tile and stage
+// (xi_image_kernel), and thread 0 fills both operands of a stage with four
+// bulk copies; the other producer warps have nothing to do.
+template <bool IMG>
 __global__ void __launch_bounds__(NTHR, 1)
     apply_product(const float* __restrict__ xi, int n, long long K, const float* __restrict__ Cimg, int nks, int T,
-                  float* __restrict__ out, int* err) {
+                  float* __restrict__ out, int* err, const float* __restrict__ Ximg) {
     WsSmem& sm = ws_smem();
     const int warp = threadIdx.x >> 5;
     const int ntb = (T + 127) / 128;
@@ -309,10 +313,29 @@ __global__ void __launch_bounds__(NTHR, 1)
     const int G = gridDim.x;
     const int my_tiles = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
     const long long S = (long long)my_tiles * nks;
-    ws_init(sm, NPROD + 1);
+    ws_init(sm, IMG ? 1 : NPROD + 1);
     const uint32_t tmem = sm.tmem_base;
 
-    if (warp < NPROD) {
+    if (IMG && warp < NPROD) {
+        if (threadIdx.x == 0) {
+            int tile = blockIdx.x, ks = 0;
+            for (long long g = 0; g < S; ++g) {
+                const int b = (int)(g % NB);
+                if (g >= NB && !ws_wait(sm, &sm.empty[b], g / NB - 1, err)) break;
+                const float* a_src = Ximg + ((long long)((tile / ntb) * nks + ks) * 2) * (128 * TK);
+                const float* b_src = Cimg + ((long long)((tile % ntb) * nks + ks) * 2) * (128 * TK);
+                mbar_arrive_expect_tx(&sm.full[b], 4 * 128 * TK * 4);
+                bulk_load(sm.a_hi[b], a_src, 128 * TK * 4, &sm.full[b]);
+                bulk_load(sm.a_lo[b], a_src + 128 * TK, 128 * TK * 4, &sm.full[b]);
+                bulk_load(sm.b_hi[b], b_src, 128 * TK * 4, &sm.full[b]);
+                bulk_load(sm.b_lo[b], b_src + 128 * TK, 128 * TK * 4, &sm.full[b]);
+                if (++ks == nks) {
+                    ks = 0;
+                    tile += G;
+                }
+            }
+        }
+    } else if (warp < NPROD) {
         const int p = threadIdx.x;
         const int kq = (p >> 3) & 3, jt = (p >> 5) * 16 + (p & 7) * 2;
         const uint32_t o0 = (uint32_t)(jt * 128 + 4 * kq), o1 = o0 + 128;  // rows jt, jt + 1; + ((u ^ row % 8) << 4)
@@ -453,6 +476,35 @@ __global__ void split_c_kernel(const double* __restrict__ C, int T, int n, int n
     img[128 * TK + o] = l;
 }
 
+// Ximg[jt][ks][hi, lo][128 x TK swizzled]: the TF32 split of xi^T's tile of
+// reals jt * 128 .. + 127 and ACE vectors ks * TK .. + TK - 1, in the K-major
+// 128-byte swizzle layout the product's A operand takes (zero past K and n).
+// Thread e: one real (row, fastest, so a warp reads 32 consecutive reals of
+// one vector) and 4 consecutive vectors, written as one 16-byte chunk.
+__global__ void xi_image_kernel(const float* __restrict__ xi, int n, long long K, int nks, float* __restrict__ Ximg) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long ntile = (K + 127) / 128;
+    if (e >= ntile * nks * 128 * (TK / 4)) return;
+    const int row = (int)(e % 128), kq = (int)((e / 128) % (TK / 4));
+    const long long blk = e / (128 * (TK / 4));
+    const int ks = (int)(blk % nks);
+    const long long j = (blk / nks) * 128 + row;
+    float h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int k = ks * TK + 4 * kq + i;
+        const float x = (k < n && j < K) ? __ldg(xi + (long long)k * K + j) : 0.f;
+        uint32_t hx, lx;
+        umma::split_tf32(x, hx, lx);
+        h[i] = __uint_as_float(hx);
+        l[i] = __uint_as_float(lx);
+    }
+    float* img = Ximg + blk * 2 * (128 * TK);
+    const uint32_t o = umma::sw128_offset(row, 4 * kq) / 4;
+    *reinterpret_cast<float4*>(img + o) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(img + 128 * TK + o) = make_float4(l[0], l[1], l[2], l[3]);
+}
+
 cudaError_t set_smem(const void* k, cudaStream_t st) {
     if (stream_capturing(st)) return cudaSuccess;  // set by the same launch outside capture before
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(WsSmem) + 1024));
@@ -487,18 +539,35 @@ size_t apply_product_scratch(int T, int n) {
     return (size_t)((T + 127) / 128) * ((n + TK - 1) / TK) * 2 * 128 * TK;
 }
 
+size_t xi_image_floats(int n, long long K) {
+    return (size_t)((K + 127) / 128) * ((n + TK - 1) / TK) * 2 * 128 * TK;
+}
+
+cudaError_t launch_xi_image(const float* xi, int n, long long K, float* Ximg, cudaStream_t st) {
+    if (((uintptr_t)Ximg % 16) || n < 1 || K < 1) return cudaErrorInvalidValue;
+    const int nks = (n + TK - 1) / TK;
+    const long long tot = (K + 127) / 128 * nks * 128 * (TK / 4);
+    xi_image_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(xi, n, K, nks, Ximg);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_apply_product(const double* C, int T, int n, const float* xi, long long K, float* Cimg, float* out,
-                                 int sms, int* err, cudaStream_t st) {
-    if (K % 2 != 0 || ((uintptr_t)xi % 8) || ((uintptr_t)out % 8) || ((uintptr_t)Cimg % 16))
+                                 int sms, int* err, cudaStream_t st, const float* Ximg) {
+    if (K % 2 != 0 || ((uintptr_t)xi % 8) || ((uintptr_t)out % 8) || ((uintptr_t)Cimg % 16) ||
+        ((uintptr_t)Ximg % 16))
         return cudaErrorInvalidValue;
     const int nks = (n + TK - 1) / TK;
     const long long tot = (long long)((T + 127) / 128) * nks * 128 * TK;
     split_c_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(C, T, n, nks, Cimg);
-    cudaError_t e = set_smem((const void*)apply_product, st);
+    const void* k = Ximg ? (const void*)apply_product<true> : (const void*)apply_product<false>;
+    cudaError_t e = set_smem(k, st);
     if (e != cudaSuccess) return e;
     const long long ntiles = ((K + 127) / 128) * ((T + 127) / 128);
     const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(ntiles, sms));
-    apply_product<<<grid, NTHR, sizeof(WsSmem) + 1024, st>>>(xi, n, K, Cimg, nks, T, out, err);
+    if (Ximg)
+        apply_product<true><<<grid, NTHR, sizeof(WsSmem) + 1024, st>>>(xi, n, K, Cimg, nks, T, out, err, Ximg);
+    else
+        apply_product<false><<<grid, NTHR, sizeof(WsSmem) + 1024, st>>>(xi, n, K, Cimg, nks, T, out, err, nullptr);
     return cudaGetLastError();
 }
 

@@ -308,10 +308,47 @@ def test_tensor_core_apply_ragged_shapes(n, T):
     xh, th = host(d_xi), host(d_tr)  # the float inputs, exactly
     C = gen.gamma_overlap(th, xh)
     ref = -(C @ xh)
-    K = host(ace.ace_apply(plan, d_xi, d_tr))
+    K0 = ace.ace_apply(plan, d_xi, d_tr)
+    K = host(K0)
     assert rel(K, ref) <= 1e-6
     E = ace.ace_apply_energy(plan, d_xi, d_tr)
     assert abs(E + np.sum(C * C)) <= 1e-6 * np.sum(C * C)
+    # with xi's split image (ace_apply_prepare) the product takes xi by bulk
+    # copies: the same hi / lo operands in the same order, so the same bits
+    ace.ace_apply_prepare(plan, d_xi)
+    assert torch.equal(ace.ace_apply(plan, d_xi, d_tr), K0)
+    plan.close()
+
+
+def test_apply_prepare_lifetime():
+    """The split image of xi serves only the xi it was made from: a build
+    clears it, another xi pointer or count does not use it, a new prepare
+    after xi changes in place gives that xi's product; each against the FP64
+    evaluation of -xi (xi^T psi) on the float inputs."""
+    s = gen.config_small()
+    n = len(s["psi"])
+    plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "mixed")
+    tr = dev(gen.random_trials(s["cell"], s["ecut"], 9, seed=5), plan)
+    th = host(tr)
+
+    def ref(x):
+        xh = host(x)
+        return -(gen.gamma_overlap(th, xh) @ xh)
+
+    xi, _ = ace.ace_build(plan, dev(s["psi"], plan), s["alpha"])
+    ace.ace_apply_prepare(plan, xi)
+    assert rel(host(ace.ace_apply(plan, xi, tr)), ref(xi)) <= 1e-6
+    other = xi.clone().mul_(0.25)  # another pointer, same count, other contents
+    assert rel(host(ace.ace_apply(plan, other, tr)), ref(other)) <= 1e-6
+    assert rel(host(ace.ace_apply(plan, xi[:5], tr)), ref(xi[:5])) <= 1e-6  # same pointer, fewer vectors
+    xi2 = xi.clone()
+    xi.mul_(0.5)  # in place: the image is stale until prepared again
+    ace.ace_apply_prepare(plan, xi)
+    assert rel(host(ace.ace_apply(plan, xi, tr)), ref(xi)) <= 1e-6
+    ace.ace_apply_prepare(plan, xi2)
+    xi3, _ = ace.ace_build(plan, dev(s["psi"], plan), s["alpha"], xi=xi2)  # the build clears the image
+    xi3.mul_(2.0)
+    assert rel(host(ace.ace_apply(plan, xi3, tr)), ref(xi3)) <= 1e-6
     plan.close()
 
 
