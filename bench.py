@@ -423,7 +423,8 @@ def run_ours(args):
     kcfg = plan.config()
     variant, streams = kcfg["pair_variant"], kcfg["pair_streams"]
     vname = {1: "tile passes", 2: "transposed-plane passes", 3: "persistent pipeline kernel",
-             4: "plane-kernel forward pass, tile passes after it"}[variant]
+             4: "plane-kernel forward pass, tile passes after it",
+             5: "plane passes on clusters of two half-plane blocks"}[variant]
     group = 32 if (variant != 3 and streams == 2) else 64  # transforms per launch (algorithmic count)
     pbg, _ = pass_bytes(n, N, batch=group)
     pipe_bytes = sum(pbg.values())  # per build, counted per launch (orbital reads and W updates included)
@@ -459,7 +460,7 @@ def run_ours(args):
         pb64, nl64 = pass_bytes(n, N, batch=64)
         per_pass = {}
         per_pass["variant"] = {1: "tile passes", 2: "transposed-plane passes", 3: "tile passes",
-                               4: "hybrid"}[variant]
+                               4: "hybrid", 5: "half-plane pairs"}[variant]
         for k in ("pair_fwd", "pair_coulomb", "pair_inv"):
             ms = st1[k + "_ms"] / 2
             per_pass[k] = {"ms_per_build": ms, "launches_per_build": nl64,

@@ -78,9 +78,11 @@ typedef struct {
                           1 = every pass in order on the call's stream */
     int pair_variant;  /* kernels of the pair passes (Eq. 2-4): 1 tile passes, 2 transposed-
                           plane passes, 3 one persistent kernel for all three passes, 4 the
-                          plane-kernel forward pass with the tile passes after it (2 and 3:
-                          single precision, n^3 boxes with n in {32, 80, 96, 160}; 4: single
-                          precision, n in {32, 60, 80, 90, 96, 100, 108, 120, 160});
+                          plane-kernel forward pass with the tile passes after it, 5 the
+                          plane passes on clusters of two blocks holding half a plane each
+                          (2 and 3: single precision, n^3 boxes with n in {32, 80, 96, 160};
+                          4: single precision, n in {32, 60, 80, 90, 96, 100, 108, 120, 160};
+                          5: single precision, n = 120);
                           0 = automatic: where several apply (and pair_streams is 0, both 1
                           and 2 streams) they are timed at plan creation on the plan's own
                           buffers and the fastest is kept (see ace_plan_config) */
@@ -114,10 +116,11 @@ int ace_plan_create(ace_plan** plan, const int grid[3], const double cell[9], do
 
 void ace_plan_destroy(ace_plan* plan);
 
-/* The plan's pair-pass kernels: pair_variant (1 to 4 as in ace_opts),
- * pair_streams, and, where plan creation timed them, tune_ms[5] = ms per
+/* The plan's pair-pass kernels: pair_variant (1 to 5 as in ace_opts),
+ * pair_streams, and, where plan creation timed them, tune_ms[6] = ms per
  * timing run of {tile passes on 1 stream, on 2 streams, transposed-plane
- * passes, persistent kernel, hybrid} (0 = not timed).  Any output may be NULL. */
+ * passes, persistent kernel, hybrid, half-plane pairs} (0 = not timed).  Any
+ * output may be NULL. */
 int ace_plan_config(const ace_plan* plan, int* pair_variant, int* pair_streams, float* tune_ms);
 
 /* The pair-tile shape of the plan's pair passes: row_block = 0 packs

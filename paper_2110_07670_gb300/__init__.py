@@ -178,11 +178,11 @@ class Plan:
 
     def config(self):
         """dict(pair_variant, pair_streams, row_block, tune_ms, ...) of the pair-pass
-        kernels (1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid)
+        kernels (1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid, 5 half-plane pairs)
         the pair-tile shape (ace_plan_tuning) and the pair passes' FFT radix plan
         (ace_plan_radix: first radix of every axis, and the candidates timed)."""
         v, st = ctypes.c_int(0), ctypes.c_int(0)
-        tm = (ctypes.c_float * 5)()
+        tm = (ctypes.c_float * 6)()
         _check(load().ace_plan_config(self.handle, ctypes.byref(v), ctypes.byref(st), tm))
         rb, cached = ctypes.c_int(0), ctypes.c_int(0)
         rbm = (ctypes.c_float * 4)()
@@ -196,7 +196,7 @@ class Plan:
                              for k in range(nc.value) if rms[k] > 0},
                 "from_tune_cache": bool(cached.value),
                 "tune_ms": {k: round(float(x), 3) for k, x in
-                            zip(("tile_1_stream", "tile_2_streams", "planes", "pipeline", "hybrid"), tm)
+                            zip(("tile_1_stream", "tile_2_streams", "planes", "pipeline", "hybrid", "half_planes"), tm)
                             if x > 0},
                 "row_block_ms": {k: round(float(x), 3) for k, x in zip(("rows", "2", "4", "8"), rbm) if x > 0}}
 

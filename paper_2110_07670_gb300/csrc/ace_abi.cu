@@ -130,7 +130,9 @@ struct ace_plan {
     } scdm;
     int variant = 1;           // pair passes: 1 tile, 2 transposed planes, 3 persistent pipeline, 4 hybrid
     bool hybrid = false;       // variant 4: plane-kernel P1 in the tile layout, then the tile P2 / P3
-    float tune_ms[5] = {0, 0, 0, 0, 0};  // autotune: tile x1 stream, tile x2, planes x2, pipeline, hybrid x2
+    bool half = false;         // variant 5: P1 / P3 on clusters of two half-plane blocks (halfplane.cuh)
+    float tune_ms[6] = {0, 0, 0, 0, 0, 0};  // autotune: tile x1 stream, tile x2, planes x2, pipeline, hybrid x2,
+                                          // half planes x2
     float tune_rb_ms[4] = {0, 0, 0, 0};  // autotune of the chosen variant's row block: row order, 2, 4, 8 rows
     int tune_cached = 0;                 // 1: the choice came from the tune cache (ACE_TUNE_CACHE)
     int pair_r0 = 0;                     // first radix of the pair passes' plan on every axis (0: make_axis_plan's)
@@ -158,6 +160,7 @@ struct ace_plan {
     cudaEvent_t fork_ev = nullptr;
     PassShape s_xy{}, s_x{}, s_y{}, s_z{};
     int ntiles_last = 1;  // tiles of the pass that accumulates W
+    int ntiles_xy = 1;    // ... with the tile or plane passes (2 n for the half-plane pairs)
     int batch = 1;
     size_t esz = 8;  // bytes of one real
     void* d_phi = nullptr;
@@ -314,7 +317,7 @@ int setup_shapes(ace_plan* P) {
         P->s_xy.cube = P->s_z.cube = 1;
         if (P->s_xy.smem > (size_t)smax || P->s_z.smem > (size_t)smax)
             return fail(ACE_ERR_GRID_TOO_SMALL, "plane tile exceeds shared memory");
-        P->ntiles_last = n;
+        P->ntiles_last = P->ntiles_xy = n;
         return ACE_OK;
     }
     P->fused_xy = (size_t)(plane + n1 + n2) * c <= (size_t)std::min(smax, 160 * 1024);
@@ -334,7 +337,7 @@ int setup_shapes(ace_plan* P) {
         if (s == &P->s_xy && !P->fused_xy) continue;
         if (s->smem > (size_t)smax) return fail(ACE_ERR_GRID_TOO_SMALL, "grid axis too long for one thread block tile");
     }
-    P->ntiles_last = P->fused_xy ? n0 : n0 * (n1 / P->s_x.ty);
+    P->ntiles_last = P->ntiles_xy = P->fused_xy ? n0 : n0 * (n1 / P->s_x.ty);
     return ACE_OK;
 }
 
@@ -431,6 +434,12 @@ int pair_batch(ace_plan* P, PassArgs& a, int nb, cudaStream_t st, int lane) {
         ACE_CKL(zline_coulomb_launch(P->n[0], a, nb, st));
         mark(P, PH_PINV, st, lane);
         ACE_CKL(tplane_pair_launch(P->n[0], 1, a, nb, st));
+    } else if (P->half) {
+        ACE_CKL(halfplane_pair_launch(P->n[0], 0, a, nb, st));
+        mark(P, PH_PCOUL, st, lane);
+        ACE_CKL(zline_coulomb_launch(P->n[0], a, nb, st));
+        mark(P, PH_PINV, st, lane);
+        ACE_CKL(halfplane_pair_launch(P->n[0], 1, a, nb, st));
     } else if (P->hybrid) {
         ACE_CKL(tplane_pair_launch(P->n[0], 2, a, nb, st));
         mark(P, PH_PCOUL, st, lane);
@@ -1105,6 +1114,8 @@ void set_variant(ace_plan* P, int v, int streams) {
     P->tplane = v == 2 || v == 3;
     P->fused = v == 3;
     P->hybrid = v == 4;
+    P->half = v == 5;
+    P->ntiles_last = v == 5 ? 2 * P->n[0] : P->ntiles_xy;  // one energy partial per half-plane block
     P->pair_streams = streams;
 }
 
@@ -1142,7 +1153,10 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     const int fixed_streams = opts && opts->pair_streams > 0 ? opts->pair_streams : 0;
     const bool t_ok = sizeof(R) == 4 && P->zline && P->d_kern_t != nullptr;
     const bool h_ok = sizeof(R) == 4 && P->zline;  // every compile-time cube
-    if (req < 0 || req > 4) return fail(ACE_ERR_INVALID_ARG, "pair_variant must be 0 (automatic), 1, 2, 3 or 4");
+    const bool c_ok = h_ok && halfplane_supported(P->n[0]);
+    if (req < 0 || req > 5) return fail(ACE_ERR_INVALID_ARG, "pair_variant must be 0 (automatic), 1, 2, 3, 4 or 5");
+    if (req == 5 && !c_ok)
+        return fail(ACE_ERR_INVALID_ARG, "pair_variant 5 needs a single-precision 120^3 plan");
     if ((req == 2 || req == 3) && !t_ok)
         return fail(ACE_ERR_INVALID_ARG,
                     "pair_variant 2 and 3 need a single-precision n^3 plan with n in {32, 80, 96, 160}");
@@ -1164,6 +1178,7 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
         cand.push_back({3, 1, 3});
     }
     if (h_ok) cand.push_back({4, fixed_streams ? fixed_streams : 2, 4});
+    if (c_ok) cand.push_back({5, fixed_streams ? fixed_streams : 2, 5});
     if (sizeof(R) != 4 || cand.size() == 1) {  // double plans: no timing, the two-stream tile passes
         set_variant(P, 1, fixed_streams ? fixed_streams : 2);
         return ACE_OK;
@@ -1193,8 +1208,8 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
                                     : 0;
                 bool r_ok = false;  // the radix plan (a fourth field; 0 when absent) is one of this plan's
                 for (int k = 0; k < nr0; ++k) r_ok = r_ok || r0s[k] == r2;
-                if ((got == 3 || got == 4) && v2 >= 1 && v2 <= 4 && s2 >= 1 && s2 <= 8 && rb2 >= 0 && rb2 <= 64 &&
-                    (v2 != 2 && v2 != 3 ? true : t_ok) && (v2 != 4 || h_ok) && r_ok) {
+                if ((got == 3 || got == 4) && v2 >= 1 && v2 <= 5 && s2 >= 1 && s2 <= 8 && rb2 >= 0 && rb2 <= 64 &&
+                    (v2 != 2 && v2 != 3 ? true : t_ok) && (v2 != 4 || h_ok) && (v2 != 5 || c_ok) && r_ok) {
                     v = v2;  // the last matching line wins
                     st = s2;
                     rb = rb2;
@@ -1262,7 +1277,7 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     int rc = ACE_OK;
     float best = 1e30f;
     int best_v = 1, best_s = 2, best_rb = P->row_block, best_r0 = P->pair_r0;
-    float var_ms[4][5] = {};  // per radix plan and variant slot
+    float var_ms[4][6] = {};  // per radix plan and variant slot
     do {
         if (cudaMemsetAsync(P->d_phi, 0, (size_t)n * P->N * sizeof(R), ts) != cudaSuccess ||
             cudaMemsetAsync(P->d_acc, 0, (size_t)n * P->N * sizeof(R), ts) != cudaSuccess) {
@@ -1292,7 +1307,7 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
         if (rc != ACE_OK) break;
         for (int k = 0; k < nr0; ++k)
             if (r0s[k] == best_r0)
-                for (int v = 0; v < 5; ++v) P->tune_ms[v] = var_ms[k][v];
+                for (int v = 0; v < 6; ++v) P->tune_ms[v] = var_ms[k][v];
         if (best_r0 != P->pair_r0 && (rc = pair_tables<R>(P, best_r0)) != ACE_OK) break;
         // then the pair-tile shape of the chosen kernels: row order, or column-
         // shared transforms in blocks of 2, 4 or 8 rows (pack_pairs_blocked)
@@ -1906,7 +1921,7 @@ int ace_plan_config(const ace_plan* plan, int* pair_variant, int* pair_streams, 
     if (pair_variant) *pair_variant = plan->variant;
     if (pair_streams) *pair_streams = plan->variant == 3 ? 1 : plan->pair_streams;
     if (tune_ms)
-        for (int i = 0; i < 5; ++i) tune_ms[i] = plan->tune_ms[i];
+        for (int i = 0; i < 6; ++i) tune_ms[i] = plan->tune_ms[i];
     return ACE_OK;
 }
 

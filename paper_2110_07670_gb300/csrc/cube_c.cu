@@ -3,6 +3,7 @@
 #include "pipeline.cuh"
 #include "plane.cuh"
 #include "zline.cuh"
+#include "halfplane.cuh"
 
 namespace ace {
 
@@ -20,5 +21,6 @@ template cudaError_t tplane_launch<160>(int, const PassArgs&, int, cudaStream_t)
 template cudaError_t pipeline_launch<160>(const PassArgs&, const PipeArgs&, cudaStream_t);
 template cudaError_t tplane_launch<108>(int, const PassArgs&, int, cudaStream_t);
 template cudaError_t tplane_launch<120>(int, const PassArgs&, int, cudaStream_t);
+template cudaError_t halfplane_launch<120>(int, const PassArgs&, int, cudaStream_t);
 
 }  // namespace ace

@@ -3,6 +3,7 @@
 #include "pipeline.cuh"
 #include "plane.cuh"
 #include "zline.cuh"
+#include "halfplane.cuh"
 
 namespace ace {
 
@@ -139,6 +140,19 @@ cudaError_t pipeline_pair_launch(int n, const PassArgs& a, const PipeArgs& p, cu
         case 80: return pipeline_launch<80>(a, p, st);
         case 96: return pipeline_launch<96>(a, p, st);
         case 160: return pipeline_launch<160>(a, p, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+extern template cudaError_t halfplane_launch<120>(int, const PassArgs&, int, cudaStream_t);
+extern template cudaError_t halfplane_launch<120, 10>(int, const PassArgs&, int, cudaStream_t);
+extern template cudaError_t halfplane_launch<120, 8>(int, const PassArgs&, int, cudaStream_t);
+
+cudaError_t halfplane_pair_launch(int n, int which, const PassArgs& a, int batch, cudaStream_t st) {
+    switch (alt_key(n, a.r0)) {
+        case alt_key(120, 0): return halfplane_launch<120>(which, a, batch, st);
+        case alt_key(120, 10): return halfplane_launch<120, 10>(which, a, batch, st);
+        case alt_key(120, 8): return halfplane_launch<120, 8>(which, a, batch, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -4,6 +4,7 @@
 #include "pipeline.cuh"
 #include "plane.cuh"
 #include "zline.cuh"
+#include "halfplane.cuh"
 
 namespace ace {
 
@@ -11,9 +12,11 @@ template cudaError_t pass_detail::dispatch_cube<120, 10>(const PassArgs&, const 
                                                     int, cudaStream_t);
 template cudaError_t zline_launch<120, 10>(const PassArgs&, int, cudaStream_t);
 template cudaError_t tplane_launch<120, 10>(int, const PassArgs&, int, cudaStream_t);
+template cudaError_t halfplane_launch<120, 10>(int, const PassArgs&, int, cudaStream_t);
 template cudaError_t pass_detail::dispatch_cube<120, 8>(const PassArgs&, const PassShape&, int, int, int, int,
                                                     int, cudaStream_t);
 template cudaError_t zline_launch<120, 8>(const PassArgs&, int, cudaStream_t);
 template cudaError_t tplane_launch<120, 8>(int, const PassArgs&, int, cudaStream_t);
+template cudaError_t halfplane_launch<120, 8>(int, const PassArgs&, int, cudaStream_t);
 
 }  // namespace ace

@@ -134,6 +134,10 @@ inline int pair_radix_alternatives(int n, int* r0) {
 // N % 16 == 0: which = 0 pair product + forward, 1 inverse + exchange accumulation
 constexpr bool tplane_supported(int n) { return n % 16 == 0; }
 cudaError_t tplane_pair_launch(int n, int which, const PassArgs& a, int batch, cudaStream_t st);
+// plane passes on clusters of two half-plane blocks (halfplane.cuh): which =
+// 0 pair product + forward, 1 inverse + exchange accumulation; n = 120
+constexpr bool halfplane_supported(int n) { return n == 120; }
+cudaError_t halfplane_pair_launch(int n, int which, const PassArgs& a, int batch, cudaStream_t st);
 // the three pair passes as one persistent kernel (pipeline.cuh), same boxes
 struct PipeArgs {
     int ntrans;       // packed transforms: quads a.t0 .. a.t0 + ntrans - 1

@@ -68,7 +68,7 @@ def system(n):
 # (one plan) for its own rotation of the plane swizzle
 CASES = [(80, 10, v) for v in (1, 2, 3, 4)] + \
         [(96, r, v) for r in (12, 8, 16) for v in (1, 2, 3, 4)] + \
-        [(120, r, v) for r in (12, 10, 8) for v in (1, 4)] + \
+        [(120, r, v) for r in (12, 10, 8) for v in (1, 4, 5)] + \
         [(160, r, v) for r in (16, 10) for v in (1, 2, 3, 4)]
 
 
