@@ -61,7 +61,14 @@ def qrcp_pivots(A, k):
     (rows x columns), each step taking the column of largest trailing norm.
     Rank deficient (ValueError) when that norm^2 is not above 1e-10 times the
     largest column norm^2 of A: fewer than k independent columns beyond
-    rounding."""
+    rounding.  Where 1e-10 comes from: columns that are dependent in exact
+    arithmetic keep a trailing norm^2 at the level of their inputs' rounding,
+    (m u)^2 of the largest for m <= 2048 rows -- about 1e-14 for orbitals
+    stored in single precision (u = 2^-24 once each value is rounded), 1e-26
+    for double; a column whose independent part is above 1e-5 of the largest
+    column (norm^2 above 1e-10) is resolved by any of the FP64 or float-float
+    evaluations (relative error 2^-44 or below) without ambiguity.  1e-10 sits
+    four orders above the first level and leaves the second untouched."""
     R = np.array(A, dtype=np.float64)
     nr, nc = R.shape
     perm = np.arange(nc)
