@@ -63,12 +63,12 @@ def qrcp_pivots(A, k):
     largest column norm^2 of A: fewer than k independent columns beyond
     rounding.  Where 1e-10 comes from: columns that are dependent in exact
     arithmetic keep a trailing norm^2 at the level of their inputs' rounding,
-    (m u)^2 of the largest for m <= 2048 rows -- about 1e-14 for orbitals
-    stored in single precision (u = 2^-24 once each value is rounded), 1e-26
-    for double; a column whose independent part is above 1e-5 of the largest
-    column (norm^2 above 1e-10) is resolved by any of the FP64 or float-float
-    evaluations (relative error 2^-44 or below) without ambiguity.  1e-10 sits
-    four orders above the first level and leaves the second untouched."""
+    u^2 of the largest column's -- about 4e-15 for orbitals stored in single
+    precision (u = 2^-24), 1e-32 for double -- plus the evaluation's own
+    error (at most m 2^-53 in FP64 or 2^-44 in float-float per entry, m <=
+    2048 rows, so below 1e-22 in norm^2).  A column whose independent part is
+    above 1e-5 of the largest (norm^2 above 1e-10) is therefore told apart
+    from a dependent one by four orders in either precision."""
     R = np.array(A, dtype=np.float64)
     nr, nc = R.shape
     perm = np.arange(nc)
