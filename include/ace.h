@@ -80,7 +80,8 @@ typedef struct {
                           plane passes, 3 one persistent kernel for all three passes, 4 the
                           plane-kernel forward pass with the tile passes after it, 5 the
                           plane passes on clusters of two blocks holding half a plane each
-                          (2 and 3: single precision, n^3 boxes with n in {32, 80, 96, 160};
+                          (2: single precision, n^3 boxes with n in {32, 80, 96, 120, 160};
+                          3: single precision, n in {32, 80, 96, 160};
                           4: single precision, n in {32, 60, 80, 90, 96, 100, 108, 120, 160};
                           5: single precision, n = 120);
                           0 = automatic: where several apply (and pair_streams is 0, both 1

@@ -111,7 +111,7 @@ struct ace_plan {
     int lookahead = 1;         // L2 look-ahead of the pair passes, in transforms (env ACE_LOOKAHEAD)
     bool zline = false;        // per-pencil Coulomb pass (zline.cuh) with the kernel table d_kern
     float* d_kern = nullptr;   // 4 pi / |G|^2 / N in the tile passes' spectrum layout (zline only)
-    float* d_kern_t = nullptr; // the same for transposed planes (n % 16 == 0 cubes)
+    float* d_kern_t = nullptr; // the same for transposed planes (n % 8 == 0 cubes)
     double coul_rc = 0;        // Coulomb cutoff radius (0: 4 pi / |G|^2 with G = 0 dropped)
     int coul_g0 = 0;           // 1: the bare kernel keeps K(0) = 4 pi chi (auxiliary function)
     double coul_k0 = 0;        // that K(0)
@@ -1152,14 +1152,17 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     for (int k = 0; k < 4; ++k) P->r0_cand[k] = k < nr0 ? r0s[k] : 0;
     const int fixed_streams = opts && opts->pair_streams > 0 ? opts->pair_streams : 0;
     const bool t_ok = sizeof(R) == 4 && P->zline && P->d_kern_t != nullptr;
+    const bool p_ok = t_ok && pipeline_supported(P->n[0]);
     const bool h_ok = sizeof(R) == 4 && P->zline;  // every compile-time cube
     const bool c_ok = h_ok && halfplane_supported(P->n[0]);
     if (req < 0 || req > 5) return fail(ACE_ERR_INVALID_ARG, "pair_variant must be 0 (automatic), 1, 2, 3, 4 or 5");
     if (req == 5 && !c_ok)
         return fail(ACE_ERR_INVALID_ARG, "pair_variant 5 needs a single-precision 120^3 plan");
-    if ((req == 2 || req == 3) && !t_ok)
+    if (req == 2 && !t_ok)
         return fail(ACE_ERR_INVALID_ARG,
-                    "pair_variant 2 and 3 need a single-precision n^3 plan with n in {32, 80, 96, 160}");
+                    "pair_variant 2 needs a single-precision n^3 plan with n in {32, 80, 96, 120, 160}");
+    if (req == 3 && !p_ok)
+        return fail(ACE_ERR_INVALID_ARG, "pair_variant 3 needs a single-precision n^3 plan with n in {32, 80, 96, 160}");
     if (req == 4 && !h_ok)
         return fail(ACE_ERR_INVALID_ARG,
                     "pair_variant 4 needs a single-precision n^3 plan with n in {32, 60, 80, 90, 96, 100, 108, 120, 160}");
@@ -1173,10 +1176,8 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
     std::vector<Cand> cand;
     if (!fixed_streams || fixed_streams == 1) cand.push_back({1, 1, 0});
     if (!fixed_streams || fixed_streams >= 2) cand.push_back({1, fixed_streams ? fixed_streams : 2, 1});
-    if (t_ok) {
-        cand.push_back({2, fixed_streams ? fixed_streams : 2, 2});
-        cand.push_back({3, 1, 3});
-    }
+    if (t_ok) cand.push_back({2, fixed_streams ? fixed_streams : 2, 2});
+    if (p_ok) cand.push_back({3, 1, 3});
     if (h_ok) cand.push_back({4, fixed_streams ? fixed_streams : 2, 4});
     if (c_ok) cand.push_back({5, fixed_streams ? fixed_streams : 2, 5});
     if (sizeof(R) != 4 || cand.size() == 1) {  // double plans: no timing, the two-stream tile passes
@@ -1209,7 +1210,7 @@ int choose_pair_variant(ace_plan* P, const ace_opts* opts) {
                 bool r_ok = false;  // the radix plan (a fourth field; 0 when absent) is one of this plan's
                 for (int k = 0; k < nr0; ++k) r_ok = r_ok || r0s[k] == r2;
                 if ((got == 3 || got == 4) && v2 >= 1 && v2 <= 5 && s2 >= 1 && s2 <= 8 && rb2 >= 0 && rb2 <= 64 &&
-                    (v2 != 2 && v2 != 3 ? true : t_ok) && (v2 != 4 || h_ok) && (v2 != 5 || c_ok) && r_ok) {
+                    (v2 != 2 || t_ok) && (v2 != 3 || p_ok) && (v2 != 4 || h_ok) && (v2 != 5 || c_ok) && r_ok) {
                     v = v2;  // the last matching line wins
                     st = s2;
                     rb = rb2;

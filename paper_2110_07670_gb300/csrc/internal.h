@@ -131,8 +131,10 @@ inline int pair_radix_alternatives(int n, int* r0) {
     }
 }
 // plane passes with transposed spectrum planes (plane.cuh), N^3 boxes with
-// N % 16 == 0: which = 0 pair product + forward, 1 inverse + exchange accumulation
-constexpr bool tplane_supported(int n) { return n % 16 == 0; }
+// N % 8 == 0: which = 0 pair product + forward, 1 inverse + exchange accumulation
+constexpr bool tplane_supported(int n) { return n % 8 == 0; }
+// ... and as one persistent kernel (its pencil groups: 16 per warp, N / 16 warps)
+constexpr bool pipeline_supported(int n) { return n % 16 == 0; }
 cudaError_t tplane_pair_launch(int n, int which, const PassArgs& a, int batch, cudaStream_t st);
 // plane passes on clusters of two half-plane blocks (halfplane.cuh): which =
 // 0 pair product + forward, 1 inverse + exchange accumulation; n = 120

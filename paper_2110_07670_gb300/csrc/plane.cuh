@@ -276,7 +276,7 @@ template <int N, int F0 = 0, int TPL = 2>
 __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q, int z, cx<float>* tile,
                                                 const cx<float>* tw, double* red, double* e_dst) {
     using G = Geo<N, F0, TPL>;
-    static_assert(N % 16 == 0, "the vector epilogue tiles planes by 4 rows x 16 columns");
+    static_assert(N % 8 == 0, "the vector epilogue tiles planes by 4 rows x 16 (or 8) columns");
     constexpr long long NN = (long long)N * N, N3 = NN * N;
     const long long plane0 = (long long)z * NN;
     const int h = (int)threadIdx.x / N, line = (int)threadIdx.x - h * N;
@@ -338,7 +338,8 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
     // Exchange accumulation (Eq. 2) and pair energies (Eq. 4) in 4-wide
     // vectors: a half-warp takes 4 rows x 16 columns, lane (r, c) the four
     // columns 4c .. 4c + 3 of row r; with the pitch P = 1 (mod 16) its 16
-    // lanes read 16 distinct bank pairs.
+    // lanes read 16 distinct bank pairs.  (N % 16 != 0: a quarter-warp takes
+    // 4 rows x 8 columns, and tasks past the plane's are skipped.)
     float e1 = 0.0f, e2 = 0.0f;
     {
         const bool has2 = q.c >= 0, share = has2 && q.c == q.a, sym = a.symmetric != 0;
@@ -351,20 +352,25 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
         float* wc_p = reinterpret_cast<float*>(a.accl) + (has2 ? q.c : q.a) * N3 + plane0;
         float* wb_p = sym ? reinterpret_cast<float*>(a.accr) + q.b * N3 + plane0 : nullptr;
         float* wd_p = sym ? reinterpret_cast<float*>(a.accr) + (has2 ? q.d : q.b) * N3 + plane0 : nullptr;
-        const int hw = threadIdx.x >> 4, l16 = threadIdx.x & 15;
+        constexpr int TW = N % 16 == 0 ? 16 : 8;  // columns per task, TW lanes (4 rows x TW / 4 vectors)
+        const int hw = threadIdx.x / TW, l16 = threadIdx.x % TW;
         const int rr = l16 & 3, cc = l16 >> 2;
-        // N^2 / 64 tasks over N / 8 half-warps: N / 8 tasks each, taken U at a
-        // time with every load of the U tasks issued before the first update
-        constexpr int HW = G::NT / 16, PER = (N / 4) * (N / 16) / HW, U = PER % 2 == 0 ? 2 : 1;
-        static_assert(PER * HW == (N / 4) * (N / 16), "tasks divide evenly");
+        // N^2 / (4 TW) tasks over NT / TW lane groups, taken U at a time with
+        // every load of the U tasks issued before the first update
+        constexpr int HW = G::NT / TW, NTASK = (N / 4) * (N / TW);
+        constexpr int PER = (NTASK + HW - 1) / HW, U = PER % 2 == 0 ? 2 : 1;
+        constexpr bool EVEN = NTASK % HW == 0;
         for (int k0 = 0; k0 < PER; k0 += U) {
             float4 la[U], rb[U], lc[U], rd[U];
             long long rof[U];
             int sof[U];
+            bool on[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int task = hw + (k0 + u) * HW;
-                const int y = (task / (N / 16)) * 4 + rr, x = (task % (N / 16)) * 16 + 4 * cc;
+                on[u] = EVEN || task < NTASK;
+                if (!on[u]) continue;
+                const int y = (task / (N / TW)) * 4 + rr, x = (task % (N / TW)) * TW + 4 * cc;
                 rof[u] = (long long)y * N + x;
                 sof[u] = y * G::P + x;
                 la[u] = ldg4(la_p + rof[u]);
@@ -376,6 +382,7 @@ __device__ __forceinline__ void inv_accum_plane(const PassArgs& a, const Quad& q
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
+                if (!on[u]) continue;
                 const cx<float>* src = tile + sof[u];
                 const cx<float> v[4] = {src[0], src[1], src[2], src[3]};
                 const float4 v1 = make_float4(v[0].re, v[1].re, v[2].re, v[3].re);
@@ -461,8 +468,8 @@ cudaError_t tplane_launch(int which, const PassArgs& a, int batch, cudaStream_t 
     using G = plane_detail::Geo<N, F0, TPL>;
     if (which == 2)
         return plane_detail::launch_plane(plane_detail::pair_fwd<N, true, F0, TPL>, G::smem, N, G::NT, a, batch, st);
-    if constexpr (N % 16 != 0) {
-        return cudaErrorInvalidValue;  // transposed planes: n % 16 == 0 only
+    if constexpr (N % 8 != 0) {
+        return cudaErrorInvalidValue;  // transposed planes: n % 8 == 0 only
     } else {
         if (which == 0)
             return plane_detail::launch_plane(plane_detail::pair_fwd<N, false, F0, TPL>, G::smem, N, G::NT, a, batch, st);

@@ -418,11 +418,15 @@ def test_automatic_variant_choice_and_rejections():
     assert p64.config()["pair_variant"] == 1 and p64.config()["tune_ms"] == {}
     p64.close()
     small = small_system()
-    for v in (2, 3, 4):  # 16^3 has no compile-time kernels, double has none either
+    for v in (2, 3, 4, 5):  # 16^3 has no compile-time kernels, double has none either
         with pytest.raises(ace.AceError):
             ace.Plan(small["grid"], small["cell"], small["ecut"], 5, "mixed", pair_variant=v)
         with pytest.raises(ace.AceError):
             ace.Plan(s["grid"], s["cell"], s["ecut"], n, "fp64", pair_variant=v)
+    with pytest.raises(ace.AceError):  # the half-plane pairs exist for 120^3 only
+        ace.Plan(s["grid"], s["cell"], s["ecut"], n, "mixed", pair_variant=5)
+    with pytest.raises(ace.AceError):
+        ace.Plan(s["grid"], s["cell"], s["ecut"], n, "mixed", pair_variant=6)
 
 
 def _csr_set(pairs):

@@ -68,7 +68,7 @@ def system(n):
 # (one plan) for its own rotation of the plane swizzle
 CASES = [(80, 10, v) for v in (1, 2, 3, 4)] + \
         [(96, r, v) for r in (12, 8, 16) for v in (1, 2, 3, 4)] + \
-        [(120, r, v) for r in (12, 10, 8) for v in (1, 4, 5)] + \
+        [(120, r, v) for r in (12, 10, 8) for v in (1, 2, 4, 5)] + \
         [(160, r, v) for r in (16, 10) for v in (1, 2, 3, 4)]
 
 
@@ -129,6 +129,9 @@ def test_radix_plan_rejections(monkeypatch):
     with pytest.raises(ace.AceError):  # 32^3 has make_axis_plan's 8 x 4 only
         ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], 8, "mixed")
     monkeypatch.delenv("ACE_PAIR_RADIX")
+    s120 = system(120)
+    with pytest.raises(ace.AceError):  # the persistent pipeline needs n % 16 == 0
+        ace.Plan((120, 120, 120), s120["cell"], s120["ecut"], N_ORB, "mixed", pair_variant=3)
     p = ace.Plan(cfg["grid"], cfg["cell"], cfg["ecut"], 8, "mixed")
     assert len(p.config()["radix_ms"]) <= 1
     p.close()
