@@ -160,9 +160,50 @@ __device__ __forceinline__ void butterfly_at(cx<R>* row, const int (&idx)[RAD], 
     for (int s = 0; s < RAD; ++s) row[idx[s]] = u[s];
 }
 
+// The same butterfly with its twiddles already in registers (w[q] for q > 0,
+// conjugated for SGN > 0).
+template <int RAD, int SGN, typename R>
+__device__ __forceinline__ void butterfly_at_w(cx<R>* row, const int (&idx)[RAD], const cx<R> (&w)[RAD], bool tw_on) {
+    cx<R> u[RAD];
+#pragma unroll
+    for (int q = 0; q < RAD; ++q) u[q] = row[idx[q]];
+    if (SGN > 0 && tw_on) {
+#pragma unroll
+        for (int q = 1; q < RAD; ++q) u[q] = cmul(u[q], w[q]);
+    }
+    Dft<RAD, SGN, R>::run(u);
+    if (SGN < 0 && tw_on) {
+#pragma unroll
+        for (int s = 1; s < RAD; ++s) u[s] = cmul(u[s], w[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < RAD; ++s) row[idx[s]] = u[s];
+}
+
 template <int RAD, int SGN, int N, int LB, int NT, typename R>
 __device__ __forceinline__ void static_stage_rows_swizzled(cx<R>* buf, const cx<R>* tw) {
     constexpr int M = LB / RAD, NB = N / RAD, TOTAL = NB * N, TS = N / LB;
+    if constexpr (M > 1 && NT % NB == 0) {
+        // every butterfly of this thread has the same j (NT is a multiple of
+        // the butterflies per row): its twiddles are read once
+        const int i = (int)threadIdx.x % NB, j = i % M, beta = i / M;
+        cx<R> w[RAD];
+#pragma unroll
+        for (int q = 1; q < RAD; ++q) {
+            w[q] = tw[q * TS * j];
+            if (SGN > 0) w[q].im = -w[q].im;
+        }
+        w[0] = mk(R(1), R(0));
+        const int p0 = beta * LB + j;
+        for (int line = (int)threadIdx.x / NB; line < N; line += NT / NB) {
+            int idx[RAD];
+#pragma unroll
+            for (int q = 0; q < RAD; ++q) idx[q] = plane_swizzle(p0 + q * M, line, N);
+            butterfly_at_w<RAD, SGN, R>(buf + line * N, idx, w, j > 0);
+        }
+        __syncthreads();
+        return;
+    }
     for (int b = threadIdx.x; b < TOTAL; b += NT) {
         const int line = b / NB, i = b - line * NB;
         const int beta = i / M, j = i - beta * M;
