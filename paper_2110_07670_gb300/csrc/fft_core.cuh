@@ -444,6 +444,38 @@ struct CPlan {
 template <int RAD, int SGN, int N, int LB, int NLINES, int ESTRIDE, int LSTRIDE, int NT, typename R>
 __device__ __forceinline__ void static_stage(cx<R>* buf, const cx<R>* tw) {
     constexpr int M = LB / RAD, NB = N / RAD, TOTAL = NB * NLINES, TS = N / LB;
+    if constexpr (ESTRIDE == 1 && M > 1 && NT % NB == 0) {
+        // contiguous lines, NT a multiple of the butterflies per line: every
+        // butterfly of this thread has the same j, so its twiddles are read once
+        const int i = (int)threadIdx.x % NB, beta = i / M, j = i - beta * M;
+        cx<R> w[RAD];
+#pragma unroll
+        for (int q = 1; q < RAD; ++q) {
+            w[q] = tw[q * TS * j];
+            if (SGN > 0) w[q].im = -w[q].im;
+        }
+        const bool tw_on = j > 0;
+#pragma unroll 2
+        for (int line = (int)threadIdx.x / NB; line < NLINES; line += NT / NB) {
+            cx<R>* base = buf + line * LSTRIDE + beta * LB + j;
+            cx<R> u[RAD];
+#pragma unroll
+            for (int q = 0; q < RAD; ++q) u[q] = base[q * M];
+            if (SGN > 0 && tw_on) {
+#pragma unroll
+                for (int q = 1; q < RAD; ++q) u[q] = cmul(u[q], w[q]);
+            }
+            Dft<RAD, SGN, R>::run(u);
+            if (SGN < 0 && tw_on) {
+#pragma unroll
+                for (int q = 1; q < RAD; ++q) u[q] = cmul(u[q], w[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < RAD; ++q) base[q * M] = u[q];
+        }
+        __syncthreads();
+        return;
+    }
 #pragma unroll 2
     for (int b = threadIdx.x; b < TOTAL; b += NT) {
         int line, i;
