@@ -130,6 +130,13 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _plan_name(r0, n):
+    """'r0 x n/r0' for a two-stage plan of an axis of length n (its first radix r0)."""
+    if r0 <= 0:
+        return None
+    return f"{r0} x {n // r0}" if n // r0 > 1 else f"{r0}"
+
+
 class Plan:
     """One system: grid, cell (rows = lattice vectors, bohr), cutoff (Ry),
     the largest occupied set, and the precision ("mixed" or "fp64").
@@ -191,8 +198,8 @@ class Plan:
         rc, rms = (ctypes.c_int * 4)(), (ctypes.c_float * 4)()
         _check(load().ace_plan_radix(self.handle, ctypes.byref(r0), ctypes.byref(nc), rc, rms))
         return {"pair_variant": v.value, "pair_streams": st.value, "row_block": rb.value,
-                "radix_plan": f"{r0.value} x {self.grid[0] // r0.value}" if r0.value > 0 else None,
-                "radix_ms": {f"{rc[k]} x {self.grid[0] // rc[k]}": round(float(rms[k]), 3)
+                "radix_plan": _plan_name(r0.value, self.grid[0]),
+                "radix_ms": {_plan_name(rc[k], self.grid[0]): round(float(rms[k]), 3)
                              for k in range(nc.value) if rms[k] > 0},
                 "from_tune_cache": bool(cached.value),
                 "tune_ms": {k: round(float(x), 3) for k, x in
