@@ -81,7 +81,7 @@ constexpr bool cube_supported(int n) {
 }
 // threads of a plane block: the butterfly counts of both stages divide evenly
 constexpr int cube_xy_threads(int n) {
-    return n == 32 ? 128 : n == 96 ? 384 : n == 120 ? 480 : n == 160 ? 320 : (n * n >= 12000 ? 512 : 256);
+    return n == 32 ? 128 : n == 96 ? 256 : n == 120 ? 480 : n == 160 ? 320 : (n * n >= 12000 ? 512 : 256);
 }
 // Plane layout of N % 16 == 0 cubes: within each 16-element block of a row,
 // x position p sits in slot p ^ w, w = (((p >> 4) + s_N y) & 7) | ((y & 1) << 3);

@@ -260,7 +260,9 @@ struct CubeShape {
     static constexpr int kMaxThreads = NT;
     // two resident plane blocks where two N x N complex tiles fit in shared
     // memory (N <= 108); otherwise one, with the whole register file for it
-    static constexpr int kMinBlocks = (TZ == 1 && TY == N && TX == N && 2 * (N * N * 8 + 4096) <= 227 * 1024) ? 2 : 1;
+    static constexpr bool kPlane = TZ == 1 && TY == N && TX == N;
+    static constexpr int kMinBlocks = !kPlane ? 1 : (3 * (N * N * 8 + 2 * N * 8 + 1280) <= 228 * 1024 && NT <= 256) ? 3
+                                                  : (2 * (N * N * 8 + 4096) <= 227 * 1024 ? 2 : 1);
     static constexpr int n0 = N, n1 = N, n2 = N, tz = TZ, ty = TY, tx = TX;
     static constexpr int axes = (TZ == 1 && TY == N && TX == N) ? 3 : (TZ == N ? 4 : (TZ == 1 && TX == N ? 1 : 2));
     // Plane tiles of N % 16 == 0 boxes are stored (in shared and global memory)
@@ -744,6 +746,8 @@ cudaError_t launch_one(const PassArgs& a, const PassShape& s, int batch, cudaStr
     auto k = tile_pass<Shape, R, PRO, EPI, MID, SGN>;
     if (s.smem > 48 * 1024 && !stream_capturing(st)) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+        if (e == cudaSuccess && Shape::kMinBlocks > 2)  // three plane blocks need the whole shared carveout
+            e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
     }
     const int ntiles = (a.n0 / s.tz) * (a.n1 / s.ty) * (a.n2 / s.tx);
