@@ -261,8 +261,8 @@ def pass_bytes(n, N, esz=4, batch=64):
 # profiles/dram_pair_passes_water32_96cubed.md): the tile-pass forward kernel,
 # the plane-kernel forward pass of the hybrid variant, and the Coulomb and
 # accumulation kernels both variants share.
-MEASURED_TRAFFIC_PER_LAUNCH = {"pair_fwd": None, "pair_fwd_hybrid": 0.5464e9, "pair_coulomb": 0.8472e9,
-                               "pair_inv": 0.8511e9}
+MEASURED_TRAFFIC_PER_LAUNCH = {"pair_fwd": None, "pair_fwd_hybrid": 0.5473e9, "pair_coulomb": 0.8473e9,
+                               "pair_inv": 0.8595e9}
 
 
 def cpu_baseline(cfg, rows=5):
