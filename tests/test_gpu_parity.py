@@ -411,7 +411,8 @@ def test_automatic_variant_choice_and_rejections():
     n = len(s["psi"])
     plan = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "mixed")  # 32^3: all variants apply, timed
     cfg = plan.config()
-    assert cfg["pair_variant"] in (1, 2, 3) and cfg["pair_streams"] in (1, 2)
+    # any timed candidate may win (the half-plane pairs are not one at 32^3)
+    assert cfg["pair_variant"] in (1, 2, 3, 4) and cfg["pair_streams"] in (1, 2)
     assert set(cfg["tune_ms"]) == {"tile_1_stream", "tile_2_streams", "planes", "pipeline", "hybrid"}
     plan.close()
     p64 = ace.Plan(s["grid"], s["cell"], s["ecut"], n, "fp64")
